@@ -1,0 +1,376 @@
+"""Pins of the FP64 oracle to things other than itself (no GPU needed).
+
+Each test ties one piece of the oracle to an independent fact: the scene generator's
+separately written truth renderer, closed-form moments of Gaussian mixtures, Monte Carlo
+over the variational distribution, scipy's Poisson pmf, finite differences, brute force.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+from scipy import integrate, optimize, stats
+
+import synth
+from oracle import celeste_oracle as O
+
+T = torch.float64
+
+
+def _theta_gal(u, e_dev=0.4, e_axis=0.5, ang=0.7, scale=2.0, alpha=0.3):
+    th = np.zeros(27)
+    th[0:2] = u
+    th[2], th[3], th[4], th[5], th[6] = math.log(e_dev / (1 - e_dev)), math.log(e_axis / (1 - e_axis)), ang, math.log(scale), alpha
+    th[7], th[8], th[9], th[10] = 2.0, math.log(0.05), 2.3, math.log(0.08)
+    th[11:15], th[15:19] = [0.1, -0.2, 0.3, 0.05], np.log([0.02, 0.03, 0.01, 0.04])
+    th[19:23], th[23:27] = [-0.1, 0.25, 0.2, -0.15], np.log([0.03, 0.01, 0.02, 0.05])
+    return th
+
+
+@pytest.fixture(scope="module")
+def tiny_scene():
+    return synth.tiny(seed=11, n_sources=3, n_images=3)
+
+
+# ----------------------------------------------------------------------------- profiles
+def test_profiles_match_independent_renderer(tiny_scene):
+    """Oracle star/galaxy profiles equal the generator's separately written renderer."""
+    im = tiny_scene.images[1]
+    mix = tuple(torch.as_tensor(a) for a in (tiny_scene.exp_nu, tiny_scene.exp_tau, tiny_scene.dev_nu, tiny_scene.dev_tau))
+    u = np.array([14.3, 12.8])
+    th = _theta_gal(u)
+    pos = im.wcs[:4].reshape(2, 2) @ u + im.wcs[4:]
+    psf = O.psf_at(im, float(pos[0]), float(pos[1]))
+    shape = (1 / (1 + math.exp(-th[2])), 1 / (1 + math.exp(-th[3])), th[4], math.exp(th[5]))
+    for is_gal in (False, True):
+        sl, rate = synth._render_truth(im, pos, is_gal, shape, 1.0, 12)
+        ys, xs = np.mgrid[sl[0], sl[1]]
+        f0, f1 = O.profiles(torch.as_tensor(th), im, torch.as_tensor(xs.reshape(-1), dtype=T),
+                            torch.as_tensor(ys.reshape(-1), dtype=T), psf, mix)
+        ref = rate.reshape(-1) / im.iota
+        got = (f1 if is_gal else f0).numpy()
+        np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-300)
+
+
+def _big_grid(im_like_W=200, H=200):
+    ys, xs = np.mgrid[0:H, 0:im_like_W]
+    return torch.as_tensor(xs.reshape(-1), dtype=T), torch.as_tensor(ys.reshape(-1), dtype=T)
+
+
+def test_profiles_unit_flux_and_moments():
+    """Each profile sums to 1 over the pixel grid, and its first/second moments equal the
+    closed form of the Gaussian mixture: mean pos + sum w_k m_k, covariance
+    sum_k w_k (S_k + m_k m_k^T) - mbar mbar^T + (sum_j nu_j tau_j) A Sigma_g A^T."""
+    rng = np.random.default_rng(3)
+    psf = np.zeros((3, 6, 6))
+    psf[:, 0, 0] = np.log([0.2, 0.5, 0.3])
+    psf[:, 1, 0], psf[:, 2, 0] = [0.3, -0.2, 0.1], [-0.1, 0.25, 0.0]
+    psf[:, 3, 0], psf[:, 4, 0], psf[:, 5, 0] = np.log([1.2, 1.8, 2.5]), np.log([1.5, 1.1, 2.2]), np.arctanh([0.2, -0.25, 0.1])
+    ang = 0.4
+    A = 1.05 * np.array([[math.cos(ang), -math.sin(ang)], [math.sin(ang), math.cos(ang)]])
+    im = synth.Image(np.zeros((200, 200), np.float32), 2, 100.0, 200.0, np.array([A[0, 0], A[0, 1], A[1, 0], A[1, 1], 3.0, -2.0]), psf)
+    mix = tuple(torch.as_tensor(a) for a in (synth.mixtures.EXP_NU, synth.mixtures.EXP_TAU, synth.mixtures.DEV_NU, synth.mixtures.DEV_TAU))
+    u = np.array([88.4, 101.7])
+    e_dev, e_axis, e_ang, scale = 0.35, 0.45, 1.1, 2.5
+    th = _theta_gal(u, e_dev, e_axis, e_ang, scale)
+    pos = A @ u + im.wcs[4:]
+    w, m, cov = [t.numpy() for t in O.psf_at(im, float(pos[0]), float(pos[1]))]
+    px, py = _big_grid()
+    f0, f1 = O.profiles(torch.as_tensor(th), im, px, py, O.psf_at(im, float(pos[0]), float(pos[1])), mix)
+    P = np.stack([px.numpy(), py.numpy()], -1)
+    mbar = (w[:, None] * m).sum(0)
+    Sk = np.stack([np.array([[c[0], c[1]], [c[1], c[2]]]) for c in cov])
+    cov_psf = (w[:, None, None] * (Sk + m[:, :, None] * m[:, None, :])).sum(0) - np.outer(mbar, mbar)
+    R = np.array([[math.cos(e_ang), -math.sin(e_ang)], [math.sin(e_ang), math.cos(e_ang)]])
+    Sg = scale ** 2 * R @ np.diag([1, e_axis ** 2]) @ R.T
+    tau_bar = (1 - e_dev) * (synth.mixtures.EXP_NU * synth.mixtures.EXP_TAU).sum() + e_dev * (synth.mixtures.DEV_NU * synth.mixtures.DEV_TAU).sum()
+    for f, extra in ((f0.numpy(), 0.0), (f1.numpy(), tau_bar * A @ Sg @ A.T)):
+        assert abs(f.sum() - 1.0) < 1e-7
+        mean = (f[:, None] * P).sum(0)
+        np.testing.assert_allclose(mean, pos + mbar, atol=1e-6)
+        d = P - mean
+        C = (f[:, None, None] * d[:, :, None] * d[:, None, :]).sum(0)
+        np.testing.assert_allclose(C, cov_psf + extra, rtol=2e-5, atol=2e-5)
+
+
+def test_mixture_tables_half_light_radius():
+    """The tables are unit-flux mixtures whose circular half-light radius is 1 (within 1e-3)."""
+    for nu, tau in ((synth.mixtures.EXP_NU, synth.mixtures.EXP_TAU), (synth.mixtures.DEV_NU, synth.mixtures.DEV_TAU)):
+        assert abs(nu.sum() - 1.0) < 1e-12 and (nu > 0).all() and (tau > 0).all()
+        enclosed = lambda r: integrate.quad(lambda t: (nu / (2 * np.pi * tau) * np.exp(-t * t / (2 * tau))).sum() * 2 * np.pi * t, 0, r, limit=400, points=[0.01, 0.1])[0]
+        assert abs(enclosed(1.0) - 0.5) < 1e-3 * 0.5
+        assert abs(optimize.brentq(lambda r: enclosed(r) - 0.5, 0.2, 5.0) - 1.0) < 1e-3
+
+
+# ----------------------------------------------------------------------------- brightness, KL, pixel term
+def _sample_latents(rng, th, n):
+    a = rng.random(n) < 1 / (1 + math.exp(-th[6]))
+    r1 = np.where(a, th[9], th[7])
+    r2 = np.where(a, math.exp(th[10]), math.exp(th[8]))
+    c1 = np.where(a[:, None], th[19:23], th[11:15])
+    c2 = np.where(a[:, None], np.exp(th[23:27]), np.exp(th[15:19]))
+    logr = r1 + np.sqrt(r2) * rng.standard_normal(n)
+    c = c1 + np.sqrt(c2) * rng.standard_normal((n, 4))
+    return a, logr, c, (r1, r2, c1, c2)
+
+
+def test_brightness_moments_monte_carlo():
+    """E[G], E[G^2] at a pixel equal Monte Carlo over q(a) q(r|a) q(c|a) within 5 sigma."""
+    rng = np.random.default_rng(5)
+    th = _theta_gal([0, 0])
+    th[8], th[10] = math.log(0.2), math.log(0.15)
+    f0, f1 = 0.013, 0.021
+    for band in range(5):
+        a, logr, c, _ = _sample_latents(rng, th, 2_000_000)
+        lb = np.exp(logr + c @ synth.COLOR_MIX[band])
+        G = lb * np.where(a, f1, f0)
+        L1, L2 = O.brightness_moments(torch.as_tensor(th), band)
+        a1 = 1 / (1 + math.exp(-th[6]))
+        EG = (1 - a1) * float(L1[0]) * f0 + a1 * float(L1[1]) * f1
+        EG2 = (1 - a1) * float(L2[0]) * f0 ** 2 + a1 * float(L2[1]) * f1 ** 2
+        assert abs(G.mean() - EG) < 5 * G.std() / math.sqrt(len(G))
+        assert abs((G * G).mean() - EG2) < 5 * (G * G).std() / math.sqrt(len(G))
+
+
+def test_kl_monte_carlo():
+    """KL(q||p) of one source equals Monte Carlo of log q(z) - log p(z) within 5 sigma."""
+    rng = np.random.default_rng(9)
+    priors = np.array([0.3, 2.0, 1.0, 0.0, 0.25])
+    th = _theta_gal([0, 0], alpha=-0.4)
+    th[8], th[10] = math.log(0.3), math.log(0.5)
+    a, logr, c, (r1, r2, c1, c2) = _sample_latents(rng, th, 2_000_000)
+    a1 = 1 / (1 + math.exp(-th[6]))
+    logq = np.where(a, math.log(a1), math.log(1 - a1)) + stats.norm.logpdf(logr, r1, np.sqrt(r2)) \
+        + stats.norm.logpdf(c, c1, np.sqrt(c2)).sum(1)
+    logp = np.where(a, math.log(priors[0]), math.log(1 - priors[0])) + stats.norm.logpdf(logr, priors[1], math.sqrt(priors[2])) \
+        + stats.norm.logpdf(c, priors[3], math.sqrt(priors[4])).sum(1)
+    d = logq - logp
+    kl = float(O.kl_source(torch.as_tensor(th), priors))
+    assert abs(d.mean() - kl) < 5 * d.std() / math.sqrt(len(d))
+
+
+def test_pixel_term_is_poisson_logpmf():
+    """With Var[F] = 0 the pixel term is the Poisson log pmf (textbook)."""
+    x = torch.tensor([0.0, 1.0, 7.0, 130.0, 1000.0])
+    E = torch.tensor([0.5, 2.0, 6.3, 141.0, 990.0])
+    got = O.pixel_term(x, E, torch.zeros_like(E), torch.lgamma(x + 1)).numpy()
+    np.testing.assert_allclose(got, stats.poisson.logpmf(x.numpy().astype(int), E.numpy()), rtol=1e-12)
+
+
+def test_delta_method_error_is_second_order():
+    """log E - V/(2E^2) approximates E[log F] of a lognormal F to O((V/E^2)^2)."""
+    for cv2 in (1e-3, 1e-2):
+        s2 = math.log1p(cv2)
+        E, V = 50.0, cv2 * 2500.0
+        exact = math.log(E) - 0.5 * s2        # E[log F] for lognormal with mean E, variance V
+        approx = math.log(E) - V / (2 * E * E)
+        assert abs(exact - approx) < cv2 * cv2
+
+
+def test_rate_moments_monte_carlo(tiny_scene):
+    """Per-pixel E[F] and Var[F] (target + neighbours, sky, calibration) equal Monte Carlo of the model."""
+    orc = O.Oracle(tiny_scene)
+    s = next(s for s in range(tiny_scene.n_sources) if any(orc.nbr[s][n] for n in orc.nbr[s]))
+    n = next(n for n in orc.nbr[s] if orc.nbr[s][n])
+    thetas = tiny_scene.theta0.copy()
+    thetas[:, 8] = thetas[:, 10] = math.log(0.1)
+    thetas[:, 15:19] = thetas[:, 23:27] = math.log(0.05)
+    thetas[:, 6] = 0.2
+    data = orc._patch_data(s, thetas)
+    k = [r[0] for r in orc.rects[s]].index(n)
+    im, px, py, x, lgx, bE, bV, psf = data[k]
+    sel = torch.arange(0, len(px), max(1, len(px) // 7))
+    px, py, bE, bV = px[sel], py[sel], bE[sel], bV[sel]
+    EG, EG2 = O.source_moments(torch.as_tensor(thetas[s]), im, px, py, psf, orc.mix)
+    E = im.sky + im.iota * (bE + EG)
+    V = im.iota ** 2 * (bV + EG2 - EG * EG)
+    rng = np.random.default_rng(2)
+    N = 400_000
+    F = np.full((N, len(px)), im.sky)
+    for t in [s] + orc.nbr[s][n]:
+        f0, f1 = O.profiles(torch.as_tensor(thetas[t]), im, px, py, orc.psf_for(t, n), orc.mix)
+        a, logr, c, _ = _sample_latents(rng, thetas[t], N)
+        lb = np.exp(logr + c @ synth.COLOR_MIX[im.band])
+        F += im.iota * lb[:, None] * np.where(a[:, None], f1.numpy()[None], f0.numpy()[None])
+    se = F.std(0) / math.sqrt(N)
+    assert np.all(np.abs(F.mean(0) - E.numpy()) < 5 * se + 1e-9)
+    var_se = np.sqrt(((F - F.mean(0)) ** 4).mean(0) / N)
+    assert np.all(np.abs(F.var(0) - V.numpy()) < 5 * var_se + 1e-9)
+
+
+def test_elbo_differences_are_poisson_loglik_differences():
+    """Star with (near) zero flux/colour variance and P(galaxy) ~ 0: moving it changes the ELBO by
+    exactly the change of the Poisson log-likelihood of an independently rendered star."""
+    sc = synth.single_source(seed=21, size=25, is_gal=False, log_r=4.0)
+    orc = O.Oracle(sc)
+    th = sc.theta0[0].copy()
+    th[6] = -60.0
+    th[8] = th[10] = -40.0
+    th[15:19] = th[23:27] = -40.0
+    fl = np.exp(th[7] + synth.COLOR_MIX @ th[11:15])
+
+    rects = {r[0]: r[1:] for r in orc.rects[0]}
+
+    def loglik(u):
+        tot = 0.0
+        for n, im in enumerate(sc.images):
+            x0, x1, y0, y1 = rects[n]
+            pos = im.wcs[:4].reshape(2, 2) @ u + im.wcs[4:]
+            # the oracle fixes the PSF at the catalog position; evaluate the renderer's PSF there too
+            rate = np.full((im.H, im.W), im.sky)
+            w, m, cov = synth._psf_at(im.psf, *(im.wcs[:4].reshape(2, 2) @ sc.u0[0] + im.wcs[4:]), im.H, im.W)
+            ys, xs = np.mgrid[0:im.H, 0:im.W]
+            for k in range(3):
+                d = np.stack([xs - pos[0] - m[k, 0], ys - pos[1] - m[k, 1]], -1)
+                Sinv = np.linalg.inv(cov[k])
+                q = np.einsum('...i,ij,...j->...', d, Sinv, d)
+                rate += im.iota * fl[im.band] * w[k] * np.exp(-0.5 * q) / (2 * np.pi * math.sqrt(np.linalg.det(cov[k])))
+            lp = stats.poisson.logpmf(im.pixels.astype(np.int64), rate)
+            tot += lp[y0:y1 + 1, x0:x1 + 1].sum()
+        return tot
+
+    th2 = th.copy()
+    th2[0:2] += [0.31, -0.17]
+    dL = orc.elbo(0, th2, sc.theta0) - orc.elbo(0, th, sc.theta0)
+    assert abs(dL - (loglik(th2[0:2]) - loglik(th[0:2]))) < 1e-6 * abs(dL) + 1e-8
+    # changing only the unused (galaxy) colour variance changes the ELBO by -a_gal * dKL ~ 0,
+    # while changing the used (star) flux variance changes it by the KL and likelihood terms
+    th3 = th.copy()
+    th3[23:27] = -30.0
+    assert abs(orc.elbo(0, th3, sc.theta0) - orc.elbo(0, th, sc.theta0)) < 1e-12
+
+
+# ----------------------------------------------------------------------------- derivatives
+def test_gradient_and_hessian_match_finite_differences(tiny_scene):
+    """Autodiff gradient vs Richardson-extrapolated central differences of the ELBO; Hessian vs
+    central differences of the gradient; Hessian symmetric."""
+    orc = O.Oracle(tiny_scene)
+    s = 0
+    th = tiny_scene.theta0[s].copy()
+    th[6] = 0.4
+    th[8] = th[10] = math.log(0.1)
+    f = orc.elbo_fn(s, tiny_scene.theta0)
+    L, g, H = orc.elbo_grad_hess(s, th, tiny_scene.theta0)
+    fv = lambda t: float(f(torch.as_tensor(t)))
+    gfd = np.zeros(27)
+    for i in range(27):
+        def cd(h):
+            e = np.zeros(27)
+            e[i] = h
+            return (fv(th + e) - fv(th - e)) / (2 * h)
+        h = 1e-3
+        gfd[i] = (4 * cd(h / 2) - cd(h)) / 3
+    scale = np.maximum(np.abs(g), 1e-3 * np.abs(g).max())
+    assert np.all(np.abs(gfd - g) <= 1e-6 * scale + 1e-7), np.abs(gfd - g) / scale
+    assert np.abs(H - H.T).max() <= 1e-12 * np.abs(H).max()
+    gradf = lambda t: torch.func.grad(f)(torch.as_tensor(t)).numpy()
+    Hfd = np.zeros((27, 27))
+    for i in range(27):
+        e = np.zeros(27)
+        e[i] = 1e-4
+        Hfd[:, i] = (gradf(th + e) - gradf(th - e)) / 2e-4
+    Hs = np.maximum(np.abs(H), 1e-3 * np.sqrt(np.abs(np.outer(np.diag(H), np.diag(H)))))
+    assert np.all(np.abs(Hfd - H) <= 1e-5 * Hs + 1e-6), (np.abs(Hfd - H) / Hs).max()
+
+
+# ----------------------------------------------------------------------------- trust region
+def _model(g, B, p):
+    return g @ p + 0.5 * p @ B @ p
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_tr_subproblem_brute_force(seed):
+    """The subproblem solution is feasible and no point of a dense sampling of the ball beats it."""
+    rng = np.random.default_rng(seed)
+    n = 2 if seed % 2 == 0 else 3
+    M = rng.normal(size=(n, n))
+    B = M + M.T + rng.uniform(-2, 2) * np.eye(n)
+    g = rng.normal(size=n) * rng.choice([1e-2, 1.0, 10.0])
+    delta = rng.uniform(0.1, 3.0)
+    p, pred, _ = O.tr_subproblem(g, B, delta)
+    assert np.linalg.norm(p) <= delta * (1 + 1e-9)
+    assert abs(pred + _model(g, B, p)) < 1e-10 * (1 + abs(pred))
+    if n == 2:
+        r, a = np.meshgrid(np.linspace(0, delta, 400), np.linspace(0, 2 * np.pi, 1600))
+        P = np.stack([r * np.cos(a), r * np.sin(a)], -1).reshape(-1, 2)
+    else:
+        v = rng.normal(size=(400_000, 3))
+        v /= np.linalg.norm(v, axis=1, keepdims=True)
+        P = np.concatenate([v * delta, v * delta * rng.random((400_000, 1)) ** (1 / 3)])
+    vals = P @ g + 0.5 * np.einsum('ij,jk,ik->i', P, B, P)
+    assert _model(g, B, p) <= vals.min() + 1e-9 * (1 + abs(vals.min()))
+
+
+def test_tr_subproblem_hard_case():
+    """g orthogonal to the most negative eigenvector: the step rides that eigenvector to the boundary."""
+    Q, _ = np.linalg.qr(np.random.default_rng(1).normal(size=(4, 4)))
+    lam = np.array([-2.0, 1.0, 3.0, 5.0])
+    B = Q @ np.diag(lam) @ Q.T
+    g = Q[:, 1] * 0.5 + Q[:, 3] * 1.0
+    delta = 2.0
+    p, pred, hard = O.tr_subproblem(g, B, delta)
+    assert hard
+    assert abs(np.linalg.norm(p) - delta) < 1e-10
+    # optimality: (B + 2 I) p = -g with lambda = -lambda_min = 2
+    np.testing.assert_allclose((B + 2.0 * np.eye(4)) @ p, -g, atol=1e-10)
+
+
+# ----------------------------------------------------------------------------- Newton
+def test_newton_recovers_noise_free_star():
+    """Noise-free bright star: Newton returns the true position within 1e-3 px in <= 50 iterations."""
+    sc = synth.single_source(seed=4, size=21, noise=False, is_gal=False, log_r=4.5)
+    orc = O.Oracle(sc)
+    r = orc.newton(0, sc.theta0[0], sc.theta0)
+    assert r["status"] == O.STATUS_CONVERGED and r["iters"] <= 50
+    assert np.abs(r["theta"][0:2] - sc.truth["u"][0]).max() < 1e-3
+    assert abs(r["theta"][7] - sc.truth["log_r"][0]) < 0.05          # flux within prior pull
+
+
+@pytest.mark.slow
+def test_newton_multistart_same_optimum():
+    """Several perturbed starts reach the same optimum (identified parameters within 1e-4)."""
+    sc = synth.single_source(seed=8, size=21, is_gal=True, log_r=4.0)
+    orc = O.Oracle(sc)
+    rng = np.random.default_rng(0)
+    sols = []
+    for k in range(4):
+        th0 = sc.theta0[0] + (rng.normal(0, 0.05, 27) if k else 0.0)
+        r = orc.newton(0, th0, sc.theta0)
+        assert r["status"] == O.STATUS_CONVERGED and r["iters"] <= 50
+        sols.append(r)
+    ref = sols[0]
+    for r in sols[1:]:
+        assert abs(r["elbo"] - ref["elbo"]) <= 1e-8 * abs(ref["elbo"]) * 10
+        d = r["theta"] - ref["theta"]
+        # identified block: position, galaxy shape, type logit, galaxy brightness
+        idx = [0, 1, 2, 3, 5, 9, 10] + list(range(19, 27))
+        assert np.abs(d[idx]).max() < 1e-4, d[idx]
+        assert abs(math.remainder(d[4], math.pi)) < 1e-4
+
+
+# ----------------------------------------------------------------------------- geometry
+def test_patches_and_neighbours_brute_force():
+    sc = synth.tiny(seed=3, n_sources=5, n_images=2, H=40, W=44, radius=(4, 8))
+    rects = O.patch_rects(sc)
+    nbr = O.neighbour_lists(sc, rects)
+    masks = {}
+    for s in range(sc.n_sources):
+        for n, im in enumerate(sc.images):
+            p = im.wcs[:4].reshape(2, 2) @ sc.u0[s] + im.wcs[4:]
+            c = np.floor(p + 0.5).astype(int)
+            ys, xs = np.mgrid[0:im.H, 0:im.W]
+            inside = 0 <= c[0] < im.W and 0 <= c[1] < im.H
+            m = (np.abs(xs - c[0]) <= sc.radius[s]) & (np.abs(ys - c[1]) <= sc.radius[s]) & inside
+            masks[(s, n)] = m
+            r = [t for t in rects[s] if t[0] == n]
+            if not inside:
+                assert not r
+                continue
+            (_, x0, x1, y0, y1), = r
+            ref = np.zeros_like(m)
+            ref[y0:y1 + 1, x0:x1 + 1] = True
+            assert (ref == m).all()
+    for s in range(sc.n_sources):
+        for (n, *_r) in rects[s]:
+            want = sorted(t for t in range(sc.n_sources) if t != s and (masks[(s, n)] & masks[(t, n)]).any())
+            assert sorted(nbr[s][n]) == want
