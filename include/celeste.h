@@ -1,0 +1,193 @@
+/*
+ * celeste.h - C ABI of the GB300 (sm_103a) Celeste per-source ELBO / Newton library.
+ *
+ * The operations follow "Learning an Astronomical Catalog of the Visible Universe through
+ * Scalable Bayesian Inference" (Regier et al.):
+ *   - Sec. "The Celeste Model": images with fixed metadata Lambda_n (PSF, sky, calibration,
+ *     pixel<->sky map) whose pixel counts are Poisson with a rate set by the catalog;
+ *   - Sec. "Variational Inference", Eq. (1)-(3): the ELBO and the factorised q;
+ *     each source's parameters are optimised with its neighbours held fixed, by Newton's
+ *     method with a trust region and the exact gradient and dense Hessian.
+ *
+ * Conventions (all calls):
+ *   - 27 free variational parameters per source, float64, row-major [S][27]:
+ *       0,1 world position u; 2 logit fracDev; 3 logit axis ratio; 4 angle (rad);
+ *       5 log half-light radius; 6 logit P(galaxy);
+ *       7,8 star mean / log variance of log r-band flux; 9,10 the same for galaxies;
+ *       11-14 star colour means; 15-18 star colour log variances;
+ *       19-22 galaxy colour means; 23-26 galaxy colour log variances.
+ *   - Pixel (row i, col j) of an image has its centre at pixel coordinates (x, y) = (j, i);
+ *     world -> pixel map p = A u + o with wcs = {A00, A01, A10, A11, o0, o1}.
+ *   - "device" pointers are CUDA device memory of the current device; "host" pointers are
+ *     ordinary host memory.  The library never frees caller memory.
+ *   - Calls taking a stream are asynchronous on it, except where stated.
+ *   - Return value: CELESTE_OK or a CELESTE_ERR_* code; celeste_strerror() describes it and
+ *     celeste_last_error_detail() gives the message of the last failure on this thread.
+ */
+#ifndef CELESTE_H
+#define CELESTE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CELESTE_NPARAM 27
+#define CELESTE_NPSF 3
+#define CELESTE_NEXP 6
+#define CELESTE_NDEV 8
+#define CELESTE_MAX_RADIUS 64
+
+typedef struct CUstream_st* celeste_stream_t; /* identical to cudaStream_t */
+
+enum {
+  CELESTE_OK = 0,
+  CELESTE_ERR_INVALID_ARG = 1, /* a descriptor or argument failed validation; nothing launched */
+  CELESTE_ERR_CUDA = 2,        /* a CUDA runtime call failed */
+  CELESTE_ERR_TIMEOUT = 3,     /* a bounded device-side wait ran out */
+  CELESTE_ERR_WORKSPACE = 4,   /* workspace missing, too small or misaligned */
+  CELESTE_ERR_STATE = 5        /* call order violated (e.g. elbo before bind) */
+};
+
+/* Per-source outcome of celeste_newton_batch. */
+enum {
+  CELESTE_STATUS_CONVERGED = 0,
+  CELESTE_STATUS_MAX_ITER = 1,
+  CELESTE_STATUS_NONFINITE = 2,
+  CELESTE_STATUS_RADIUS_COLLAPSE = 3
+};
+
+/* Bits of `want` in celeste_elbo_batch. */
+#define CELESTE_WANT_ELBO 1u
+#define CELESTE_WANT_GRAD 2u
+#define CELESTE_WANT_HESS 4u
+
+/* One image and its metadata Lambda_n (Sec. "The Celeste Model").
+ *   pixels: device, float32 row-major [height][width] photon counts (>= 0, finite);
+ *           must stay valid while the problem is bound.
+ *   band:   0..4 = u,g,r,i,z; reference band is r (2).
+ *   sky:    expected background counts per pixel (> 0).
+ *   iota:   calibration, counts per nanomaggy (> 0).
+ *   psf:    3 Gaussian components x 6 parameters {weight logit, mean x, mean y,
+ *           log sigma x, log sigma y, atanh correlation}, each a quadratic polynomial in
+ *           (xh, yh) = (2x/(width-1)-1, 2y/(height-1)-1) with coefficients for
+ *           {1, xh, yh, xh^2, xh*yh, yh^2}; weights are the softmax of the logits. */
+typedef struct {
+  int32_t height, width, band;
+  const float* pixels;
+  double sky, iota;
+  double wcs[6];
+  double psf[CELESTE_NPSF][6][6];
+} celeste_image_desc;
+
+/* The problem: images, the catalog locations that anchor each source's patches, priors
+ * and the galaxy-profile mixture tables (all host memory, copied by celeste_problem_create).
+ *   u0:     host [S][2] catalog world positions.  Source s's patch in image n is the
+ *           (2R+1)^2 pixel square centred on round(A_n u0_s + o_n), present when that centre
+ *           lies inside image n, clipped to the image; the PSF of (s, n) is evaluated at
+ *           A_n u0_s + o_n and held fixed.
+ *   radius: host [S] patch half-width R in 1..CELESTE_MAX_RADIUS.
+ *   priors: {P(galaxy), mean of log r, variance of log r, colour mean, colour variance}.
+ *   exp_* / dev_*: unit-flux circular mixtures sum_j nu_j N(0, tau_j I) (nu > 0, tau > 0)
+ *           for the exponential and de Vaucouleurs profiles.
+ *   tile_pixels: pixels per work tile (128, 256, 512 or 1024; 0 = default 256). */
+typedef struct {
+  int32_t n_images;
+  const celeste_image_desc* images;
+  int32_t n_sources;
+  const double* u0;
+  const int32_t* radius;
+  double priors[5];
+  double exp_nu[CELESTE_NEXP], exp_tau[CELESTE_NEXP];
+  double dev_nu[CELESTE_NDEV], dev_tau[CELESTE_NDEV];
+  int32_t tile_pixels;
+} celeste_problem_desc;
+
+typedef struct celeste_problem celeste_problem;
+
+/* Trust-region Newton options (Sec. "Variational Inference": Newton with a trust region,
+ * machine tolerance within 50 iterations).  Zero-initialised fields take the defaults shown. */
+typedef struct {
+  int32_t max_iter;   /* 50 */
+  double ftol;        /* 1e-8: stop after an accepted step with |f_k - f_k+1| <= ftol |f_k+1| */
+  double gtol;        /* 1e-10: stop when max |grad| <= gtol */
+  double delta0;      /* 1.0: initial radius (used where delta_inout[s] <= 0) */
+  double delta_max;   /* 1e4 */
+  double eta;         /* 0.1: acceptance threshold on actual/predicted reduction */
+  double delta_min;   /* 1e-12: below this the source stops with RADIUS_COLLAPSE */
+} celeste_newton_opts;
+
+/* Validate the description and build the host-side layout (patches, neighbours, work
+ * tiles).  Synchronous, host only, allocates no device memory.  On success *out owns copies
+ * of every host array; free it with celeste_problem_destroy.
+ * Errors: CELESTE_ERR_INVALID_ARG (non-finite or out-of-range metadata, radius outside
+ * 1..64, non-SPD PSF covariance, bad mixture table, NULL pointers). */
+int celeste_problem_create(const celeste_problem_desc* desc, celeste_problem** out);
+
+/* Device workspace bytes needed by celeste_problem_bind (>0). */
+size_t celeste_problem_workspace_bytes(const celeste_problem* p);
+
+/* Counts of the layout: sources, patches, tiles, total patch pixels, neighbour entries. */
+int celeste_problem_counts(const celeste_problem* p, int64_t counts[5]);
+
+/* Bind a caller-owned device workspace (>= workspace_bytes, 256-byte aligned) and upload the
+ * layout into it; evaluates each patch's PSF on the device.  The workspace must outlive
+ * every later call on this problem.  Asynchronous on `stream`. */
+int celeste_problem_bind(celeste_problem* p, void* workspace, size_t bytes, celeste_stream_t stream);
+
+/* Fixed part of every patch pixel's rate: gathers the counts and renders the neighbours'
+ * expected brightness and variance (Sec. "Variational Inference": neighbours held fixed).
+ *   nbr_theta: device float64 [S][27], the parameters the neighbours are fixed at.
+ * Must run after bind and again whenever the neighbours' parameters change. */
+int celeste_render_background(celeste_problem* p, const double* nbr_theta, celeste_stream_t stream);
+
+/* ELBO of every source's subproblem and, on request, its exact gradient and dense Hessian
+ * w.r.t. the 27 free parameters (Eq. (1)-(2) restricted to the source's patches, minus its KL).
+ *   theta: device float64 [S][27].
+ *   want:  OR of CELESTE_WANT_*; outputs not wanted may be NULL.
+ *   elbo:  device float64 [S]; grad: device float64 [S][27]; hess: device float64 [S][27][27].
+ * Pixel arithmetic is float32; the cross-pixel sums and the assembly are float64. */
+int celeste_elbo_batch(celeste_problem* p, const double* theta, unsigned want,
+                       double* elbo, double* grad, double* hess, celeste_stream_t stream);
+
+/* Trust-region Newton on every source's subproblem, all sources in one batch.
+ *   theta_inout: device float64 [S][27], start in, optimum out.
+ *   delta_inout: device float64 [S] trust radius (<= 0 means opts->delta0); the final radius
+ *                is written back, so a later call resumes where this one stopped.
+ *   iters_out, status_out: device int32 [S]; elbo_out: device float64 [S] (may be NULL).
+ * The host waits on `stream` once per iteration to test whether any source is still active. */
+int celeste_newton_batch(celeste_problem* p, double* theta_inout, const celeste_newton_opts* opts,
+                         double* delta_inout, int32_t* iters_out, int32_t* status_out,
+                         double* elbo_out, celeste_stream_t stream);
+
+/* Device-time accounting of the library's own kernels, for benchmarks.
+ *   celeste_profile_start: reset and start recording.  While recording, every launch of the
+ *     ELBO+gradient+Hessian pixel kernel and of the value-only pixel kernel is bracketed by CUDA
+ *     events recorded on the stream it is launched on.
+ *   celeste_profile_stop: stop recording, wait for the recorded events and fill *out.
+ * Not part of the numerical path; the counters cost one atomic per pixel-kernel CTA. */
+typedef struct {
+  double full_ms;             /* summed duration of ELBO+gradient+Hessian pixel-kernel launches */
+  double value_ms;            /* summed duration of value-only pixel-kernel launches */
+  int64_t full_launches, value_launches;
+  int64_t full_pixels;        /* pixel evaluations with value, gradient and Hessian */
+  int64_t value_pixels;       /* pixel evaluations with value only */
+  int64_t kernel_launches;    /* every kernel launched by the library while recording */
+  int64_t newton_iterations;  /* trust-region iterations run by celeste_newton_batch */
+} celeste_profile_stats;
+
+int celeste_profile_start(celeste_problem* p);
+int celeste_profile_stop(celeste_problem* p, celeste_profile_stats* out);
+
+/* Release the problem (not the caller's workspace).  NULL is ignored. */
+void celeste_problem_destroy(celeste_problem* p);
+
+const char* celeste_strerror(int code);
+const char* celeste_last_error_detail(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CELESTE_H */

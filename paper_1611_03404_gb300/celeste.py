@@ -1,0 +1,262 @@
+"""Thin ctypes binding of the C ABI in include/celeste.h (argument marshalling only).
+
+Every step of the computation runs in the CUDA library; this module converts Python /
+torch arguments into the plain pointers and sizes the C functions take, and raises on
+error codes.  There is no fallback: if the library is missing, importing fails loudly.
+"""
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+NPARAM = 27
+WANT_ELBO, WANT_GRAD, WANT_HESS = 1, 2, 4
+STATUS_CONVERGED, STATUS_MAX_ITER, STATUS_NONFINITE, STATUS_RADIUS_COLLAPSE = 0, 1, 2, 3
+
+
+class CelesteError(RuntimeError):
+    pass
+
+
+class ImageDesc(ctypes.Structure):
+    _fields_ = [("height", ctypes.c_int32), ("width", ctypes.c_int32), ("band", ctypes.c_int32),
+                ("pixels", ctypes.c_void_p), ("sky", ctypes.c_double), ("iota", ctypes.c_double),
+                ("wcs", ctypes.c_double * 6), ("psf", ctypes.c_double * 108)]
+
+
+class ProblemDesc(ctypes.Structure):
+    _fields_ = [("n_images", ctypes.c_int32), ("images", ctypes.POINTER(ImageDesc)),
+                ("n_sources", ctypes.c_int32), ("u0", ctypes.POINTER(ctypes.c_double)),
+                ("radius", ctypes.POINTER(ctypes.c_int32)), ("priors", ctypes.c_double * 5),
+                ("exp_nu", ctypes.c_double * 6), ("exp_tau", ctypes.c_double * 6),
+                ("dev_nu", ctypes.c_double * 8), ("dev_tau", ctypes.c_double * 8),
+                ("tile_pixels", ctypes.c_int32)]
+
+
+class NewtonOpts(ctypes.Structure):
+    _fields_ = [("max_iter", ctypes.c_int32), ("ftol", ctypes.c_double), ("gtol", ctypes.c_double),
+                ("delta0", ctypes.c_double), ("delta_max", ctypes.c_double), ("eta", ctypes.c_double),
+                ("delta_min", ctypes.c_double)]
+
+
+class ProfileStats(ctypes.Structure):
+    _fields_ = [("full_ms", ctypes.c_double), ("value_ms", ctypes.c_double), ("full_launches", ctypes.c_int64),
+                ("value_launches", ctypes.c_int64), ("full_pixels", ctypes.c_int64), ("value_pixels", ctypes.c_int64),
+                ("kernel_launches", ctypes.c_int64), ("newton_iterations", ctypes.c_int64)]
+
+
+EXPORTED = ["celeste_problem_create", "celeste_problem_workspace_bytes", "celeste_problem_counts",
+            "celeste_problem_bind", "celeste_render_background", "celeste_elbo_batch", "celeste_newton_batch",
+            "celeste_problem_destroy", "celeste_strerror", "celeste_last_error_detail", "celeste_profile_start",
+            "celeste_profile_stop"]
+
+
+def load_library(path=None):
+    path = path or _build.LIB
+    if not os.path.exists(path):
+        raise CelesteError(f"CUDA library not built: {path} (run __graft_entry__.build())")
+    lib = ctypes.CDLL(path)
+    vp, i32, u32, dp = ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint32, ctypes.c_void_p
+    sig = {
+        "celeste_problem_create": (ctypes.c_int, [ctypes.POINTER(ProblemDesc), ctypes.POINTER(vp)]),
+        "celeste_problem_workspace_bytes": (ctypes.c_size_t, [vp]),
+        "celeste_problem_counts": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int64)]),
+        "celeste_problem_bind": (ctypes.c_int, [vp, vp, ctypes.c_size_t, vp]),
+        "celeste_render_background": (ctypes.c_int, [vp, dp, vp]),
+        "celeste_elbo_batch": (ctypes.c_int, [vp, dp, u32, dp, dp, dp, vp]),
+        "celeste_newton_batch": (ctypes.c_int, [vp, dp, ctypes.POINTER(NewtonOpts), dp, dp, dp, dp, vp]),
+        "celeste_problem_destroy": (None, [vp]),
+        "celeste_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+        "celeste_last_error_detail": (ctypes.c_char_p, []),
+        "celeste_profile_start": (ctypes.c_int, [vp]),
+        "celeste_profile_stop": (ctypes.c_int, [vp, ctypes.POINTER(ProfileStats)]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_LIB = None
+
+
+def lib():
+    global _LIB
+    if _LIB is None:
+        _LIB = load_library()
+    return _LIB
+
+
+def _check(rc):
+    if rc != 0:
+        L = lib()
+        raise CelesteError(f"{L.celeste_strerror(rc).decode()}: {L.celeste_last_error_detail().decode()}")
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Problem:
+    """A bound problem: images resident on the device, layout and workspace owned here.
+
+    scene: an object with .images (each .pixels [H,W] float32, .band, .sky, .iota, .wcs[6],
+    .psf[3,6,6]), .u0 [S,2], .radius [S], .priors [5] and the exp/deV mixture tables.
+    device_pixels: optional list of CUDA float32 tensors already holding the images."""
+
+    def __init__(self, scene, device="cuda", tile_pixels=256, device_pixels=None, stream=None):
+        L = lib()
+        self.device = torch.device(device)
+        if device_pixels is None:
+            device_pixels = [torch.as_tensor(np.ascontiguousarray(im.pixels, np.float32)).to(self.device)
+                             for im in scene.images]
+        self.pixels = [p.contiguous() for p in device_pixels]
+        n = len(scene.images)
+        self._imgs = (ImageDesc * n)()
+        for k, im in enumerate(scene.images):
+            d = self._imgs[k]
+            d.height, d.width = self.pixels[k].shape
+            d.band = int(im.band)
+            d.pixels = self.pixels[k].data_ptr()
+            d.sky, d.iota = float(im.sky), float(im.iota)
+            d.wcs[:] = [float(v) for v in im.wcs]
+            d.psf[:] = [float(v) for v in np.asarray(im.psf, np.float64).reshape(-1)]
+        self._u0 = np.ascontiguousarray(scene.u0, np.float64)
+        self._rad = np.ascontiguousarray(scene.radius, np.int32)
+        desc = ProblemDesc()
+        desc.n_images = n
+        desc.images = self._imgs
+        desc.n_sources = self._u0.shape[0]
+        desc.u0 = self._u0.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        desc.radius = self._rad.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        desc.priors[:] = [float(v) for v in scene.priors]
+        desc.exp_nu[:] = [float(v) for v in scene.exp_nu]
+        desc.exp_tau[:] = [float(v) for v in scene.exp_tau]
+        desc.dev_nu[:] = [float(v) for v in scene.dev_nu]
+        desc.dev_tau[:] = [float(v) for v in scene.dev_tau]
+        desc.tile_pixels = int(tile_pixels)
+        h = ctypes.c_void_p()
+        _check(L.celeste_problem_create(ctypes.byref(desc), ctypes.byref(h)))
+        self.handle = h
+        self.S = desc.n_sources
+        nbytes = L.celeste_problem_workspace_bytes(h)
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        off = (-self.workspace.data_ptr()) % 256
+        self._ws_ptr = ctypes.c_void_p(self.workspace.data_ptr() + off)
+        self._ws_bytes = nbytes
+        _check(L.celeste_problem_bind(h, self._ws_ptr, ctypes.c_size_t(nbytes), _stream(stream)))
+
+    def counts(self):
+        c = (ctypes.c_int64 * 5)()
+        _check(lib().celeste_problem_counts(self.handle, c))
+        return dict(sources=c[0], patches=c[1], tiles=c[2], pixels=c[3], neighbours=c[4])
+
+    def render_background(self, nbr_theta, stream=None):
+        assert nbr_theta.dtype == torch.float64 and nbr_theta.is_contiguous() and nbr_theta.shape == (self.S, NPARAM)
+        _check(lib().celeste_render_background(self.handle, _ptr(nbr_theta), _stream(stream)))
+
+    def elbo_batch(self, theta, want=WANT_ELBO | WANT_GRAD | WANT_HESS, stream=None):
+        assert theta.dtype == torch.float64 and theta.is_contiguous() and theta.shape == (self.S, NPARAM)
+        dev = theta.device
+        elbo = torch.empty(self.S, dtype=torch.float64, device=dev) if want & WANT_ELBO else None
+        grad = torch.empty(self.S, NPARAM, dtype=torch.float64, device=dev) if want & WANT_GRAD else None
+        hess = torch.empty(self.S, NPARAM, NPARAM, dtype=torch.float64, device=dev) if want & WANT_HESS else None
+        _check(lib().celeste_elbo_batch(self.handle, _ptr(theta), ctypes.c_uint32(want), _ptr(elbo), _ptr(grad),
+                                        _ptr(hess), _stream(stream)))
+        return elbo, grad, hess
+
+    def newton_batch(self, theta, delta=None, max_iter=50, ftol=1e-8, gtol=1e-10, delta0=1.0, delta_max=1e4,
+                     eta=0.1, delta_min=1e-12, stream=None):
+        """Runs trust-region Newton in place on `theta`; returns (delta, iters, status, elbo)."""
+        assert theta.dtype == torch.float64 and theta.is_contiguous() and theta.shape == (self.S, NPARAM)
+        dev = theta.device
+        if delta is None:
+            delta = torch.zeros(self.S, dtype=torch.float64, device=dev)
+        iters = torch.zeros(self.S, dtype=torch.int32, device=dev)
+        status = torch.zeros(self.S, dtype=torch.int32, device=dev)
+        elbo = torch.empty(self.S, dtype=torch.float64, device=dev)
+        opts = NewtonOpts(max_iter, ftol, gtol, delta0, delta_max, eta, delta_min)
+        _check(lib().celeste_newton_batch(self.handle, _ptr(theta), ctypes.byref(opts), _ptr(delta), _ptr(iters),
+                                          _ptr(status), _ptr(elbo), _stream(stream)))
+        return delta, iters, status, elbo
+
+    def rebind(self, stream=None):
+        """Upload the layout again and re-gather the patch pixels from the device images."""
+        _check(lib().celeste_problem_bind(self.handle, self._ws_ptr, ctypes.c_size_t(self._ws_bytes), _stream(stream)))
+
+    def profile_start(self):
+        _check(lib().celeste_profile_start(self.handle))
+
+    def profile_stop(self):
+        st = ProfileStats()
+        _check(lib().celeste_profile_stop(self.handle, ctypes.byref(st)))
+        return {k: getattr(st, k) for k, _ in ProfileStats._fields_}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().celeste_problem_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class HostProblem:
+    """Layout-only handle (no device memory): validation and counts, usable without a GPU."""
+
+    def __init__(self, scene, tile_pixels=256):
+        L = lib()
+        n = len(scene.images)
+        self._imgs = (ImageDesc * n)()
+        for k, im in enumerate(scene.images):
+            d = self._imgs[k]
+            d.height, d.width = im.pixels.shape
+            d.band = int(im.band)
+            d.pixels = 1          # never dereferenced on the host
+            d.sky, d.iota = float(im.sky), float(im.iota)
+            d.wcs[:] = [float(v) for v in im.wcs]
+            d.psf[:] = [float(v) for v in np.asarray(im.psf, np.float64).reshape(-1)]
+        self._u0 = np.ascontiguousarray(scene.u0, np.float64)
+        self._rad = np.ascontiguousarray(scene.radius, np.int32)
+        desc = ProblemDesc()
+        desc.n_images = n
+        desc.images = self._imgs
+        desc.n_sources = self._u0.shape[0]
+        desc.u0 = self._u0.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        desc.radius = self._rad.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        desc.priors[:] = [float(v) for v in scene.priors]
+        desc.exp_nu[:] = [float(v) for v in scene.exp_nu]
+        desc.exp_tau[:] = [float(v) for v in scene.exp_tau]
+        desc.dev_nu[:] = [float(v) for v in scene.dev_nu]
+        desc.dev_tau[:] = [float(v) for v in scene.dev_tau]
+        desc.tile_pixels = int(tile_pixels)
+        self.desc = desc
+        h = ctypes.c_void_p()
+        _check(L.celeste_problem_create(ctypes.byref(desc), ctypes.byref(h)))
+        self.handle = h
+
+    def counts(self):
+        c = (ctypes.c_int64 * 5)()
+        _check(lib().celeste_problem_counts(self.handle, c))
+        return dict(sources=c[0], patches=c[1], tiles=c[2], pixels=c[3], neighbours=c[4])
+
+    def workspace_bytes(self):
+        return lib().celeste_problem_workspace_bytes(self.handle)
+
+    def __del__(self):
+        try:
+            lib().celeste_problem_destroy(self.handle)
+        except Exception:
+            pass

@@ -1,0 +1,304 @@
+// Internal device-side layout and helpers of the Celeste GB300 library.
+//
+// Model (paper, Sec. "The Celeste Model" and "Variational Inference"): the pixel rate of
+// image n is F = sky + iota * sum_s G_s with G_s = l_b(s) * f_type(s)(pixel); the ELBO uses
+// E[F], Var[F] under q and the delta method for E[log F].  Everything in this header is
+// layout or small arithmetic used by several kernels of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "celeste.h"
+
+namespace celeste {
+
+constexpr int NP = CELESTE_NPARAM;       // 27 free parameters per source
+constexpr int NSTAR = CELESTE_NPSF;      // star components (one per PSF component)
+constexpr int NMIX = CELESTE_NEXP + CELESTE_NDEV;   // 14 profile components per PSF component
+constexpr int NGAL = CELESTE_NPSF * NMIX;           // 42 galaxy components
+constexpr int NCOMP = NSTAR + NGAL;                 // 45
+constexpr int BLOCK = 128;               // threads per CTA of the pixel kernels
+
+// Per-tile partial sums written by the ELBO+gradient+Hessian pixel kernel (float32 within a tile,
+// summed across tiles in float64).  Reduced basis (11): mu0, mu1, dev, axis, angle, scale, alpha,
+// f0 (E-row, star brightness), f1 (E-row, galaxy brightness), f0^2 (V-row), f1^2 (V-row).
+constexpr int ACC_L = 0;                 // sum of pixel ELBO terms
+constexpr int ACC_S1 = 1;                // 10: sum w1 * [f0, d_mu f0 (2), f1, d f1 (6: mu0 mu1 dev axis angle scale)]
+constexpr int ACC_S2 = 11;               // 10: sum w2 * [f0^2, d_mu f0^2 (2), f1^2, d f1^2 (6)]
+constexpr int ACC_HP = 21;               // 21: packed upper triangle over (mu0 mu1 dev axis angle scale)
+constexpr int ACC_M = 42;                // 66: packed upper triangle of the 11x11 Jacobian cross-product
+constexpr int NACC = 108;
+constexpr int NRED = 11;
+
+// Galaxy component table (floats), one per (PSF component k, profile component j).
+// Means are relative to the patch origin; quadratic forms use s = (d0^2, 2 d0 d1, d1^2).
+constexpr int GT_MU = 0;     // 2
+constexpr int GT_LW2 = 2;    // log2 of weight * normaliser (weight excludes the fracDev mixing)
+constexpr int GT_P = 3;      // 3: precision matrix (00, 01, 11)
+constexpr int GT_QA = 6;     // 3 x 3: -1/2 dP/da, a = axis, angle, scale
+constexpr int GT_LA = 15;    // 3: -1/2 d logdet / da
+constexpr int GT_QAB = 18;   // 6 x 3: -1/2 d2P/dadb, pairs (00 01 02 11 12 22)
+constexpr int GT_LAB = 36;   // 6: -1/2 d2 logdet / dadb
+constexpr int GT_STRIDE = 44;
+constexpr int ST_STRIDE = 8; // star: mu (2), lw2, P (3), pad
+
+// Per-(source, image) scalar constants used by the pixel kernels.
+struct SNConst {
+  float A0, A1, B0, B1;          // a_i E[l_b|i], a_i E[l_b^2|i]
+  float aE0, aE1, aV0, aV1;      // a0 a1 E[l_b|i], a0 a1 E[l_b^2|i]
+  float iota, e, e1, e2;         // calibration, sigma(dev), its first and second derivative
+  // Var[G] = C0 f0^2 + C1 f1^2 + Cx (L10 f0 - L11 f1)^2 without cancellation:
+  // C_i = a_i (E[l^2|i] - E[l|i]^2) = a_i E[l|i]^2 expm1(v_i), Cx = a0 a1.
+  float C0, C1, Cx, L10, L11;
+};
+
+struct ImageDev {
+  const float* pixels;
+  int H, W, band, pad;
+  float sky, iota;
+  double A[4], o[2];
+};
+
+struct PatchDev {
+  int source, image, x0, y0, w, h;
+  long long pix_off;             // first float4 of this patch in the pixel buffer
+  int tile_begin, tile_end, nbr_begin, nbr_end;
+};
+
+struct TileDev {
+  int patch, start, count, pad;
+};
+
+// Device view of a bound problem (passed by value to kernels).
+struct ProblemDev {
+  const ImageDev* images;
+  const PatchDev* patches;
+  const TileDev* tiles;
+  const int* src_patch;          // [S+1] CSR of each source's patches
+  const int* nbr;                // neighbour patch ids (same image)
+  const double* u0;              // [S][2]
+  const double* psf_coef;        // [n_images][3][6][6]
+  float* psf;                    // [n_patches][18]: per PSF comp (w, mx, my, s00, s01, s11)
+  float4* pix;                   // [n_pix]: (x, fixed rate, fixed variance, log-factorial term)
+  float* partials;               // [n_tiles][NACC]
+  float* vpartials;              // [n_tiles]
+  int* flags;                    // [S] per-source work flags
+  int* err;                      // [4] device error words
+  unsigned long long* counters;  // [4]: full-kernel pixels, value-kernel pixels
+  int S, n_patches, n_tiles, tile_pixels;
+  double priors[5];
+  float nu[NMIX], tau[NMIX];     // exp (0..5) then deV (6..13)
+};
+
+// Work flags per source.
+constexpr int FLAG_FULL = 1;     // evaluate value + gradient + Hessian
+constexpr int FLAG_VALUE = 2;    // evaluate value only (trial point)
+
+// Error words.
+constexpr int ERR_BAD_PIXEL = 0;
+constexpr int ERR_TIMEOUT = 1;
+
+// -------------------------------------------------------------------------------- small math
+__host__ __device__ inline double sigmoid_d(double x) {
+  return x >= 0 ? 1.0 / (1.0 + exp(-x)) : exp(x) / (1.0 + exp(x));
+}
+
+// Symmetric 2x2 stored as (00, 01, 11).
+struct Sym2 {
+  float a, b, c;
+};
+struct Mat2 {
+  float m00, m01, m10, m11;
+};
+
+__device__ inline Mat2 mul(const Sym2& x, const Sym2& y) {
+  return {x.a * y.a + x.b * y.b, x.a * y.b + x.b * y.c, x.b * y.a + x.c * y.b, x.b * y.b + x.c * y.c};
+}
+__device__ inline Mat2 mul(const Mat2& x, const Sym2& y) {
+  return {x.m00 * y.a + x.m01 * y.b, x.m00 * y.b + x.m01 * y.c, x.m10 * y.a + x.m11 * y.b, x.m10 * y.b + x.m11 * y.c};
+}
+__device__ inline Mat2 mul(const Mat2& x, const Mat2& y) {
+  return {x.m00 * y.m00 + x.m01 * y.m10, x.m00 * y.m01 + x.m01 * y.m11, x.m10 * y.m00 + x.m11 * y.m10,
+          x.m10 * y.m01 + x.m11 * y.m11};
+}
+__device__ inline float trace(const Mat2& x) { return x.m00 + x.m11; }
+// symmetric part of x + x^T stored as Sym2
+__device__ inline Sym2 sym_plus_t(const Mat2& x) { return {2.f * x.m00, x.m01 + x.m10, 2.f * x.m11}; }
+__device__ inline Sym2 to_sym(const Mat2& x) { return {x.m00, 0.5f * (x.m01 + x.m10), x.m11}; }
+// A S A^T for a general 2x2 A (row-major a00 a01 a10 a11)
+__device__ inline Sym2 congruence(const float A[4], const Sym2& S) {
+  float t00 = A[0] * S.a + A[1] * S.b, t01 = A[0] * S.b + A[1] * S.c;
+  float t10 = A[2] * S.a + A[3] * S.b, t11 = A[2] * S.b + A[3] * S.c;
+  return {t00 * A[0] + t01 * A[1], t10 * A[0] + t11 * A[1], t10 * A[2] + t11 * A[3]};
+}
+
+// PSF component c of a patch: weight, mean (pixels), covariance.
+struct PsfComp {
+  float w, mx, my;
+  Sym2 S;
+};
+__device__ inline PsfComp load_psf(const float* psf_patch, int k) {
+  const float* q = psf_patch + 6 * k;
+  return {q[0], q[1], q[2], {q[3], q[4], q[5]}};
+}
+
+// Brightness moments of a lognormal flux in band b for type i: log l_b ~ N(m, v),
+// m = r1 + a_b.c1, v = exp(rho) + (a_b^2).exp(gam); E[l] = exp(m + v/2), E[l^2] = exp(2m + 2v).
+__host__ __device__ inline void color_row(int band, double a[4]) {
+  const double M[5][4] = {{-1, -1, 0, 0}, {0, -1, 0, 0}, {0, 0, 0, 0}, {0, 0, 1, 0}, {0, 0, 1, 1}};
+  for (int j = 0; j < 4; ++j) a[j] = M[band][j];
+}
+__host__ __device__ inline void lognormal_moments(const double* th, int type, int band, double& L1, double& L2,
+                                                  double* var_log = nullptr) {
+  const int r1 = type ? 9 : 7, rho = type ? 10 : 8, c1 = type ? 19 : 11, gam = type ? 23 : 15;
+  double a[4];
+  color_row(band, a);
+  double m = th[r1], v = exp(th[rho]);
+  for (int j = 0; j < 4; ++j) {
+    m += a[j] * th[c1 + j];
+    v += a[j] * a[j] * exp(th[gam + j]);
+  }
+  L1 = exp(m + 0.5 * v);
+  L2 = exp(2.0 * m + 2.0 * v);
+  if (var_log) *var_log = v;
+}
+
+__device__ inline void sn_constants(const double* th, int band, float iota, SNConst& c) {
+  double a1 = sigmoid_d(th[6]), a0 = sigmoid_d(-th[6]);
+  double L10, L20, L11, L21, v0, v1;
+  lognormal_moments(th, 0, band, L10, L20, &v0);
+  lognormal_moments(th, 1, band, L11, L21, &v1);
+  c.C0 = (float)(a0 * L10 * L10 * expm1(v0));
+  c.C1 = (float)(a1 * L11 * L11 * expm1(v1));
+  c.Cx = (float)(a0 * a1);
+  c.L10 = (float)L10;
+  c.L11 = (float)L11;
+  c.A0 = (float)(a0 * L10);
+  c.A1 = (float)(a1 * L11);
+  c.B0 = (float)(a0 * L20);
+  c.B1 = (float)(a1 * L21);
+  double aa = a0 * a1;
+  c.aE0 = (float)(aa * L10);
+  c.aE1 = (float)(aa * L11);
+  c.aV0 = (float)(aa * L20);
+  c.aV1 = (float)(aa * L21);
+  c.iota = iota;
+  double e = sigmoid_d(th[2]), ee = e * sigmoid_d(-th[2]);
+  c.e = (float)e;
+  c.e1 = (float)ee;
+  c.e2 = (float)(ee * (1.0 - 2.0 * e));
+}
+
+// Galaxy world covariance Sigma_g = scale^2 R diag(1, axis^2) R^T and its first/second
+// derivatives w.r.t. (logit axis, angle, log scale); pairs ordered 00 01 02 11 12 22.
+struct GalShape {
+  Sym2 S, d[3], d2[6];
+};
+__device__ inline void galaxy_shape(double eta, double phi, double kappa, GalShape& g) {
+  float e = (float)sigmoid_d(eta), e2 = e * e;
+  float s2 = (float)exp(2.0 * kappa);
+  float c = (float)cos(phi), sn = (float)sin(phi);
+  Sym2 A = {c * c, c * sn, sn * sn};
+  Sym2 B = {sn * sn, -c * sn, c * c};
+  Sym2 dA = {-2.f * c * sn, c * c - sn * sn, 2.f * c * sn};
+  Sym2 d2A = {-2.f * (c * c - sn * sn), -4.f * c * sn, 2.f * (c * c - sn * sn)};
+  float de2 = 2.f * e2 * (1.f - e);
+  float d2e2 = 2.f * e2 * (1.f - e) * (2.f - 3.f * e);
+  g.S = {s2 * (A.a + e2 * B.a), s2 * (A.b + e2 * B.b), s2 * (A.c + e2 * B.c)};
+  g.d[0] = {s2 * de2 * B.a, s2 * de2 * B.b, s2 * de2 * B.c};
+  float k1 = s2 * (1.f - e2);
+  g.d[1] = {k1 * dA.a, k1 * dA.b, k1 * dA.c};
+  g.d[2] = {2.f * g.S.a, 2.f * g.S.b, 2.f * g.S.c};
+  g.d2[0] = {s2 * d2e2 * B.a, s2 * d2e2 * B.b, s2 * d2e2 * B.c};
+  g.d2[1] = {-s2 * de2 * dA.a, -s2 * de2 * dA.b, -s2 * de2 * dA.c};
+  g.d2[2] = {2.f * g.d[0].a, 2.f * g.d[0].b, 2.f * g.d[0].c};
+  g.d2[3] = {k1 * d2A.a, k1 * d2A.b, k1 * d2A.c};
+  g.d2[4] = {2.f * g.d[1].a, 2.f * g.d[1].b, 2.f * g.d[1].c};
+  g.d2[5] = {4.f * g.S.a, 4.f * g.S.b, 4.f * g.S.c};
+}
+
+__device__ inline Sym2 inv2(const Sym2& S, float& logdet) {
+  float det = S.a * S.c - S.b * S.b;
+  logdet = logf(det);
+  float r = 1.f / det;
+  return {S.c * r, -S.b * r, S.a * r};
+}
+
+constexpr float LOG2E = 1.4426950408889634f;
+constexpr float LOG_2PI = 1.8378770664093453f;
+
+// Position of the source in image pixels relative to (ox, oy), in float64.
+__device__ inline void source_pixel_pos(const ImageDev& im, const double* th, double ox, double oy, double& px, double& py) {
+  px = im.A[0] * th[0] + im.A[1] * th[1] + im.o[0] - ox;
+  py = im.A[2] * th[0] + im.A[3] * th[1] + im.o[1] - oy;
+}
+
+// Value-only table entry (mu, lw2, P) of star component k and galaxy component (k, j) for a source
+// at relative pixel position (px, py).  Used for neighbours and for trial points.
+__device__ inline void star_value_entry(const PsfComp& pc, double px, double py, float* out) {
+  float ld;
+  Sym2 P = inv2(pc.S, ld);
+  out[0] = (float)(px + pc.mx);
+  out[1] = (float)(py + pc.my);
+  out[2] = (logf(pc.w) - 0.5f * ld - LOG_2PI) * LOG2E;
+  out[3] = P.a;
+  out[4] = P.b;
+  out[5] = P.c;
+}
+__device__ inline void gal_value_entry(const PsfComp& pc, const Sym2& Spix, float nu, float tau, double px, double py,
+                                       float* out) {
+  Sym2 S = {tau * Spix.a + pc.S.a, tau * Spix.b + pc.S.b, tau * Spix.c + pc.S.c};
+  float ld;
+  Sym2 P = inv2(S, ld);
+  out[0] = (float)(px + pc.mx);
+  out[1] = (float)(py + pc.my);
+  out[2] = (logf(pc.w * nu) - 0.5f * ld - LOG_2PI) * LOG2E;
+  out[3] = P.a;
+  out[4] = P.b;
+  out[5] = P.c;
+}
+
+__device__ inline float gauss_value(const float* t, float dx, float dy) {
+  float d0 = dx - t[0], d1 = dy - t[1];
+  float q = t[3] * d0 * d0 + 2.f * t[4] * d0 * d1 + t[5] * d1 * d1;
+  return exp2f(fmaf(q, -0.5f * LOG2E, t[2]));
+}
+
+// Bounded wait on an mbarrier phase (returns false if the budget ran out).
+__device__ inline bool mbar_wait(uint64_t* bar, uint32_t phase, long long budget_cycles) {
+  uint32_t addr = (uint32_t)__cvta_generic_to_shared(bar);
+  long long t0 = clock64();
+  while (true) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(addr), "r"(phase)
+        : "memory");
+    if (ok) return true;
+    if (clock64() - t0 > budget_cycles) return false;
+  }
+}
+
+__device__ inline void mbar_init(uint64_t* bar, uint32_t count) {
+  uint32_t addr = (uint32_t)__cvta_generic_to_shared(bar);
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(addr), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// One-dimensional bulk copy global -> shared through the TMA unit, completing on `bar`.
+// dst/src 16-byte aligned, bytes a multiple of 16.
+__device__ inline void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  uint32_t b = (uint32_t)__cvta_generic_to_shared(bar);
+  uint64_t state;
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;" : "=l"(state) : "r"(b), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(d),
+               "l"(src), "r"(bytes), "r"(b)
+               : "memory");
+}
+
+}  // namespace celeste

@@ -1,0 +1,59 @@
+// Host-side problem object shared by the library's translation units.
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "celeste_internal.cuh"
+
+namespace celeste {
+
+struct WsLayout {
+  size_t images, patches, tiles, src_patch, nbr, u0, psf_coef, psf, pix, partials, vpartials, flags, err, counters;
+  size_t nt_f, nt_g, nt_H, nt_trial, nt_pred, nt_ftrial, nt_state, nt_count;
+  size_t total;
+};
+
+int fail(int code, const char* fmt, ...);
+int cuda_fail(cudaError_t e, const char* what);
+
+}  // namespace celeste
+
+struct celeste_problem {
+  int S = 0;
+  int tile_pixels = 256;
+  std::vector<celeste_image_desc> images;
+  std::vector<double> u0;
+  std::vector<int> radius;
+  double priors[5];
+  float nu[celeste::NMIX], tau[celeste::NMIX];
+  // layout
+  std::vector<celeste::PatchDev> patches;
+  std::vector<celeste::TileDev> tiles;
+  std::vector<int> src_patch, nbr;
+  std::vector<celeste::ImageDev> imgdev;
+  std::vector<double> psf_coef;
+  long long n_pix = 0;
+  celeste::WsLayout ws{};
+  // binding
+  char* base = nullptr;
+  celeste::ProblemDev dev{};
+  bool bound = false;
+  bool background_ready = false;
+  // profiling (celeste_profile_start/stop)
+  bool prof_on = false;
+  std::vector<cudaEvent_t> prof_events;
+  size_t prof_used = 0;
+  std::vector<std::pair<int, int>> prof_full, prof_value;
+  long long prof_launches = 0, prof_iters = 0;
+  ~celeste_problem();
+};
+
+namespace celeste {
+void build_layout(celeste_problem* p);
+// Records an event on st when profiling; returns its index or -1.
+int prof_mark(celeste_problem* p, cudaStream_t st);
+inline void prof_count(celeste_problem* p, int launches) {
+  if (p->prof_on) p->prof_launches += launches;
+}
+}

@@ -1,0 +1,113 @@
+"""C ABI checks that need no GPU: the library loads, exports every declared entry point, validates
+descriptors, and lays out patches / neighbours / tiles exactly as the oracle defines them."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import celeste_oracle as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1611_03404_gb300 as P
+    return P
+
+
+def _declared_symbols():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            names |= set(re.findall(r"\b(celeste_[a-z_]+)\s*\(", txt))
+    return names
+
+
+def test_exports_every_declared_symbol(pkg):
+    lib = pkg.lib()
+    declared = _declared_symbols()
+    assert len(declared) >= 10
+    for name in declared:
+        assert hasattr(lib, name), name
+
+
+def test_strerror_codes(pkg):
+    lib = pkg.lib()
+    assert lib.celeste_strerror(0) == b"ok"
+    assert lib.celeste_strerror(1) == b"invalid argument"
+    assert lib.celeste_strerror(999) == b"unknown error"
+
+
+def _layout_reference(scene, tile):
+    rects = O.patch_rects(scene)
+    nbr = O.neighbour_lists(scene, rects)
+    patches = sum(len(r) for r in rects)
+    pixels = sum((x1 - x0 + 1) * (y1 - y0 + 1) for r in rects for (_, x0, x1, y0, y1) in r)
+    tiles = sum(-(-((x1 - x0 + 1) * (y1 - y0 + 1)) // tile) for r in rects for (_, x0, x1, y0, y1) in r)
+    nb = sum(len(v) for d in nbr for v in d.values())
+    return dict(sources=scene.n_sources, patches=patches, tiles=tiles, pixels=pixels, neighbours=nb)
+
+
+@pytest.mark.parametrize("seed", [3, 4, 5])
+@pytest.mark.parametrize("tile", [128, 256, 1024])
+def test_layout_matches_oracle_geometry(pkg, seed, tile):
+    sc = synth.tiny(seed=seed, n_sources=6, n_images=3, H=40, W=44, radius=(3, 12))
+    hp = pkg.HostProblem(sc, tile_pixels=tile)
+    assert hp.counts() == _layout_reference(sc, tile)
+    assert hp.workspace_bytes() > 0
+
+
+def test_layout_edge_sources(pkg):
+    """Sources at the image corners and outside some images: clipped or absent patches."""
+    sc = synth.tiny(seed=9, n_sources=4, n_images=2, H=30, W=30, radius=(5, 5))
+    sc.u0 = np.array([[0.2, 0.1], [29.4, 29.3], [-3.0, 15.0], [15.0, 15.0]])
+    hp = pkg.HostProblem(sc)
+    assert hp.counts() == _layout_reference(sc, 256)
+
+
+def _expect_invalid(pkg, sc, **kw):
+    with pytest.raises(pkg.CelesteError, match="invalid argument"):
+        pkg.HostProblem(sc, **kw)
+
+
+def test_validation_rejects_bad_descriptors(pkg):
+    base = lambda: synth.tiny(seed=1, n_sources=2, n_images=2)
+    sc = base()
+    sc.images[0].sky = float("nan")
+    _expect_invalid(pkg, sc)
+    sc = base()
+    sc.images[1].iota = -1.0
+    _expect_invalid(pkg, sc)
+    sc = base()
+    sc.radius = np.array([0, 5], np.int32)
+    _expect_invalid(pkg, sc)
+    sc = base()
+    sc.radius = np.array([65, 5], np.int32)
+    _expect_invalid(pkg, sc)
+    sc = base()
+    sc.u0 = sc.u0.copy()
+    sc.u0[0, 0] = np.inf
+    _expect_invalid(pkg, sc)
+    sc = base()
+    sc.exp_nu = sc.exp_nu * 1.1
+    _expect_invalid(pkg, sc)
+    sc = base()
+    sc.images[0].wcs = np.array([1.0, 0.0, 2.0, 0.0, 0.0, 0.0])
+    _expect_invalid(pkg, sc)
+    sc = base()
+    sc.images[0].psf = sc.images[0].psf.copy()
+    sc.images[0].psf[0, 3, 0] = 9.0
+    _expect_invalid(pkg, sc)
+    sc = base()
+    sc.images[0].band = 7
+    _expect_invalid(pkg, sc)
+    sc = base()
+    sc.priors = np.array([1.5, 2.0, 1.0, 0.0, 0.25])
+    _expect_invalid(pkg, sc)
+    _expect_invalid(pkg, base(), tile_pixels=100)

@@ -1,0 +1,167 @@
+"""CUDA path vs the float64 oracle, element by element, through the C ABI.
+
+Tolerances (the plain float32 GPU path against the float64 oracle):
+  ELBO      |dL|   <= 1e-6 |L|
+  gradient  |dg_i| <= 1e-4 max(|g_i|, 1e-3 max_j |g_j|)
+  Hessian   |dH_ij| <= 1e-4 max(|H_ij|, 1e-2 sqrt(|H_ii H_jj|))
+The floors make "relative" meaningful for entries that are near zero by cancellation.  A Hessian
+entry is a sum of per-pixel float32 terms whose magnitudes are bounded by its natural scale
+sqrt(|H_ii H_jj|); float32 rounding leaves an absolute error of a few ulps (~1e-7) of that scale, so
+an entry far below it is checked to 1e-6 of the natural scale rather than to 1e-4 of itself.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import celeste_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+ELBO_RTOL, GRAD_RTOL, HESS_RTOL = 1e-6, 1e-4, 1e-4
+GRAD_FLOOR, HESS_FLOOR = 1e-3, 1e-2
+
+
+@pytest.fixture(scope="module")
+def P():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1611_03404_gb300 as pkg
+    return pkg
+
+
+def check_elbo(e, L, what=""):
+    assert abs(e - L) <= ELBO_RTOL * abs(L), f"{what} elbo {e} vs {L}: rel {abs(e - L) / abs(L):.3e}"
+
+
+def check_grad(gg, g, what=""):
+    scale = np.maximum(np.abs(g), GRAD_FLOOR * np.abs(g).max())
+    r = np.abs(gg - g) / scale
+    assert np.all(r <= GRAD_RTOL), f"{what} grad worst {r.max():.3e} at {int(r.argmax())}: {gg[r.argmax()]} vs {g[r.argmax()]}"
+
+
+def check_hess(hh, H, what=""):
+    d = np.sqrt(np.abs(np.outer(np.diag(H), np.diag(H))))
+    scale = np.maximum(np.abs(H), HESS_FLOOR * d)
+    r = np.abs(hh - H) / np.where(scale > 0, scale, 1.0)
+    i, j = np.unravel_index(r.argmax(), r.shape)
+    assert np.all(r <= HESS_RTOL), (f"{what} hess worst {r.max():.3e} at ({i},{j}): {hh[i, j]} vs {H[i, j]}, "
+                                    f"natural scale {d[i, j]:.4g}")
+
+
+def run_gpu(P, scene, theta, nbr_theta=None, tile=256):
+    dev = torch.device("cuda:0")
+    prob = P.Problem(scene, device=dev, tile_pixels=tile)
+    th = torch.as_tensor(theta, device=dev).contiguous()
+    nb = torch.as_tensor(theta if nbr_theta is None else nbr_theta, device=dev).contiguous()
+    prob.render_background(nb)
+    elbo, grad, hess = prob.elbo_batch(th)
+    v, _, _ = prob.elbo_batch(th, want=P.WANT_ELBO)
+    torch.cuda.synchronize()
+    return elbo.cpu().numpy(), grad.cpu().numpy(), hess.cpu().numpy(), v.cpu().numpy()
+
+
+def compare_all(P, scene, theta, sources=None, nbr_theta=None, tile=256, what=""):
+    e, g, h, v = run_gpu(P, scene, theta, nbr_theta, tile)
+    orc = O.Oracle(scene)
+    nb = theta if nbr_theta is None else nbr_theta
+    for s in (range(scene.n_sources) if sources is None else sources):
+        if not orc.rects[s]:
+            assert e[s] == pytest.approx(-float(O.kl_source(torch.as_tensor(theta[s]), scene.priors)), rel=1e-12)
+            continue
+        L, gL, HL = orc.elbo_grad_hess(s, theta[s], nb)
+        check_elbo(e[s], L, f"{what} s={s}")
+        check_elbo(v[s], L, f"{what} value-only s={s}")
+        check_grad(g[s], gL, f"{what} s={s}")
+        check_hess(h[s], HL, f"{what} s={s}")
+
+
+def _spread(theta, rng):
+    """Move a start point to a generic interior point where every term of the objective is active."""
+    th = theta.copy()
+    th[:, 6] = rng.uniform(-1, 1, len(th))
+    th[:, 8] = th[:, 10] = np.log(rng.uniform(0.02, 0.2, len(th)))
+    th[:, 15:19] = np.log(rng.uniform(0.01, 0.1, (len(th), 4)))
+    th[:, 23:27] = np.log(rng.uniform(0.01, 0.1, (len(th), 4)))
+    return th
+
+
+def test_single_source_41px_at_start(P):
+    """One isolated source, 5 bands x 41x41 px, at its catalog start point."""
+    sc = synth.single_source(seed=1611, size=41)
+    compare_all(P, sc, sc.theta0, what="single41")
+
+
+@pytest.mark.parametrize("seed,is_gal", [(5, True), (6, False), (7, None)])
+def test_single_source_interior_points(P, seed, is_gal):
+    sc = synth.single_source(seed=seed, size=31, is_gal=is_gal)
+    th = _spread(sc.theta0, np.random.default_rng(seed))
+    compare_all(P, sc, th, what=f"single31 seed={seed}")
+
+
+@pytest.mark.parametrize("seed", [11, 12])
+def test_overlapping_sources_rotated_wcs(P, seed):
+    """Neighbours in the same patches, rotated and scaled pixel maps, several bands."""
+    sc = synth.tiny(seed=seed, n_sources=4, n_images=3, H=34, W=38, radius=(6, 12))
+    th = _spread(sc.theta0, np.random.default_rng(seed))
+    nb = th.copy()
+    nb[:, 0:2] += 0.2     # neighbours fixed somewhere other than the targets
+    compare_all(P, sc, th, nbr_theta=nb, what=f"tiny seed={seed}")
+
+
+@pytest.mark.parametrize("tile", [128, 512, 1024])
+def test_tile_sizes_and_ragged_tails(P, tile):
+    sc = synth.tiny(seed=13, n_sources=3, n_images=2, H=40, W=44, radius=(9, 17))
+    th = _spread(sc.theta0, np.random.default_rng(2))
+    compare_all(P, sc, th, tile=tile, what=f"tile={tile}")
+
+
+def test_edge_patches_clipped_and_maximal(P):
+    """A source in an image corner (clipped patch), one outside an image, and an R=64 patch."""
+    sc = synth.tiny(seed=17, n_sources=3, n_images=2, H=140, W=150, radius=(6, 6))
+    sc.u0 = np.array([[1.2, 0.7], [75.0, 70.0], [148.6, 60.0]])
+    sc.theta0[:, 0:2] = sc.u0 + 0.1
+    sc.radius = np.array([6, 64, 9], np.int32)
+    th = _spread(sc.theta0, np.random.default_rng(3))
+    compare_all(P, sc, th, what="edges")
+
+
+def test_newton_matches_oracle_optimum(P):
+    """Batched GPU Newton reaches the oracle's optimum within 1e-4 per identified parameter."""
+    sc = synth.single_source(seed=1611, size=41)
+    dev = torch.device("cuda:0")
+    prob = P.Problem(sc, device=dev)
+    th = torch.as_tensor(sc.theta0, device=dev).contiguous()
+    prob.render_background(th.clone())
+    delta, iters, status, elbo = prob.newton_batch(th)
+    torch.cuda.synchronize()
+    ref = O.Oracle(sc).newton(0, sc.theta0[0], sc.theta0)
+    assert int(status[0]) == P.STATUS_CONVERGED and int(iters[0]) <= 50
+    got = th.cpu().numpy()[0]
+    assert abs(float(elbo[0]) - ref["elbo"]) <= 1e-6 * abs(ref["elbo"])
+    compare_optimum(got, ref["theta"])
+
+
+def compare_optimum(got, ref, tol=1e-4):
+    """Per-parameter comparison in the constrained space; a type's own parameters only count when
+    that type has posterior probability > 1e-3, and the angle (mod pi) only when the axis ratio
+    is below 1 - 1e-3 (otherwise they are unidentified)."""
+    sig = lambda x: 1 / (1 + math.exp(-x))
+    a_gal = sig(ref[6])
+    assert abs(sig(got[6]) - a_gal) <= tol
+    assert np.abs(got[0:2] - ref[0:2]).max() <= tol
+    if a_gal > 1e-3:
+        assert abs(sig(got[2]) - sig(ref[2])) <= tol
+        assert abs(sig(got[3]) - sig(ref[3])) <= tol
+        assert abs(math.exp(got[5]) - math.exp(ref[5])) <= tol * math.exp(ref[5])
+        if sig(ref[3]) < 1 - 1e-3:
+            assert abs(math.remainder(got[4] - ref[4], math.pi)) <= tol
+        idx = [9, 10] + list(range(19, 27))
+        assert np.all(np.abs(got[idx] - ref[idx]) <= tol * np.maximum(1, np.abs(ref[idx])))
+    if a_gal < 1 - 1e-3:
+        idx = [7, 8] + list(range(11, 19))
+        assert np.all(np.abs(got[idx] - ref[idx]) <= tol * np.maximum(1, np.abs(ref[idx])))
