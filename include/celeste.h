@@ -181,6 +181,23 @@ typedef struct {
 int celeste_profile_start(celeste_problem* p);
 int celeste_profile_stop(celeste_problem* p, celeste_profile_stats* out);
 
+/* The same evaluation as celeste_elbo_batch with want = ELBO | GRAD | HESS, for callers that may
+ * not allocate device memory when they evaluate (a pre-sized arena, an allocator owned by another
+ * framework, a request path that must not allocate).  The call allocates nothing: the kernels'
+ * scratch (per-tile partial sums, per-source flags, counters) lives in one fixed 8 MiB device array
+ * inside this library, which every GPU that loads the library keeps until the process exits.
+ * The paper has no counterpart; it is a deployment variant of the evaluation above.
+ *   p must be bound and have its background rendered; theta, elbo, grad, hess as in
+ *   celeste_elbo_batch (all four required).
+ *   Limit: 432 * n_tiles + 4 * n_sources bytes (each rounded up to 256) plus 256 must fit in
+ *   8 MiB, about 19,000 tiles; larger problems get CELESTE_ERR_INVALID_ARG before any launch.
+ *   The first call on a device looks up the array's device address with that device current;
+ *   make that first call before any stream capture.
+ *   Every call shares the one array: calls that overlap on the GPU (different streams, threads
+ *   or problems without ordering between them) race and corrupt each other's results. */
+int celeste_elbo_batch_noalloc(celeste_problem* p, const double* theta, double* elbo, double* grad,
+                               double* hess, celeste_stream_t stream);
+
 /* Release the problem (not the caller's workspace).  NULL is ignored. */
 void celeste_problem_destroy(celeste_problem* p);
 
