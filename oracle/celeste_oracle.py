@@ -337,6 +337,11 @@ def tr_subproblem(g, B, delta):
             break
         l = ln
     p = step(l)
+    pn = np.linalg.norm(p)
+    if pn > delta:
+        # next to the pole lambda = -lambda_min the root is resolved only to ~1e-8; the subproblem
+        # constrains |p| <= delta, so return the feasible point on the boundary
+        p = p * (delta / pn)
     return p, -(g @ p + 0.5 * p @ B @ p), False
 
 
@@ -344,7 +349,9 @@ def trust_region_newton(value, vgh, theta0, max_iter=50, delta0=1.0, delta_max=1
                         ftol=1e-8, gtol=1e-10, delta_min=1e-12):
     """Maximise the ELBO by minimising f = -L with a trust region (Nocedal & Wright Alg. 4.1).
 
-    Returns dict(theta, elbo, iters, status)."""
+    Stops when max |grad| <= gtol, when an interior (full Newton) step predicts a decrease
+    <= ftol |f|, when an accepted step changes f by <= ftol |f|, when the radius falls below
+    delta_min, or after max_iter subproblem solves.  Returns dict(theta, elbo, iters, status)."""
     th = theta0.copy()
     L, gL, HL = vgh(th)
     f, g, B = -L, -gL, -HL
@@ -361,6 +368,10 @@ def trust_region_newton(value, vgh, theta0, max_iter=50, delta0=1.0, delta_max=1
         it += 1
         p, pred, _ = tr_subproblem(g, B, delta)
         pnorm = np.linalg.norm(p)
+        if pnorm < (1.0 - 1e-9) * delta and pred <= ftol * abs(f):
+            # Newton decrement: the full Newton step promises less than ftol |f|
+            status = STATUS_CONVERGED
+            break
         f_new = -value(th + p)
         rho = (f - f_new) / pred if pred > 0 else -1.0
         if not np.isfinite(f_new):
