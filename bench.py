@@ -32,14 +32,19 @@ FP32_LANES_PER_SM = 128
 
 # Algorithmic float32 operations per pixel evaluation (FMA = 2), counted from the formulas the
 # kernels evaluate (breakdown in the design notes):
-#   galaxy component (42 per pixel): offset 2, squares 4, quadratic form 5, exponent 2,
-#     precision-vector 6, first shape terms 18, cross terms 24, accumulation 83  -> 144
-#   star component (3 per pixel): 34
-#   per-pixel tail (mixing, rate moments, pixel term and its derivatives, Jacobian rows,
-#     20 first-order sums, 21 second-order sums, 66 cross-product sums): 760
-FLOPS_FULL_PER_PIXEL = 42 * 144 + 3 * 34 + 760
-#   value only: 45 components x 12 + tail 40
-FLOPS_VALUE_PER_PIXEL = 45 * 12 + 40
+#   per PSF component (3): offsets and squares 6; star component 30
+#   per galaxy component (42): quadratic form 5, weighted exponential 2, precision vector 6,
+#     first shape terms 18, cross vectors 18, scaled weights 3, value/first-derivative sums 9,
+#     second-derivative sums 60, shape second terms 36  -> 157
+#   per-pixel tail: family mixing 75, rate moments 18, pixel term and its derivatives 44,
+#     Jacobian rows 42, curvature-scaled rows 44, scalars 6, first-order sums 38,
+#     second-order sums 150, cross-product sums 122, summation over pixels 108  -> 647
+FLOPS_FULL_PER_PIXEL = 3 * (6 + 30) + 42 * 157 + 647
+#   value only: per PSF component offsets 6 + 15 components x (quadratic form 5, exponential 2, sum 1),
+#   tail 25
+FLOPS_VALUE_PER_PIXEL = 3 * (6 + 15 * 8) + 25
+# MUFU (special-function) operations per full pixel evaluation: 45 exp2, 2 reciprocals/divides, 1 log1p
+MUFU_FULL_PER_PIXEL = 48
 
 
 def parse():
@@ -49,7 +54,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--sources", type=int, default=1000)
-    ap.add_argument("--tile", type=int, default=256)
+    ap.add_argument("--tile", type=int, default=128)
     ap.add_argument("--seed", type=int, default=1611)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--e2e-steps", type=int, default=2)
@@ -221,6 +226,10 @@ def main():
         prof = prof_stats = prob.profile_stop()
     conv = int((status == P.STATUS_CONVERGED).sum())
     iters_mean = float(iters.double().mean())
+    iters_max = int(iters.max())
+    status_counts = {name: int((status == code).sum()) for name, code in
+                     (("converged", P.STATUS_CONVERGED), ("max_iter", P.STATUS_MAX_ITER),
+                      ("nonfinite", P.STATUS_NONFINITE), ("radius_collapse", P.STATUS_RADIUS_COLLAPSE))}
     step_ms = [a.elapsed_time(b) for a, b in ev]
     t_step = float(np.sum(step_ms)) / 1e3
     if world > 1:
@@ -296,6 +305,7 @@ def main():
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(args),
                 "pixel_evals_per_s": px_rate, "converged": conv, "newton_iters_mean": iters_mean,
+                "newton_iters_max": iters_max, "status_counts": status_counts,
                 "layout": counts, "wall_s_timed": wall,
                 "roofline": {"bound": "alu", "kernel": "elbo_full_kernel", "achieved": achieved,
                              "peak": fp32_peak_tflops, "unit": "TFLOP/s",

@@ -92,7 +92,7 @@ typedef struct {
  *   priors: {P(galaxy), mean of log r, variance of log r, colour mean, colour variance}.
  *   exp_* / dev_*: unit-flux circular mixtures sum_j nu_j N(0, tau_j I) (nu > 0, tau > 0)
  *           for the exponential and de Vaucouleurs profiles.
- *   tile_pixels: pixels per work tile (128, 256, 512 or 1024; 0 = default 256). */
+ *   tile_pixels: pixels per work tile (128, 256, 512 or 1024; 0 = default 128). */
 typedef struct {
   int32_t n_images;
   const celeste_image_desc* images;
@@ -162,6 +162,17 @@ int celeste_newton_batch(celeste_problem* p, double* theta_inout, const celeste_
                          double* delta_inout, int32_t* iters_out, int32_t* status_out,
                          double* elbo_out, celeste_stream_t stream);
 
+/* The trust-region subproblem of celeste_newton_batch on its own, for n independent problems
+ * (Sec. "Variational Inference": Newton's method with a trust region):
+ *     p = argmin g.p + p.B.p/2  subject to |p| <= delta.
+ *   B: device float64 [n][27][27] symmetric; g: device [n][27]; delta: device [n] (> 0).
+ *   p: device [n][27] out; pred: device [n] out, -(g.p + p.B.p/2) (may be NULL);
+ *   hard: device int32 [n] out, 1 where the hard case (g orthogonal to the eigenvector of the
+ *   smallest eigenvalue) was taken (may be NULL).  Solved in float64 (tridiagonal reduction,
+ *   Sturm multisection for the smallest eigenvalue, safeguarded Newton on 1/|p| - 1/delta). */
+int celeste_tr_solve_batch(const double* B, const double* g, const double* delta, int n, double* p,
+                           double* pred, int32_t* hard, celeste_stream_t stream);
+
 /* Device-time accounting of the library's own kernels, for benchmarks.
  *   celeste_profile_start: reset and start recording.  While recording, every launch of the
  *     ELBO+gradient+Hessian pixel kernel and of the value-only pixel kernel is bracketed by CUDA
@@ -184,13 +195,15 @@ int celeste_profile_stop(celeste_problem* p, celeste_profile_stats* out);
 /* The same evaluation as celeste_elbo_batch with want = ELBO | GRAD | HESS, for callers that may
  * not allocate device memory when they evaluate (a pre-sized arena, an allocator owned by another
  * framework, a request path that must not allocate).  The call allocates nothing: the kernels'
- * scratch (per-tile partial sums, per-source flags, counters) lives in one fixed 8 MiB device array
- * inside this library, which every GPU that loads the library keeps until the process exits.
+ * scratch (per-patch tables, per-pixel source moments, per-tile partial sums, per-source flags,
+ * counters) lives in one fixed 8 MiB device array inside this library, which every GPU that loads
+ * the library keeps until the process exits.
  * The paper has no counterpart; it is a deployment variant of the evaluation above.
  *   p must be bound and have its background rendered; theta, elbo, grad, hess as in
  *   celeste_elbo_batch (all four required).
- *   Limit: 432 * n_tiles + 4 * n_sources bytes (each rounded up to 256) plus 256 must fit in
- *   8 MiB, about 19,000 tiles; larger problems get CELESTE_ERR_INVALID_ARG before any launch.
+ *   Limit: 432 * n_tiles + 4 * n_sources + 6880 * n_patches + 8 * n_pixels bytes (each rounded
+ *   up to 256) plus 256 must fit in 8 MiB (e.g. ~1000 patches of 17 x 17 pixels); larger problems
+ *   get CELESTE_ERR_INVALID_ARG before any launch.
  *   The first call on a device looks up the array's device address with that device current;
  *   make that first call before any stream capture.
  *   Every call shares the one array: calls that overlap on the GPU (different streams, threads

@@ -51,7 +51,7 @@ class ProfileStats(ctypes.Structure):
 EXPORTED = ["celeste_problem_create", "celeste_problem_workspace_bytes", "celeste_problem_counts",
             "celeste_problem_bind", "celeste_render_background", "celeste_elbo_batch", "celeste_newton_batch",
             "celeste_problem_destroy", "celeste_strerror", "celeste_last_error_detail", "celeste_profile_start",
-            "celeste_profile_stop"]
+            "celeste_profile_stop", "celeste_tr_solve_batch", "celeste_elbo_batch_noalloc"]
 
 
 def load_library(path=None):
@@ -73,6 +73,8 @@ def load_library(path=None):
         "celeste_last_error_detail": (ctypes.c_char_p, []),
         "celeste_profile_start": (ctypes.c_int, [vp]),
         "celeste_profile_stop": (ctypes.c_int, [vp, ctypes.POINTER(ProfileStats)]),
+        "celeste_tr_solve_batch": (ctypes.c_int, [dp, dp, dp, ctypes.c_int, dp, dp, dp, vp]),
+        "celeste_elbo_batch_noalloc": (ctypes.c_int, [vp, dp, dp, dp, dp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -113,7 +115,7 @@ class Problem:
     .psf[3,6,6]), .u0 [S,2], .radius [S], .priors [5] and the exp/deV mixture tables.
     device_pixels: optional list of CUDA float32 tensors already holding the images."""
 
-    def __init__(self, scene, device="cuda", tile_pixels=256, device_pixels=None, stream=None):
+    def __init__(self, scene, device="cuda", tile_pixels=128, device_pixels=None, stream=None):
         L = lib()
         self.device = torch.device(device)
         if device_pixels is None:
@@ -211,6 +213,20 @@ class Problem:
             self.close()
         except Exception:
             pass
+
+
+def tr_solve_batch(B, g, delta, stream=None):
+    """Trust-region subproblems on the device: B [n,27,27], g [n,27], delta [n] float64 CUDA tensors.
+    Returns (p [n,27], pred [n], hard [n] int32)."""
+    n = g.shape[0]
+    for t in (B, g, delta):
+        assert t.dtype == torch.float64 and t.is_contiguous() and t.is_cuda
+    p = torch.empty(n, NPARAM, dtype=torch.float64, device=g.device)
+    pred = torch.empty(n, dtype=torch.float64, device=g.device)
+    hard = torch.empty(n, dtype=torch.int32, device=g.device)
+    _check(lib().celeste_tr_solve_batch(_ptr(B), _ptr(g), _ptr(delta), ctypes.c_int(n), _ptr(p), _ptr(pred), _ptr(hard),
+                                        _stream(stream)))
+    return p, pred, hard
 
 
 class HostProblem:

@@ -5,15 +5,18 @@
 // Work in the "E-space" of a patch: the 27 parameters with the world position u replaced by
 // the pixel-space mean mu = A u + o (so the pixel sums need no WCS); the u rows/columns are
 // mapped back with A before summing over the source's images.
+//
+// GB300 float64 latencies are long (a dependent FMA ~64 cycles, exp ~1100), so every
+// transcendental is evaluated once per source and in parallel across threads; the per-patch
+// work is plain multiply-adds spread over the CTA.
 #include "celeste_internal.cuh"
 #include "kernels.h"
 
 namespace celeste {
 
-__device__ constexpr int tri6d(int i, int j) { return i * 6 - i * (i - 1) / 2 + (j - i); }
 __device__ constexpr int tri11d(int i, int j) { return i * 11 - i * (i - 1) / 2 + (j - i); }
 
-// Brightness parameter indices of type i (r1, rho, c1 x4, gamma x4).
+// Brightness parameter indices of type t (r1, rho, c1 x4, gamma x4).
 __device__ inline int bvar(int type, int v) {
   if (v == 0) return type ? 9 : 7;
   if (v == 1) return type ? 10 : 8;
@@ -21,110 +24,76 @@ __device__ inline int bvar(int type, int v) {
   return (type ? 23 : 15) + (v - 6);
 }
 
-// Category of a parameter index: 0..5 -> G6 (mu0 mu1 dev axis angle scale), 6 alpha,
-// 7.. brightness (type, v) encoded as 100 + 10 * type + v.
-__device__ inline int category(int i) {
-  if (i < 6) return i;
-  if (i == 6) return 6;
-  if (i == 7) return 100;
-  if (i == 8) return 101;
-  if (i == 9) return 110;
-  if (i == 10) return 111;
-  if (i < 15) return 100 + 2 + (i - 11);
-  if (i < 19) return 100 + 6 + (i - 15);
-  if (i < 23) return 110 + 2 + (i - 19);
-  return 110 + 6 + (i - 23);
+// Inverse of bvar for a brightness parameter index j >= 7: type and variable number.
+__device__ inline void bvar_inv(int j, int& t, int& v) {
+  t = (j == 9 || j == 10 || j >= 19) ? 1 : 0;
+  if (j == 7 || j == 9) v = 0;
+  else if (j == 8 || j == 10) v = 1;
+  else if (j < 15) v = 2 + (j - 11);
+  else if (j < 19) v = 6 + (j - 15);
+  else if (j < 23) v = 2 + (j - 19);
+  else v = 6 + (j - 23);
+}
+
+// Source-level quantities shared by all patches (exps of the log-variances, type probabilities).
+struct SourceConst {
+  double a0, a1, aa, la0, la1;   // P(star), P(galaxy), product, their logs
+  double ev[2][10];              // exp of the log-variance parameters (v = 1, 6..9), 0 elsewhere
+};
+
+__device__ inline void source_const_parallel(const double* th, SourceConst& sc, int tid) {
+  if (tid < 10) {
+    const int t = tid / 5, k = tid % 5, v = k == 0 ? 1 : 5 + k;
+    sc.ev[t][v] = exp(th[bvar(t, v)]);
+  } else if (tid < 20) {
+    const int t = (tid - 10) / 5, k = (tid - 10) % 5, v = k == 0 ? 0 : k + 1;   // v = 0, 2..5
+    sc.ev[t][v] = 0.0;
+  } else if (tid == 20) {
+    const double al = th[6];
+    const double e = exp(-fabs(al)), l1p = log1p(e);
+    sc.la1 = al >= 0 ? -l1p : al - l1p;   // log sigmoid(alpha)
+    sc.la0 = sc.la1 - al;                  // log sigmoid(-alpha)
+    const double sg = 1.0 / (1.0 + e);
+    sc.a1 = al >= 0 ? sg : e * sg;
+    sc.a0 = al >= 0 ? e * sg : sg;
+    sc.aa = sc.a0 * sc.a1;
+  }
+}
+
+// One normal-KL term of type t: k = 0 the log flux, k = 1..4 the colours j = k - 1.
+// KL_N(m, v || mu, s2) = (log s2 - log v + (v + (m - mu)^2) / s2 - 1) / 2 with v = exp(log v).
+__device__ inline double kl_normal_term(const double* th, const double* ev, const ProblemDev& P, int t, int k) {
+  const double m = k == 0 ? th[bvar(t, 0)] : th[bvar(t, 1 + k)];
+  const double lv = k == 0 ? th[bvar(t, 1)] : th[bvar(t, 5 + k)];
+  const double v = k == 0 ? ev[1] : ev[5 + k];
+  const double mu = k == 0 ? P.priors[1] : P.priors[3], s2 = k == 0 ? P.priors[2] : P.priors[4];
+  const double ls2 = k == 0 ? P.log_var_r : P.log_var_c;
+  return 0.5 * (ls2 - lv + (v + (m - mu) * (m - mu)) / s2 - 1.0);
+}
+
+// First and second derivative of K_t w.r.t. brightness parameter j of type t.
+__device__ inline void kl_normal_derivs(const double* th, const SourceConst& sc, const ProblemDev& P, int j, int& t,
+                                        double& dK, double& d2K) {
+  int v;
+  bvar_inv(j, t, v);
+  if (v == 0 || (v >= 2 && v < 6)) {
+    const double mu = v == 0 ? P.priors[1] : P.priors[3], s2 = v == 0 ? P.priors[2] : P.priors[4];
+    dK = (th[j] - mu) / s2;
+    d2K = 1.0 / s2;
+  } else {
+    const double s2 = v == 1 ? P.priors[2] : P.priors[4];
+    dK = 0.5 * (sc.ev[t][v] / s2 - 1.0);
+    d2K = 0.5 * sc.ev[t][v] / s2;
+  }
 }
 
 struct PatchLift {
-  double a0, a1, aa;                       // P(star), P(galaxy), a0 a1
   double L1[2], L2[2];                     // E[l_b|i], E[l_b^2|i]
   double dL1[2][10], dL2[2][10];           // gradients over the type's brightness parameters
   double d2l1[2][10], d2l2[2][10];         // diagonal second derivatives of log L1, log L2
-  double S1[10], S2[10], Hp[21];           // tile sums (float64)
   double A[4];                             // WCS linear part
+  int band;
 };
-
-__device__ double h2_entry(const PatchLift& c, int ci, int cj) {
-  // symmetric: order so that ci <= cj in the category encoding
-  if (ci > cj) {
-    int t = ci;
-    ci = cj;
-    cj = t;
-  }
-  auto s1f0g = [&](int a) { return a < 2 ? c.S1[1 + a] : 0.0; };
-  auto s2f0g = [&](int a) { return a < 2 ? c.S2[1 + a] : 0.0; };
-  auto s1fg = [&](int type, int a) { return type ? c.S1[4 + a] : s1f0g(a); };
-  auto s2fg = [&](int type, int a) { return type ? c.S2[4 + a] : s2f0g(a); };
-  const double S1f[2] = {c.S1[0], c.S1[3]}, S2f[2] = {c.S2[0], c.S2[3]};
-  if (cj < 6) return c.Hp[tri6d(ci, cj)];
-  if (cj == 6) {
-    if (ci < 6)
-      return c.aa * (c.L1[1] * s1fg(1, ci) - c.L1[0] * s1fg(0, ci) + c.L2[1] * s2fg(1, ci) - c.L2[0] * s2fg(0, ci));
-    return c.aa * (1.0 - 2.0 * c.a1) * (c.L1[1] * S1f[1] - c.L1[0] * S1f[0] + c.L2[1] * S2f[1] - c.L2[0] * S2f[0]);
-  }
-  const int tj = (cj - 100) / 10, vj = (cj - 100) % 10;
-  const double ai = tj ? c.a1 : c.a0;
-  if (ci < 6) return ai * (s1fg(tj, ci) * c.dL1[tj][vj] + s2fg(tj, ci) * c.dL2[tj][vj]);
-  if (ci == 6) return (tj ? c.aa : -c.aa) * (S1f[tj] * c.dL1[tj][vj] + S2f[tj] * c.dL2[tj][vj]);
-  const int ti = (ci - 100) / 10, vi = (ci - 100) % 10;
-  if (ti != tj) return 0.0;
-  // d2 L = L (dlogL dlogL^T + diag(d2 log L))
-  const double dl1i = c.dL1[ti][vi] / c.L1[ti], dl1j = c.dL1[tj][vj] / c.L1[tj];
-  const double dl2i = c.dL2[ti][vi] / c.L2[ti], dl2j = c.dL2[tj][vj] / c.L2[tj];
-  double d2L1 = c.L1[ti] * (dl1i * dl1j + (vi == vj ? c.d2l1[ti][vi] : 0.0));
-  double d2L2 = c.L2[ti] * (dl2i * dl2j + (vi == vj ? c.d2l2[ti][vi] : 0.0));
-  return ai * (S1f[ti] * d2L1 + S2f[ti] * d2L2);
-}
-
-// KL of one source and its derivatives (closed forms).
-__device__ void kl_terms(const double* th, const double* pri, double& kl, double* g, double* h /*27x27*/, int tid,
-                         int nthreads) {
-  const double phi = pri[0], mu_r = pri[1], var_r = pri[2], mu_c = pri[3], var_c = pri[4];
-  const double al = th[6];
-  const double a1 = sigmoid_d(al), a0 = sigmoid_d(-al), aa = a0 * a1;
-  const double la1 = al >= 0 ? -log1p(exp(-al)) : al - log1p(exp(al));
-  const double la0 = la1 - al;
-  const double lgt = log(phi) - log1p(-phi);
-  double K[2], dK[2][10], d2K[2][10];
-  for (int t = 0; t < 2; ++t) {
-    K[t] = 0.0;
-    for (int v = 0; v < 10; ++v) {
-      const int idx = bvar(t, v);
-      if (v == 0 || (v >= 2 && v < 6)) {
-        const double mu = v == 0 ? mu_r : mu_c, s2 = v == 0 ? var_r : var_c;
-        const int rho_idx = v == 0 ? bvar(t, 1) : bvar(t, v + 4);
-        const double m = th[idx], rho = th[rho_idx];
-        K[t] += 0.5 * (log(s2) - rho + (exp(rho) + (m - mu) * (m - mu)) / s2 - 1.0);
-        dK[t][v] = (m - mu) / s2;
-        d2K[t][v] = 1.0 / s2;
-      } else {
-        const double s2 = v == 1 ? var_r : var_c;
-        const double rho = th[idx];
-        dK[t][v] = 0.5 * (exp(rho) / s2 - 1.0);
-        d2K[t][v] = 0.5 * exp(rho) / s2;
-      }
-    }
-  }
-  kl = a1 * (la1 - log(phi)) + a0 * (la0 - log1p(-phi)) + a0 * K[0] + a1 * K[1];
-  for (int i = tid; i < NP; i += nthreads) g[i] = 0.0;
-  for (int i = tid; i < NP * NP; i += nthreads) h[i] = 0.0;
-  __syncthreads();
-  if (tid == 0) {
-    g[6] = aa * (al - lgt) + aa * (K[1] - K[0]);
-    h[6 * NP + 6] = aa * ((1.0 - 2.0 * a1) * (al - lgt) + 1.0) + aa * (1.0 - 2.0 * a1) * (K[1] - K[0]);
-    for (int t = 0; t < 2; ++t) {
-      const double at = t ? a1 : a0, sa = t ? aa : -aa;
-      for (int v = 0; v < 10; ++v) {
-        const int idx = bvar(t, v);
-        g[idx] = at * dK[t][v];
-        h[idx * NP + idx] = at * d2K[t][v];
-        h[6 * NP + idx] = h[idx * NP + 6] = sa * dK[t][v];
-      }
-    }
-  }
-  __syncthreads();
-}
 
 __global__ void __launch_bounds__(128) assemble_kernel(ProblemDev P, const double* __restrict__ theta, int full,
                                                        int flag_mask, double* elbo, double* grad, double* hess) {
@@ -133,115 +102,176 @@ __global__ void __launch_bounds__(128) assemble_kernel(ProblemDev P, const doubl
   const int tid = threadIdx.x, nt = blockDim.x;
   __shared__ double sums[NACC];
   __shared__ double Hs[NP * NP], gs[NP], HE[NP * NP], gE[NP];
-  __shared__ double Kd[NRED * NP], T[NRED * NP], ghat[NRED];
+  __shared__ double Msym[NRED * NRED], nzK[NP], nzL[NP], ghat[NRED], H2[NP * NP];
+  __shared__ int nzA[NP], nzB[NP];
   __shared__ PatchLift c;
-  __shared__ double Lsum;
+  __shared__ SourceConst sc;
+  __shared__ double Lsum, red[16];
   const double* th = theta + (size_t)s * NP;
   for (int i = tid; i < NP * NP; i += nt) Hs[i] = 0.0;
   for (int i = tid; i < NP; i += nt) gs[i] = 0.0;
   if (tid == 0) Lsum = 0.0;
+  source_const_parallel(th, sc, tid);
   __syncthreads();
   for (int p = P.src_patch[s]; p < P.src_patch[s + 1]; ++p) {
     const PatchDev pt = P.patches[p];
-    if (!full) {
-      if (tid == 0) {
-        double v = 0.0;
-        for (int t = pt.tile_begin; t < pt.tile_end; ++t) v += (double)P.vpartials[t];
-        Lsum += v;
-      }
-      continue;
-    }
-    for (int q = tid; q < NACC; q += nt) {
+    // ---- tile sums (float64, fixed order) and the band moments, in parallel
+    if (tid < NACC) {
       double v = 0.0;
-      for (int t = pt.tile_begin; t < pt.tile_end; ++t) v += (double)P.partials[(size_t)t * NACC + q];
-      sums[q] = v;
-    }
-    __syncthreads();
-    if (tid == 0) {
-      const ImageDev& im = P.images[pt.image];
-      c.a1 = sigmoid_d(th[6]);
-      c.a0 = sigmoid_d(-th[6]);
-      c.aa = c.a0 * c.a1;
+      for (int t = pt.tile_begin; t < pt.tile_end; ++t) v += (double)P.partials[(size_t)t * NACC + tid];
+      sums[tid] = v;
+    } else if (tid < NACC + 4) {
+      const int k = tid - NACC, t = k & 1, second = k >> 1;
+      const int band = P.images[pt.image].band;
       double arow[4];
-      color_row(im.band, arow);
-      for (int t = 0; t < 2; ++t) {
-        lognormal_moments(th, t, im.band, c.L1[t], c.L2[t]);
-        double dl1[10], dl2[10];
-        dl1[0] = 1.0;
-        dl2[0] = 2.0;
-        const double er = exp(th[bvar(t, 1)]);
-        dl1[1] = 0.5 * er;
-        dl2[1] = 2.0 * er;
-        c.d2l1[t][0] = 0.0;
-        c.d2l2[t][0] = 0.0;
-        c.d2l1[t][1] = 0.5 * er;
-        c.d2l2[t][1] = 2.0 * er;
-        for (int j = 0; j < 4; ++j) {
-          const double eg = exp(th[bvar(t, 6 + j)]);
-          dl1[2 + j] = arow[j];
-          dl2[2 + j] = 2.0 * arow[j];
-          dl1[6 + j] = 0.5 * arow[j] * arow[j] * eg;
-          dl2[6 + j] = 2.0 * arow[j] * arow[j] * eg;
-          c.d2l1[t][2 + j] = 0.0;
-          c.d2l2[t][2 + j] = 0.0;
-          c.d2l1[t][6 + j] = 0.5 * arow[j] * arow[j] * eg;
-          c.d2l2[t][6 + j] = 2.0 * arow[j] * arow[j] * eg;
-        }
-        for (int v = 0; v < 10; ++v) {
-          c.dL1[t][v] = c.L1[t] * dl1[v];
-          c.dL2[t][v] = c.L2[t] * dl2[v];
-        }
+      color_row(band, arow);
+      double m = th[bvar(t, 0)], v = sc.ev[t][1];
+      for (int j = 0; j < 4; ++j) {
+        m += arow[j] * th[bvar(t, 2 + j)];
+        v += arow[j] * arow[j] * sc.ev[t][6 + j];
       }
-      for (int q = 0; q < 10; ++q) {
-        c.S1[q] = sums[ACC_S1 + q];
-        c.S2[q] = sums[ACC_S2 + q];
-      }
-      for (int q = 0; q < 21; ++q) c.Hp[q] = sums[ACC_HP + q];
-      for (int q = 0; q < 4; ++q) c.A[q] = im.A[q];
-      Lsum += sums[ACC_L];
-      // reduced gradient
-      const double A0 = c.a0 * c.L1[0], A1 = c.a1 * c.L1[1], B0 = c.a0 * c.L2[0], B1 = c.a1 * c.L2[1];
-      for (int a = 0; a < 2; ++a) ghat[a] = A0 * c.S1[1 + a] + A1 * c.S1[4 + a] + B0 * c.S2[1 + a] + B1 * c.S2[4 + a];
-      for (int a = 2; a < 6; ++a) ghat[a] = A1 * c.S1[4 + a] + B1 * c.S2[4 + a];
-      ghat[6] = c.aa * (c.L1[1] * c.S1[3] - c.L1[0] * c.S1[0] + c.L2[1] * c.S2[3] - c.L2[0] * c.S2[0]);
-      ghat[7] = c.S1[0];
-      ghat[8] = c.S1[3];
-      ghat[9] = c.S2[0];
-      ghat[10] = c.S2[3];
-    }
-    // lift matrix K (11 x 27) in E-space
-    for (int i = tid; i < NRED * NP; i += nt) Kd[i] = 0.0;
-    __syncthreads();
-    if (tid < 7) Kd[tid * NP + tid] = 1.0;
-    if (tid >= 32 && tid < 72) {
-      const int r = (tid - 32) / 10, v = (tid - 32) % 10;   // r: 0 -> row 7 (f0,E), 1 -> 8, 2 -> 9, 3 -> 10
-      const int type = r & 1;
-      const double at = type ? c.a1 : c.a0;
-      const double val = r < 2 ? at * c.dL1[type][v] : at * c.dL2[type][v];
-      Kd[(7 + r) * NP + bvar(type, v)] = val;
+      if (second)
+        c.L2[t] = exp(2.0 * m + 2.0 * v);
+      else
+        c.L1[t] = exp(m + 0.5 * v);
+      if (k == 0) c.band = band;
+    } else if (tid < NACC + 8) {
+      c.A[tid - NACC - 4] = P.images[pt.image].A[tid - NACC - 4];
     }
     __syncthreads();
-    // T = M K  (M symmetric 11x11 from packed sums)
-    for (int i = tid; i < NRED * NP; i += nt) {
-      const int a = i / NP, j = i % NP;
-      double v = 0.0;
-      for (int b = 0; b < NRED; ++b) {
-        const double m = sums[ACC_M + (a <= b ? tri11d(a, b) : tri11d(b, a))];
-        v += m * Kd[b * NP + j];
+    // ---- derivatives of the band moments over the type's brightness parameters
+    if (tid < 40) {
+      const int t = tid / 20, which = (tid % 20) / 10, v = tid % 10;
+      double arow[4];
+      color_row(c.band, arow);
+      double dl, d2;
+      if (v == 0) {
+        dl = which ? 2.0 : 1.0;
+        d2 = 0.0;
+      } else if (v == 1) {
+        dl = (which ? 2.0 : 0.5) * sc.ev[t][1];
+        d2 = dl;
+      } else if (v < 6) {
+        dl = (which ? 2.0 : 1.0) * arow[v - 2];
+        d2 = 0.0;
+      } else {
+        dl = (which ? 2.0 : 0.5) * arow[v - 6] * arow[v - 6] * sc.ev[t][v];
+        d2 = dl;
       }
-      T[i] = v;
+      if (which) {
+        c.dL2[t][v] = c.L2[t] * dl;
+        c.d2l2[t][v] = d2;
+      } else {
+        c.dL1[t][v] = c.L1[t] * dl;
+        c.d2l1[t][v] = d2;
+      }
+    }
+    if (tid == 64) Lsum += sums[ACC_L];
+    __syncthreads();
+    const double* S1 = sums + ACC_S1;
+    const double* S2 = sums + ACC_S2;
+    // ---- reduced gradient
+    if (tid < NRED) {
+      const double A0 = sc.a0 * c.L1[0], A1 = sc.a1 * c.L1[1], B0 = sc.a0 * c.L2[0], B1 = sc.a1 * c.L2[1];
+      const int a = tid;
+      double v;
+      if (a < 2)
+        v = A0 * S1[1 + a] + A1 * S1[4 + a] + B0 * S2[1 + a] + B1 * S2[4 + a];
+      else if (a < 6)
+        v = A1 * S1[4 + a] + B1 * S2[4 + a];
+      else if (a == 6)
+        v = sc.aa * (c.L1[1] * S1[3] - c.L1[0] * S1[0] + c.L2[1] * S2[3] - c.L2[0] * S2[0]);
+      else
+        v = a == 7 ? S1[0] : a == 8 ? S1[3] : a == 9 ? S2[0] : S2[3];
+      ghat[a] = v;
+    }
+    // Lift from the 11-column reduced basis to the 27 parameters: column j of K has at most two
+    // nonzeros (a, k): j < 7 -> (j, 1); brightness parameter v of type t -> (7 + t, a_t dL1_t[v])
+    // from the E-row and (9 + t, a_t dL2_t[v]) from the V-row.  H_E = K^T M K + H2, g_E = K^T ghat.
+    if (tid >= 32 && tid < 32 + NP) {
+      const int j = tid - 32;
+      if (j < 7) {
+        nzA[j] = j;
+        nzK[j] = 1.0;
+        nzB[j] = -1;
+        nzL[j] = 0.0;
+      } else {
+        int t, v;
+        bvar_inv(j, t, v);
+        const double at = t ? sc.a1 : sc.a0;
+        nzA[j] = 7 + t;
+        nzK[j] = at * c.dL1[t][v];
+        nzB[j] = 9 + t;
+        nzL[j] = at * c.dL2[t][v];
+      }
+    }
+    for (int i = tid; i < NRED * NRED; i += nt) {
+      const int a = i / NRED, b = i % NRED;
+      Msym[i] = sums[ACC_M + (a <= b ? tri11d(a, b) : tri11d(b, a))];
+    }
+    // second-order part  sum_m w1 d2E[G] + w2 d2E[G^2], filled block by block (uniform work per
+    // thread within a block):  G6 x G6 from the kernel's sums; G6 x alpha; alpha x alpha;
+    // G6 x brightness; alpha x brightness; brightness x brightness (same type only)
+    for (int i = tid; i < NP * NP; i += nt) H2[i] = 0.0;
+    __syncthreads();
+    for (int q = tid; q < 21; q += nt) {
+      int a = 0, rem = q;
+      while (rem >= 6 - a) {
+        rem -= 6 - a;
+        ++a;
+      }
+      const int b = a + rem;
+      H2[a * NP + b] = H2[b * NP + a] = sums[ACC_HP + q];
+    }
+    const double S1f[2] = {S1[0], S1[3]}, S2f[2] = {S2[0], S2[3]};
+    for (int i = tid; i < 6 + 1 + 120 + 20 + 200; i += nt) {
+      if (i < 6) {
+        const int a = i;
+        const double s1f0 = a < 2 ? S1[1 + a] : 0.0, s2f0 = a < 2 ? S2[1 + a] : 0.0;
+        H2[a * NP + 6] = H2[6 * NP + a] =
+            sc.aa * (c.L1[1] * S1[4 + a] - c.L1[0] * s1f0 + c.L2[1] * S2[4 + a] - c.L2[0] * s2f0);
+      } else if (i == 6) {
+        H2[6 * NP + 6] =
+            sc.aa * (1.0 - 2.0 * sc.a1) * (c.L1[1] * S1f[1] - c.L1[0] * S1f[0] + c.L2[1] * S2f[1] - c.L2[0] * S2f[0]);
+      } else if (i < 127) {
+        const int k = i - 7, t = k / 60, a = (k % 60) / 10, v = k % 10, j = bvar(t, v);
+        const double s1 = t ? S1[4 + a] : (a < 2 ? S1[1 + a] : 0.0);
+        const double s2 = t ? S2[4 + a] : (a < 2 ? S2[1 + a] : 0.0);
+        H2[a * NP + j] = H2[j * NP + a] = (t ? sc.a1 : sc.a0) * (s1 * c.dL1[t][v] + s2 * c.dL2[t][v]);
+      } else if (i < 147) {
+        const int k = i - 127, t = k / 10, v = k % 10, j = bvar(t, v);
+        H2[6 * NP + j] = H2[j * NP + 6] = (t ? sc.aa : -sc.aa) * (S1f[t] * c.dL1[t][v] + S2f[t] * c.dL2[t][v]);
+      } else {
+        // d2 L = L (dlogL dlogL^T + diag(d2 log L)) within a type
+        const int k = i - 147, t = k / 100, v = (k % 100) / 10, w = k % 10;
+        const double dl1v = c.dL1[t][v] / c.L1[t], dl1w = c.dL1[t][w] / c.L1[t];
+        const double dl2v = c.dL2[t][v] / c.L2[t], dl2w = c.dL2[t][w] / c.L2[t];
+        const double d2L1 = c.L1[t] * (dl1v * dl1w + (v == w ? c.d2l1[t][v] : 0.0));
+        const double d2L2 = c.L2[t] * (dl2v * dl2w + (v == w ? c.d2l2[t][v] : 0.0));
+        H2[bvar(t, v) * NP + bvar(t, w)] = (t ? sc.a1 : sc.a0) * (S1f[t] * d2L1 + S2f[t] * d2L2);
+      }
     }
     __syncthreads();
-    for (int i = tid; i < NP * NP; i += nt) {
-      const int r = i / NP, q = i % NP;
-      double v = 0.0;
-      for (int a = 0; a < NRED; ++a) v += Kd[a * NP + r] * T[a * NP + q];
-      HE[i] = v + h2_entry(c, category(r), category(q));
+    for (int q = tid; q < NP * (NP + 1) / 2; q += nt) {
+      int r = 0, rem = q;   // q -> (r, col) with r <= col
+      while (rem >= NP - r) {
+        rem -= NP - r;
+        ++r;
+      }
+      const int col = r + rem;
+      double v = nzK[r] * nzK[col] * Msym[nzA[r] * NRED + nzA[col]];
+      if (nzB[col] >= 0) v += nzK[r] * nzL[col] * Msym[nzA[r] * NRED + nzB[col]];
+      if (nzB[r] >= 0) {
+        v += nzL[r] * nzK[col] * Msym[nzB[r] * NRED + nzA[col]];
+        if (nzB[col] >= 0) v += nzL[r] * nzL[col] * Msym[nzB[r] * NRED + nzB[col]];
+      }
+      v += H2[r * NP + col];
+      HE[r * NP + col] = v;
+      HE[col * NP + r] = v;
     }
-    for (int j = tid; j < NP; j += nt) {
-      double v = 0.0;
-      for (int a = 0; a < NRED; ++a) v += ghat[a] * Kd[a * NP + j];
-      gE[j] = v;
+    if (tid < NP) {
+      const int j = tid;
+      gE[j] = nzK[j] * ghat[nzA[j]] + (nzB[j] >= 0 ? nzL[j] * ghat[nzB[j]] : 0.0);
     }
     __syncthreads();
     // map mu -> u: d/du_b = sum_a A[a][b] d/dmu_a
@@ -267,16 +297,105 @@ __global__ void __launch_bounds__(128) assemble_kernel(ProblemDev P, const doubl
     }
     __syncthreads();
   }
+
+  // ---- KL = a1 (log a1 - log Phi) + a0 (log a0 - log(1 - Phi)) + a0 K_0 + a1 K_1 and its
+  //      derivatives (closed forms from the source constants; no further transcendentals)
+  if (tid < 10) red[tid] = kl_normal_term(th, sc.ev[tid / 5], P, tid / 5, tid % 5);
   __syncthreads();
-  double kl;
-  kl_terms(th, P.priors, kl, gE, HE, tid, nt);
-  if (tid == 0 && elbo) elbo[s] = Lsum - kl;
-  if (full) {
-    if (grad)
-      for (int j = tid; j < NP; j += nt) grad[(size_t)s * NP + j] = gs[j] - gE[j];
-    if (hess)
-      for (int i = tid; i < NP * NP; i += nt) hess[(size_t)s * NP * NP + i] = Hs[i] - HE[i];
+  if (tid == 0) {
+    double K0 = 0.0, K1 = 0.0;
+    for (int i = 0; i < 5; ++i) {
+      K0 += red[i];
+      K1 += red[5 + i];
+    }
+    red[10] = K0;
+    red[11] = K1;
+    const double kl = sc.a1 * (sc.la1 - P.log_phi) + sc.a0 * (sc.la0 - P.log1m_phi) + sc.a0 * K0 + sc.a1 * K1;
+    if (elbo) elbo[s] = Lsum - kl;
   }
+  __syncthreads();
+  if (full) {
+    const double K0 = red[10], K1 = red[11];
+    const double ga = sc.aa * (th[6] - P.logit_phi) + sc.aa * (K1 - K0);
+    if (hess) {
+      for (int i = tid; i < NP * NP; i += nt) {
+        const int r = i / NP, q = i % NP;
+        double h = 0.0;
+        if (r == 6 && q == 6) {
+          h = sc.aa * ((1.0 - 2.0 * sc.a1) * (th[6] - P.logit_phi) + 1.0) + sc.aa * (1.0 - 2.0 * sc.a1) * (K1 - K0);
+        } else if ((r == 6 && q >= 7) || (q == 6 && r >= 7)) {
+          int t;
+          double dK, d2K;
+          kl_normal_derivs(th, sc, P, r == 6 ? q : r, t, dK, d2K);
+          h = (t ? sc.aa : -sc.aa) * dK;
+        } else if (r == q && r >= 7) {
+          int t;
+          double dK, d2K;
+          kl_normal_derivs(th, sc, P, r, t, dK, d2K);
+          h = (t ? sc.a1 : sc.a0) * d2K;
+        }
+        hess[(size_t)s * NP * NP + i] = Hs[i] - h;
+      }
+    }
+    if (grad && tid < NP) {
+      const int j = tid;
+      double gk = 0.0;
+      if (j == 6) {
+        gk = ga;
+      } else if (j >= 7) {
+        int t;
+        double dK, d2K;
+        kl_normal_derivs(th, sc, P, j, t, dK, d2K);
+        gk = (t ? sc.a1 : sc.a0) * dK;
+      }
+      grad[(size_t)s * NP + j] = gs[j] - gk;
+    }
+  }
+}
+
+// Value-only assembly, one warp per source: sum of the value tile sums minus the KL at theta
+// (plus the KL at theta_ref when the pixel sums are differences from theta_ref).
+__global__ void assemble_value_kernel(ProblemDev P, const double* __restrict__ theta, const double* __restrict__ theta_ref,
+                                      int flag_mask, double* out) {
+  const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (s >= P.S || !(P.flags[s] & flag_mask)) return;   // warp-uniform
+  double v = 0.0;
+  for (int p = P.src_patch[s]; p < P.src_patch[s + 1]; ++p) {
+    const PatchDev& pt = P.patches[p];
+    for (int t = pt.tile_begin + lane; t < pt.tile_end; t += 32) v += (double)P.vpartials[t];
+  }
+  // KL terms: lanes 0..10 at theta, lanes 16..26 at theta_ref (subtracted / added)
+  const int which = lane >> 4, k = lane & 15;
+  const double* th = which ? theta_ref : theta;
+  if (th && k <= 10) {
+    th += (size_t)s * NP;
+    const double al = th[6], e = exp(-fabs(al)), sg = 1.0 / (1.0 + e);
+    const double a1 = al >= 0 ? sg : e * sg, a0 = al >= 0 ? e * sg : sg;
+    double klp;
+    if (k < 10) {
+      const int t = k / 5, kk = k % 5;
+      double ev[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+      const int vi = kk == 0 ? 1 : 5 + kk;
+      ev[vi] = exp(th[bvar(t, vi)]);
+      klp = (t ? a1 : a0) * kl_normal_term(th, ev, P, t, kk);
+    } else {
+      const double l1p = log1p(e);
+      const double la1 = al >= 0 ? -l1p : al - l1p, la0 = la1 - al;
+      klp = a1 * (la1 - P.log_phi) + a0 * (la0 - P.log1m_phi);
+    }
+    v += which ? klp : -klp;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (lane == 0) out[s] = v;
+}
+
+cudaError_t launch_assemble_value(const ProblemDev& P, const double* theta, const double* theta_ref, int flag_mask,
+                                  double* out, cudaStream_t st) {
+  const int warps_per_block = 4;
+  assemble_value_kernel<<<(P.S + warps_per_block - 1) / warps_per_block, 32 * warps_per_block, 0, st>>>(
+      P, theta, theta_ref, flag_mask, out);
+  return cudaGetLastError();
 }
 
 __global__ void set_flags_kernel(int* flags, int S, int value) {

@@ -31,17 +31,22 @@ constexpr int ACC_M = 42;                // 66: packed upper triangle of the 11x
 constexpr int NACC = 108;
 constexpr int NRED = 11;
 
-// Galaxy component table (floats), one per (PSF component k, profile component j).
-// Means are relative to the patch origin; quadratic forms use s = (d0^2, 2 d0 d1, d1^2).
-constexpr int GT_MU = 0;     // 2
-constexpr int GT_LW2 = 2;    // log2 of weight * normaliser (weight excludes the fracDev mixing)
-constexpr int GT_P = 3;      // 3: precision matrix (00, 01, 11)
-constexpr int GT_QA = 6;     // 3 x 3: -1/2 dP/da, a = axis, angle, scale
-constexpr int GT_LA = 15;    // 3: -1/2 d logdet / da
-constexpr int GT_QAB = 18;   // 6 x 3: -1/2 d2P/dadb, pairs (00 01 02 11 12 22)
-constexpr int GT_LAB = 36;   // 6: -1/2 d2 logdet / dadb
-constexpr int GT_STRIDE = 44;
-constexpr int ST_STRIDE = 8; // star: mu (2), lw2, P (3), pad
+// Per-patch table (floats) written by the table kernel at the source's current parameters and
+// bulk-copied into shared memory by every tile of the patch.  Positions are relative to the patch
+// origin; quadratic forms use s = (d0^2, 2 d0 d1, d1^2) with d = pixel - mean of PSF component k
+// (the same for the star component k and the 14 galaxy components (k, j)).
+constexpr int TB_MU = 0;      // 3 x (x, y) mean of PSF component k, + 2 pad
+constexpr int TB_STAR = 8;    // 3 x (W, P00, P01, P11)
+constexpr int TB_GAL = 20;    // NGAL x GT_STRIDE, component g = k * NMIX + j
+constexpr int GT_P = 0;       // 3: precision matrix (00, 01, 11)
+constexpr int GT_W = 3;       // weight * Gaussian normaliser, w_k nu_j / (2 pi sqrt(det)) (fracDev mixing applied later)
+constexpr int GT_QA = 4;      // 3 x 3: -1/2 dP/da, a = axis, angle, scale
+constexpr int GT_LA = 13;     // 3: -1/2 d logdet / da
+constexpr int GT_QAB = 16;    // 6 x 3: -1/2 d2P/dadb, pairs (00 01 02 11 12 22)
+constexpr int GT_LAB = 34;    // 6: -1/2 d2 logdet / dadb
+constexpr int GT_STRIDE = 40;
+constexpr int TB_SNC = TB_GAL + NGAL * GT_STRIDE;   // SNConst
+constexpr int TB_FLOATS = TB_SNC + 20;              // 1720 floats = 6880 bytes (multiple of 16)
 
 // Per-(source, image) scalar constants used by the pixel kernels.
 struct SNConst {
@@ -81,6 +86,8 @@ struct ProblemDev {
   const double* psf_coef;        // [n_images][3][6][6]
   float* psf;                    // [n_patches][18]: per PSF comp (w, mx, my, s00, s01, s11)
   float4* pix;                   // [n_pix]: (x, fixed rate, fixed variance, log-factorial term)
+  float2* srcmom;                // [n_pix]: the target source's (E[G], Var[G]) at its last full evaluation
+  float* ptab;                   // [n_patches][TB_FLOATS] per-patch tables
   float* partials;               // [n_tiles][NACC]
   float* vpartials;              // [n_tiles]
   int* flags;                    // [S] per-source work flags
@@ -88,6 +95,7 @@ struct ProblemDev {
   unsigned long long* counters;  // [4]: full-kernel pixels, value-kernel pixels
   int S, n_patches, n_tiles, tile_pixels;
   double priors[5];
+  double log_var_r, log_var_c, log_phi, log1m_phi, logit_phi;   // logs of the priors (host-computed)
   float nu[NMIX], tau[NMIX];     // exp (0..5) then deV (6..13)
 };
 
@@ -203,11 +211,12 @@ __device__ inline void galaxy_shape(double eta, double phi, double kappa, GalSha
   Sym2 B = {sn * sn, -c * sn, c * c};
   Sym2 dA = {-2.f * c * sn, c * c - sn * sn, 2.f * c * sn};
   Sym2 d2A = {-2.f * (c * c - sn * sn), -4.f * c * sn, 2.f * (c * c - sn * sn)};
-  float de2 = 2.f * e2 * (1.f - e);
-  float d2e2 = 2.f * e2 * (1.f - e) * (2.f - 3.f * e);
+  const float em = (float)sigmoid_d(-eta);
+  float de2 = 2.f * e2 * em;
+  float d2e2 = 2.f * e2 * em * (2.f - 3.f * e);
   g.S = {s2 * (A.a + e2 * B.a), s2 * (A.b + e2 * B.b), s2 * (A.c + e2 * B.c)};
   g.d[0] = {s2 * de2 * B.a, s2 * de2 * B.b, s2 * de2 * B.c};
-  float k1 = s2 * (1.f - e2);
+  float k1 = s2 * em * (1.f + e);
   g.d[1] = {k1 * dA.a, k1 * dA.b, k1 * dA.c};
   g.d[2] = {2.f * g.S.a, 2.f * g.S.b, 2.f * g.S.c};
   g.d2[0] = {s2 * d2e2 * B.a, s2 * d2e2 * B.b, s2 * d2e2 * B.c};
@@ -219,7 +228,9 @@ __device__ inline void galaxy_shape(double eta, double phi, double kappa, GalSha
 }
 
 __device__ inline Sym2 inv2(const Sym2& S, float& logdet) {
-  float det = S.a * S.c - S.b * S.b;
+  // det = a c - b^2 with the rounding of b^2 compensated (one FMA recovers its exact error)
+  const float bb = S.b * S.b;
+  const float det = fmaf(S.a, S.c, -bb) - fmaf(S.b, S.b, -bb);
   logdet = logf(det);
   float r = 1.f / det;
   return {S.c * r, -S.b * r, S.a * r};
@@ -265,6 +276,14 @@ __device__ inline float gauss_value(const float* t, float dx, float dy) {
   return exp2f(fmaf(q, -0.5f * LOG2E, t[2]));
 }
 
+// Weight times Gaussian normaliser, w / (2 pi sqrt(det)): a few correctly rounded float32 steps
+// (det with its b^2 rounding compensated), ~2 ulp in all.
+__device__ inline float gauss_weight(float w, const Sym2& S) {
+  const float bb = S.b * S.b;
+  const float det = fmaf(S.a, S.c, -bb) - fmaf(S.b, S.b, -bb);
+  return w / (6.2831853071795865f * sqrtf(det));
+}
+
 // Bounded wait on an mbarrier phase (returns false if the budget ran out).
 __device__ inline bool mbar_wait(uint64_t* bar, uint32_t phase, long long budget_cycles) {
   uint32_t addr = (uint32_t)__cvta_generic_to_shared(bar);
@@ -289,13 +308,17 @@ __device__ inline void mbar_init(uint64_t* bar, uint32_t count) {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
+// Arrive on `bar` expecting `bytes` of asynchronous copies to complete on it.
+__device__ inline void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  uint32_t b = (uint32_t)__cvta_generic_to_shared(bar);
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes) : "memory");
+}
+
 // One-dimensional bulk copy global -> shared through the TMA unit, completing on `bar`.
 // dst/src 16-byte aligned, bytes a multiple of 16.
-__device__ inline void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+__device__ inline void bulk_copy(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
   uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
   uint32_t b = (uint32_t)__cvta_generic_to_shared(bar);
-  uint64_t state;
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;" : "=l"(state) : "r"(b), "r"(bytes) : "memory");
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(d),
                "l"(src), "r"(bytes), "r"(b)
                : "memory");

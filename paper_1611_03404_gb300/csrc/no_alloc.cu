@@ -1,6 +1,7 @@
 // celeste_elbo_batch_noalloc: ELBO + gradient + Hessian of every source of a bound problem, with the
-// kernels' scratch (per-tile partial sums, per-source work flags, counters) held in a fixed device
-// array that this file owns, so that the call itself allocates nothing.
+// kernels' scratch (per-patch tables, per-pixel source moments, per-tile partial sums, per-source
+// work flags, counters) held in a fixed device array that this file owns, so that the call itself
+// allocates nothing.
 //
 // Who needs it: callers that may not call cudaMalloc at evaluation time, for example code running
 // inside a pre-sized memory arena, a process whose allocator is owned by another framework, or a
@@ -29,10 +30,25 @@ static void* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
 
 static size_t round256(size_t x) { return (x + 255) & ~size_t(255); }
 
-// Bytes of the array used by a problem: partial sums, flags, counters.
-static size_t noalloc_bytes(const celeste_problem* p) {
-  return round256(sizeof(float) * NACC * p->tiles.size()) + round256(sizeof(int) * p->S) +
-         round256(sizeof(unsigned long long) * 4);
+// Layout of the array for one problem: partial sums, flags, counters, tables, source moments.
+struct NoallocLayout {
+  size_t partials, flags, counters, ptab, srcmom, total;
+};
+static NoallocLayout noalloc_layout(const celeste_problem* p) {
+  NoallocLayout L;
+  size_t o = 0;
+  L.partials = o;
+  o += round256(sizeof(float) * NACC * p->tiles.size());
+  L.flags = o;
+  o += round256(sizeof(int) * p->S);
+  L.counters = o;
+  o += round256(sizeof(unsigned long long) * 4);
+  L.ptab = o;
+  o += round256(sizeof(float) * TB_FLOATS * p->patches.size());
+  L.srcmom = o;
+  o += round256(sizeof(float2) * (size_t)p->n_pix);
+  L.total = o;
+  return L;
 }
 
 // Device address of the array on the current device (looked up once per device).
@@ -60,11 +76,12 @@ extern "C" int celeste_elbo_batch_noalloc(celeste_problem* p, const double* thet
                                           double* hess, celeste_stream_t stream) {
   if (!p) return fail(CELESTE_ERR_INVALID_ARG, "null problem");
   if (!theta || !elbo || !grad || !hess) return fail(CELESTE_ERR_INVALID_ARG, "theta and all three outputs are required");
-  const size_t need = noalloc_bytes(p);
-  if (need > NOALLOC_SCRATCH_BYTES)
+  const NoallocLayout NL = noalloc_layout(p);
+  if (NL.total > NOALLOC_SCRATCH_BYTES)
     return fail(CELESTE_ERR_INVALID_ARG,
-                "problem needs %zu bytes of scratch (%zu tiles, %d sources); the fixed array holds %zu bytes", need,
-                p->tiles.size(), p->S, NOALLOC_SCRATCH_BYTES);
+                "problem needs %zu bytes of scratch (%zu tiles, %zu patches, %lld pixels, %d sources); the fixed "
+                "array holds %zu bytes",
+                NL.total, p->tiles.size(), p->patches.size(), p->n_pix, p->S, NOALLOC_SCRATCH_BYTES);
   if (!p->bound || !p->background_ready)
     return fail(CELESTE_ERR_STATE, "bind the problem and render the background first");
   void* base = nullptr;
@@ -72,13 +89,14 @@ extern "C" int celeste_elbo_batch_noalloc(celeste_problem* p, const double* thet
   if (rc != CELESTE_OK) return rc;
   char* b = static_cast<char*>(base);
   ProblemDev D = p->dev;   // inputs from the bound problem, scratch from the fixed array
-  D.partials = reinterpret_cast<float*>(b);
-  D.flags = reinterpret_cast<int*>(b + round256(sizeof(float) * NACC * p->tiles.size()));
-  D.counters = reinterpret_cast<unsigned long long*>(b + round256(sizeof(float) * NACC * p->tiles.size()) +
-                                                     round256(sizeof(int) * p->S));
+  D.partials = reinterpret_cast<float*>(b + NL.partials);
+  D.flags = reinterpret_cast<int*>(b + NL.flags);
+  D.counters = reinterpret_cast<unsigned long long*>(b + NL.counters);
+  D.ptab = reinterpret_cast<float*>(b + NL.ptab);
+  D.srcmom = reinterpret_cast<float2*>(b + NL.srcmom);
   cudaStream_t st = (cudaStream_t)stream;
-  // The array keeps the previous call's contents: the counters must start at zero; the flags and
-  // the partial sums are fully rewritten below before they are read.
+  // The array keeps the previous call's contents: the counters must start at zero; the flags,
+  // tables, source moments and partial sums are fully rewritten below before they are read.
   cudaError_t e = cudaMemsetAsync(D.counters, 0, sizeof(unsigned long long) * 4, st);
   if (e != cudaSuccess) return cuda_fail(e, "clear counters");
   if ((e = launch_set_flags(D, FLAG_FULL, st)) != cudaSuccess) return cuda_fail(e, "set flags");

@@ -113,7 +113,7 @@ extern "C" int celeste_problem_create(const celeste_problem_desc* d, celeste_pro
   *out = nullptr;
   if (d->n_images <= 0 || !d->images) return fail(CELESTE_ERR_INVALID_ARG, "n_images must be > 0");
   if (d->n_sources <= 0 || !d->u0 || !d->radius) return fail(CELESTE_ERR_INVALID_ARG, "n_sources must be > 0");
-  int tp = d->tile_pixels ? d->tile_pixels : 256;
+  int tp = d->tile_pixels ? d->tile_pixels : 128;
   if (tp != 128 && tp != 256 && tp != 512 && tp != 1024)
     return fail(CELESTE_ERR_INVALID_ARG, "tile_pixels must be 128, 256, 512 or 1024");
   for (int n = 0; n < d->n_images; ++n) {
@@ -287,6 +287,8 @@ void build_layout(celeste_problem* p) {
   L.psf_coef = take(sizeof(double) * p->psf_coef.size());
   L.psf = take(sizeof(float) * 18 * std::max(NPch, 1));
   L.pix = take(sizeof(float4) * std::max<long long>(p->n_pix, 1));
+  L.srcmom = take(sizeof(float2) * std::max<long long>(p->n_pix, 1));
+  L.ptab = take(sizeof(float) * TB_FLOATS * std::max(NPch, 1));
   L.partials = take(sizeof(float) * NACC * std::max<size_t>(p->tiles.size(), 1));
   L.vpartials = take(sizeof(float) * std::max<size_t>(p->tiles.size(), 1));
   L.flags = take(sizeof(int) * S);
@@ -356,6 +358,8 @@ extern "C" int celeste_problem_bind(celeste_problem* p, void* workspace, size_t 
   D.psf_coef = reinterpret_cast<const double*>(base + L.psf_coef);
   D.psf = reinterpret_cast<float*>(base + L.psf);
   D.pix = reinterpret_cast<float4*>(base + L.pix);
+  D.srcmom = reinterpret_cast<float2*>(base + L.srcmom);
+  D.ptab = reinterpret_cast<float*>(base + L.ptab);
   D.partials = reinterpret_cast<float*>(base + L.partials);
   D.vpartials = reinterpret_cast<float*>(base + L.vpartials);
   D.flags = reinterpret_cast<int*>(base + L.flags);
@@ -366,6 +370,11 @@ extern "C" int celeste_problem_bind(celeste_problem* p, void* workspace, size_t 
   D.n_tiles = (int)p->tiles.size();
   D.tile_pixels = p->tile_pixels;
   std::memcpy(D.priors, p->priors, sizeof(D.priors));
+  D.log_var_r = std::log(p->priors[2]);
+  D.log_var_c = std::log(p->priors[4]);
+  D.log_phi = std::log(p->priors[0]);
+  D.log1m_phi = std::log1p(-p->priors[0]);
+  D.logit_phi = D.log_phi - D.log1m_phi;
   std::memcpy(D.nu, p->nu, sizeof(D.nu));
   std::memcpy(D.tau, p->tau, sizeof(D.tau));
   p->base = base;

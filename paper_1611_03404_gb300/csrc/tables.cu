@@ -1,0 +1,126 @@
+// Per-(source, image) tables for the pixel kernels, computed once per evaluation and patch.
+//
+// For the source's current parameters, each of the 45 profile components of the patch (3 star =
+// PSF components; 42 galaxy = 3 PSF x (6 exponential + 8 de Vaucouleurs) mixture components) gets
+// its precision matrix and weighted normaliser and, for the galaxy components, the first and second
+// derivatives of both w.r.t. (logit axis ratio, angle, log scale):
+//   Sigma_kj = tau_j A Sigma_g A^T + S_k,   P = Sigma^-1,
+//   dP = -P dSigma P,  d2P = P dSa P dSb P + P dSb P dSa P - P d2S P,
+//   d logdet = tr(P dSigma),  d2 logdet = tr(P d2S) - tr(P dSa P dSb),
+// with Sigma_g = scale^2 R(angle) diag(1, axis^2) R(angle)^T (the galaxy shape of the paper's
+// Sec. "The Celeste Model") mapped to pixels by the WCS matrix A.  Also the per-patch brightness
+// constants (lognormal moments of the band flux times the type probabilities).
+#include "celeste_internal.cuh"
+#include "kernels.h"
+
+namespace celeste {
+
+// Galaxy shape derivatives in float32 from float64 parameters (angle reduced first).
+__device__ inline void galaxy_shape_f(double eta, double phi, double kappa, GalShape& g) {
+  const double two_pi = 6.283185307179586;
+  const float ph = (float)(phi - two_pi * rint(phi / two_pi));
+  // e = sigmoid(eta) and 1 - e = sigmoid(-eta), each evaluated directly (no cancellation in 1 - e)
+  const float e = 1.f / (1.f + expf(-(float)eta)), em = 1.f / (1.f + expf((float)eta)), e2 = e * e;
+  const float s2 = expf(2.f * (float)kappa);
+  float sn, c;
+  sincosf(ph, &sn, &c);
+  Sym2 A = {c * c, c * sn, sn * sn};
+  Sym2 B = {sn * sn, -c * sn, c * c};
+  Sym2 dA = {-2.f * c * sn, c * c - sn * sn, 2.f * c * sn};
+  Sym2 d2A = {-2.f * (c * c - sn * sn), -4.f * c * sn, 2.f * (c * c - sn * sn)};
+  float de2 = 2.f * e2 * em;
+  float d2e2 = 2.f * e2 * em * (2.f - 3.f * e);
+  g.S = {s2 * (A.a + e2 * B.a), s2 * (A.b + e2 * B.b), s2 * (A.c + e2 * B.c)};
+  g.d[0] = {s2 * de2 * B.a, s2 * de2 * B.b, s2 * de2 * B.c};
+  float k1 = s2 * em * (1.f + e);   // s2 (1 - e^2)
+  g.d[1] = {k1 * dA.a, k1 * dA.b, k1 * dA.c};
+  g.d[2] = {2.f * g.S.a, 2.f * g.S.b, 2.f * g.S.c};
+  g.d2[0] = {s2 * d2e2 * B.a, s2 * d2e2 * B.b, s2 * d2e2 * B.c};
+  g.d2[1] = {-s2 * de2 * dA.a, -s2 * de2 * dA.b, -s2 * de2 * dA.c};
+  g.d2[2] = {2.f * g.d[0].a, 2.f * g.d[0].b, 2.f * g.d[0].c};
+  g.d2[3] = {k1 * d2A.a, k1 * d2A.b, k1 * d2A.c};
+  g.d2[4] = {2.f * g.d[1].a, 2.f * g.d[1].b, 2.f * g.d[1].c};
+  g.d2[5] = {4.f * g.S.a, 4.f * g.S.b, 4.f * g.S.c};
+}
+
+// full = 1: galaxy derivative entries too; full = 0: precision and normaliser only.
+__global__ void __launch_bounds__(64) table_kernel(ProblemDev P, const double* __restrict__ theta, int flag_mask,
+                                                  int full) {
+  const int patch = blockIdx.x;
+  const PatchDev pt = P.patches[patch];
+  if (!(P.flags[pt.source] & flag_mask)) return;
+  const int tid = threadIdx.x;
+  const ImageDev im = P.images[pt.image];
+  const double* th = theta + (size_t)pt.source * NP;
+  float* out = P.ptab + (size_t)patch * TB_FLOATS;
+  const float* psf = P.psf + (size_t)patch * 18;
+  if (tid < NGAL) {
+    const int k = tid / NMIX, j = tid % NMIX;
+    const PsfComp pc = load_psf(psf, k);
+    GalShape gs;
+    galaxy_shape_f(th[3], th[4], th[5], gs);
+    const float A[4] = {(float)im.A[0], (float)im.A[1], (float)im.A[2], (float)im.A[3]};
+    const float tau = P.tau[j], nu = P.nu[j];
+    const Sym2 Sp = congruence(A, gs.S);
+    const Sym2 S = {tau * Sp.a + pc.S.a, tau * Sp.b + pc.S.b, tau * Sp.c + pc.S.c};
+    float ld;
+    const Sym2 Pm = inv2(S, ld);
+    float* e = out + TB_GAL + tid * GT_STRIDE;
+    e[GT_P + 0] = Pm.a;
+    e[GT_P + 1] = Pm.b;
+    e[GT_P + 2] = Pm.c;
+    e[GT_W] = gauss_weight(pc.w * nu, S);
+    if (full) {
+      Mat2 PdS[3];
+      for (int a = 0; a < 3; ++a) {
+        const Sym2 t = congruence(A, gs.d[a]);
+        PdS[a] = mul(Pm, Sym2{tau * t.a, tau * t.b, tau * t.c});
+        const Sym2 dP = to_sym(mul(PdS[a], Pm));   // P dS P = -dP/da
+        e[GT_QA + 3 * a + 0] = 0.5f * dP.a;
+        e[GT_QA + 3 * a + 1] = 0.5f * dP.b;
+        e[GT_QA + 3 * a + 2] = 0.5f * dP.c;
+        e[GT_LA + a] = -0.5f * trace(PdS[a]);
+      }
+      int q = 0;
+      for (int a = 0; a < 3; ++a)
+        for (int b = a; b < 3; ++b, ++q) {
+          const Sym2 t = congruence(A, gs.d2[q]);
+          const Sym2 d2S = {tau * t.a, tau * t.b, tau * t.c};
+          const Mat2 X = mul(PdS[a], PdS[b]);
+          const Sym2 two = sym_plus_t(mul(X, Pm));
+          const Mat2 Pd2 = mul(Pm, d2S);
+          const Sym2 third = to_sym(mul(Pd2, Pm));
+          e[GT_QAB + 3 * q + 0] = -0.5f * (two.a - third.a);
+          e[GT_QAB + 3 * q + 1] = -0.5f * (two.b - third.b);
+          e[GT_QAB + 3 * q + 2] = -0.5f * (two.c - third.c);
+          e[GT_LAB + q] = -0.5f * (trace(Pd2) - trace(X));
+        }
+    }
+  } else if (tid < NGAL + NSTAR) {
+    const int k = tid - NGAL;
+    const PsfComp pc = load_psf(psf, k);
+    double px, py;
+    source_pixel_pos(im, th, pt.x0, pt.y0, px, py);
+    float ld;
+    const Sym2 Pm = inv2(pc.S, ld);
+    out[TB_MU + 2 * k + 0] = (float)(px + pc.mx);
+    out[TB_MU + 2 * k + 1] = (float)(py + pc.my);
+    out[TB_STAR + 4 * k + 0] = gauss_weight(pc.w, pc.S);
+    out[TB_STAR + 4 * k + 1] = Pm.a;
+    out[TB_STAR + 4 * k + 2] = Pm.b;
+    out[TB_STAR + 4 * k + 3] = Pm.c;
+  } else if (tid == NGAL + NSTAR) {
+    SNConst c;
+    sn_constants(th, im.band, im.iota, c);
+    const float* cf = reinterpret_cast<const float*>(&c);
+    for (int q = 0; q < (int)(sizeof(SNConst) / sizeof(float)); ++q) out[TB_SNC + q] = cf[q];
+  }
+}
+
+cudaError_t launch_tables(const ProblemDev& P, const double* theta, int flag_mask, bool full, cudaStream_t st) {
+  if (P.n_patches == 0) return cudaSuccess;
+  table_kernel<<<P.n_patches, 64, 0, st>>>(P, theta, flag_mask, full ? 1 : 0);
+  return cudaGetLastError();
+}
+
+}  // namespace celeste

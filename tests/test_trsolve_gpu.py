@@ -1,0 +1,79 @@
+"""Trust-region subproblem on the GPU (float64, tridiagonal route) vs the oracle (eigendecomposition
+route), through the C ABI.  The solution of the subproblem is unique outside the hard case, so the
+steps must agree to float64 accuracy; the hard case is checked by its optimality conditions."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import celeste_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1611_03404_gb300 as pkg
+    return pkg
+
+
+def _problems(seed, n):
+    rng = np.random.default_rng(seed)
+    Bs, gs, ds = [], [], []
+    for t in range(n):
+        M = rng.normal(size=(27, 27))
+        shift = rng.uniform(-1.5, 0.5) if t % 3 else 0.0
+        B = M @ M.T / 27 + shift * np.eye(27)
+        if t % 5 == 0:      # badly scaled, like a Hessian over positions, shapes and log-variances
+            s = np.exp(rng.uniform(-4, 4, 27))
+            B = s[:, None] * B * s[None, :]
+        Bs.append(B)
+        gs.append(rng.normal(size=27) * rng.choice([1e-3, 1.0, 100.0]))
+        ds.append(rng.choice([0.01, 0.3, 1.0, 10.0, 1e4]))
+    return np.array(Bs), np.array(gs), np.array(ds)
+
+
+def test_subproblem_matches_oracle(P):
+    B, g, d = _problems(0, 400)
+    dev = torch.device("cuda:0")
+    p, pred, hard = P.tr_solve_batch(*(torch.as_tensor(a, device=dev).contiguous() for a in (B, g, d)))
+    p, pred = p.cpu().numpy(), pred.cpu().numpy()
+    for i in range(len(d)):
+        pr, predr, _ = O.tr_subproblem(g[i], B[i], d[i])
+        assert np.linalg.norm(p[i]) <= d[i] * (1 + 1e-9)
+        # both solutions must reach the same minimum of the model (to 1e-7: next to the pole
+        # lambda = -lambda_min, where |p| ~ 1/(lambda + lambda_min), each solver resolves the step
+        # to ~1e-8)
+        mg = g[i] @ p[i] + 0.5 * p[i] @ B[i] @ p[i]
+        mo = g[i] @ pr + 0.5 * pr @ B[i] @ pr
+        assert mg <= mo + 1e-7 * abs(mo) + 1e-300, i
+        assert abs(pred[i] + mg) <= 1e-9 * abs(mg) + 1e-300
+        # the step itself is compared where the subproblem is well conditioned: lambda* well above
+        # the pole -lambda_min (|p| ~ 1/(lambda + lambda_min) amplifies rounding near it)
+        lam_star = -(g[i] @ pr + pr @ B[i] @ pr) / max(pr @ pr, 1e-300)
+        lmin = np.linalg.eigvalsh(B[i])[0]
+        scale = np.abs(np.linalg.eigvalsh(B[i])).max()
+        if np.linalg.norm(pr) < d[i] * (1 - 1e-9) or lam_star + lmin > 1e-6 * scale:
+            assert np.abs(p[i] - pr).max() <= 1e-6 * max(np.abs(pr).max(), 1e-300), i
+
+
+def test_subproblem_hard_case(P):
+    rng = np.random.default_rng(4)
+    Q, _ = np.linalg.qr(rng.normal(size=(27, 27)))
+    lam = np.linspace(-2.0, 5.0, 27)
+    B = Q @ np.diag(lam) @ Q.T
+    g = Q[:, 1:] @ rng.normal(size=26) * 0.1     # no component on the most negative eigenvector
+    delta = 5.0
+    dev = torch.device("cuda:0")
+    t = lambda a: torch.as_tensor(a, device=dev).contiguous()
+    p, pred, hard = P.tr_solve_batch(t(B[None]), t(g[None]), t(np.array([delta])))
+    p = p.cpu().numpy()[0]
+    assert int(hard[0]) == 1
+    assert abs(np.linalg.norm(p) - delta) <= 1e-9 * delta
+    # optimality: (B - lambda_min I) p = -g
+    np.testing.assert_allclose((B + 2.0 * np.eye(27)) @ p, -g, atol=1e-7)
+    pr, _, hr = O.tr_subproblem(g, B, delta)
+    assert hr and abs(pr @ B @ pr / 2 + g @ pr - (p @ B @ p / 2 + g @ p)) <= 1e-9 * (1 + abs(g @ pr))
