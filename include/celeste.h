@@ -117,6 +117,10 @@ typedef struct {
   double delta_max;   /* 1e4 */
   double eta;         /* 0.1: acceptance threshold on actual/predicted reduction */
   double delta_min;   /* 1e-12: below this the source stops with RADIUS_COLLAPSE */
+  int32_t graph_iters; /* 4: Newton iterations captured in one CUDA graph and run between two
+                          host checks of the active count; 1: plain launches, one check per
+                          iteration.  Iterations after the last source stops launch kernels
+                          that find empty worklists and change nothing. */
 } celeste_newton_opts;
 
 /* Validate the description and build the host-side layout (patches, neighbours, work
@@ -157,7 +161,9 @@ int celeste_elbo_batch(celeste_problem* p, const double* theta, unsigned want,
  *   delta_inout: device float64 [S] trust radius (<= 0 means opts->delta0); the final radius
  *                is written back, so a later call resumes where this one stopped.
  *   iters_out, status_out: device int32 [S]; elbo_out: device float64 [S] (may be NULL).
- * The host waits on `stream` once per iteration to test whether any source is still active. */
+ * The iterations run as CUDA graphs of opts->graph_iters iterations (captured on a stream private
+ * to the problem, launched on `stream`, kept for later calls with the same arguments); the host
+ * waits on `stream` after each graph to test whether any source is still active. */
 int celeste_newton_batch(celeste_problem* p, double* theta_inout, const celeste_newton_opts* opts,
                          double* delta_inout, int32_t* iters_out, int32_t* status_out,
                          double* elbo_out, celeste_stream_t stream);
@@ -196,14 +202,15 @@ int celeste_profile_stop(celeste_problem* p, celeste_profile_stats* out);
  * not allocate device memory when they evaluate (a pre-sized arena, an allocator owned by another
  * framework, a request path that must not allocate).  The call allocates nothing: the kernels'
  * scratch (per-patch tables, per-pixel source moments, per-tile partial sums, per-source flags,
- * counters) lives in one fixed 8 MiB device array inside this library, which every GPU that loads
+ * worklists, counters) lives in one fixed 8 MiB device array inside this library, which every GPU that loads
  * the library keeps until the process exits.
  * The paper has no counterpart; it is a deployment variant of the evaluation above.
  *   p must be bound and have its background rendered; theta, elbo, grad, hess as in
  *   celeste_elbo_batch (all four required).
- *   Limit: 432 * n_tiles + 4 * n_sources + 6880 * n_patches + 8 * n_pixels bytes (each rounded
- *   up to 256) plus 256 must fit in 8 MiB (e.g. ~1000 patches of 17 x 17 pixels); larger problems
- *   get CELESTE_ERR_INVALID_ARG before any launch.
+ *   Limit: 432 * n_tiles, 4 * n_sources, 6880 * n_patches, 8 * n_pixels and
+ *   4 * (n_tiles + n_patches + n_sources) bytes, each rounded up to 256, plus 512 must fit in
+ *   8 MiB (e.g. ~1000 patches of 17 x 17 pixels); larger problems get CELESTE_ERR_INVALID_ARG
+ *   before any launch.
  *   The first call on a device looks up the array's device address with that device current;
  *   make that first call before any stream capture.
  *   Every call shares the one array: calls that overlap on the GPU (different streams, threads

@@ -39,7 +39,7 @@ class ProblemDesc(ctypes.Structure):
 class NewtonOpts(ctypes.Structure):
     _fields_ = [("max_iter", ctypes.c_int32), ("ftol", ctypes.c_double), ("gtol", ctypes.c_double),
                 ("delta0", ctypes.c_double), ("delta_max", ctypes.c_double), ("eta", ctypes.c_double),
-                ("delta_min", ctypes.c_double)]
+                ("delta_min", ctypes.c_double), ("graph_iters", ctypes.c_int32)]
 
 
 class ProfileStats(ctypes.Structure):
@@ -177,7 +177,7 @@ class Problem:
         return elbo, grad, hess
 
     def newton_batch(self, theta, delta=None, max_iter=50, ftol=1e-8, gtol=1e-10, delta0=1.0, delta_max=1e4,
-                     eta=0.1, delta_min=1e-12, stream=None):
+                     eta=0.1, delta_min=1e-12, graph_iters=4, stream=None):
         """Runs trust-region Newton in place on `theta`; returns (delta, iters, status, elbo)."""
         assert theta.dtype == torch.float64 and theta.is_contiguous() and theta.shape == (self.S, NPARAM)
         dev = theta.device
@@ -186,7 +186,7 @@ class Problem:
         iters = torch.zeros(self.S, dtype=torch.int32, device=dev)
         status = torch.zeros(self.S, dtype=torch.int32, device=dev)
         elbo = torch.empty(self.S, dtype=torch.float64, device=dev)
-        opts = NewtonOpts(max_iter, ftol, gtol, delta0, delta_max, eta, delta_min)
+        opts = NewtonOpts(max_iter, ftol, gtol, delta0, delta_max, eta, delta_min, graph_iters)
         _check(lib().celeste_newton_batch(self.handle, _ptr(theta), ctypes.byref(opts), _ptr(delta), _ptr(iters),
                                           _ptr(status), _ptr(elbo), _stream(stream)))
         return delta, iters, status, elbo

@@ -31,15 +31,16 @@ extern "C" int celeste_elbo_batch(celeste_problem* p, const double* theta, unsig
   const int flag = full ? FLAG_FULL : FLAG_VALUE;
   cudaError_t e = launch_set_flags(p->dev, flag, st);
   if (e != cudaSuccess) return cuda_fail(e, "set flags");
+  if ((e = launch_worklists(p->dev, flag, st)) != cudaSuccess) return cuda_fail(e, "worklists");
   const int m0 = prof_mark(p, st);
-  e = full ? launch_full(p->dev, theta, st) : launch_value(p->dev, theta, flag, false, st);
+  e = full ? launch_full(p->dev, theta, st) : launch_value(p->dev, theta, false, st);
   if (e != cudaSuccess) return cuda_fail(e, "pixel kernel");
   const int m1 = prof_mark(p, st);
   if (p->prof_on) (full ? p->prof_full : p->prof_value).push_back({m0, m1});
-  prof_count(p, 3);
-  e = full ? launch_assemble(p->dev, theta, true, flag, (want & CELESTE_WANT_ELBO) ? elbo : nullptr,
+  prof_count(p, 5);
+  e = full ? launch_assemble(p->dev, theta, true, (want & CELESTE_WANT_ELBO) ? elbo : nullptr,
                              (want & CELESTE_WANT_GRAD) ? grad : nullptr, (want & CELESTE_WANT_HESS) ? hess : nullptr, st)
-           : launch_assemble_value(p->dev, theta, nullptr, flag, elbo, st);
+           : launch_assemble_value(p->dev, theta, nullptr, elbo, st);
   if (e != cudaSuccess) return cuda_fail(e, "assemble kernel");
   return CELESTE_OK;
 }

@@ -9,6 +9,8 @@
 // GB300 float64 latencies are long (a dependent FMA ~64 cycles, exp ~1100), so every
 // transcendental is evaluated once per source and in parallel across threads; the per-patch
 // work is plain multiply-adds spread over the CTA.
+#include <algorithm>
+
 #include "celeste_internal.cuh"
 #include "kernels.h"
 
@@ -96,9 +98,9 @@ struct PatchLift {
 };
 
 __global__ void __launch_bounds__(128) assemble_kernel(ProblemDev P, const double* __restrict__ theta, int full,
-                                                       int flag_mask, double* elbo, double* grad, double* hess) {
-  const int s = blockIdx.x;
-  if (!(P.flags[s] & flag_mask)) return;
+                                                       double* elbo, double* grad, double* hess) {
+  const int n_items = P.wl_count[WL_SOURCES];
+  const int* items = wl_list(P, WL_SOURCES);
   const int tid = threadIdx.x, nt = blockDim.x;
   __shared__ double sums[NACC];
   __shared__ double Hs[NP * NP], gs[NP], HE[NP * NP], gE[NP];
@@ -107,6 +109,8 @@ __global__ void __launch_bounds__(128) assemble_kernel(ProblemDev P, const doubl
   __shared__ PatchLift c;
   __shared__ SourceConst sc;
   __shared__ double Lsum, red[16];
+  for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
+  const int s = items[w];
   const double* th = theta + (size_t)s * NP;
   for (int i = tid; i < NP * NP; i += nt) Hs[i] = 0.0;
   for (int i = tid; i < NP; i += nt) gs[i] = 0.0;
@@ -351,14 +355,20 @@ __global__ void __launch_bounds__(128) assemble_kernel(ProblemDev P, const doubl
       grad[(size_t)s * NP + j] = gs[j] - gk;
     }
   }
+  __syncthreads();   // shared state is reused by the next source
+  }
 }
 
 // Value-only assembly, one warp per source: sum of the value tile sums minus the KL at theta
 // (plus the KL at theta_ref when the pixel sums are differences from theta_ref).
 __global__ void assemble_value_kernel(ProblemDev P, const double* __restrict__ theta, const double* __restrict__ theta_ref,
-                                      int flag_mask, double* out) {
-  const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  if (s >= P.S || !(P.flags[s] & flag_mask)) return;   // warp-uniform
+                                      double* out) {
+  const int n_items = P.wl_count[WL_SOURCES];
+  const int* items = wl_list(P, WL_SOURCES);
+  const int lane = threadIdx.x & 31;
+  const int nwarps = gridDim.x * (blockDim.x >> 5);
+  for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < n_items; w += nwarps) {   // warp-uniform
+  const int s = items[w];
   double v = 0.0;
   for (int p = P.src_patch[s]; p < P.src_patch[s + 1]; ++p) {
     const PatchDev& pt = P.patches[p];
@@ -368,7 +378,7 @@ __global__ void assemble_value_kernel(ProblemDev P, const double* __restrict__ t
   const int which = lane >> 4, k = lane & 15;
   const double* th = which ? theta_ref : theta;
   if (th && k <= 10) {
-    th += (size_t)s * NP;
+    th += (size_t)s * NP;   // (per-lane pointer; th is reset each source)
     const double al = th[6], e = exp(-fabs(al)), sg = 1.0 / (1.0 + e);
     const double a1 = al >= 0 ? sg : e * sg, a0 = al >= 0 ? e * sg : sg;
     double klp;
@@ -388,13 +398,14 @@ __global__ void assemble_value_kernel(ProblemDev P, const double* __restrict__ t
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   if (lane == 0) out[s] = v;
+  }
 }
 
-cudaError_t launch_assemble_value(const ProblemDev& P, const double* theta, const double* theta_ref, int flag_mask,
-                                  double* out, cudaStream_t st) {
+cudaError_t launch_assemble_value(const ProblemDev& P, const double* theta, const double* theta_ref, double* out,
+                                  cudaStream_t st) {
   const int warps_per_block = 4;
-  assemble_value_kernel<<<(P.S + warps_per_block - 1) / warps_per_block, 32 * warps_per_block, 0, st>>>(
-      P, theta, theta_ref, flag_mask, out);
+  const int blocks = std::max(1, std::min((P.S + warps_per_block - 1) / warps_per_block, P.n_sm * 8));
+  assemble_value_kernel<<<blocks, 32 * warps_per_block, 0, st>>>(P, theta, theta_ref, out);
   return cudaGetLastError();
 }
 
@@ -403,9 +414,56 @@ __global__ void set_flags_kernel(int* flags, int S, int value) {
   if (s < S) flags[s] = value;
 }
 
-cudaError_t launch_assemble(const ProblemDev& P, const double* theta, bool full, int flag_mask, double* elbo,
-                            double* grad, double* hess, cudaStream_t st) {
-  assemble_kernel<<<P.S, 128, 0, st>>>(P, theta, full ? 1 : 0, flag_mask, elbo, grad, hess);
+// Worklists of the tiles, patches and sources whose source's flags match `mask` (warp-aggregated
+// appends; the order inside a list is not significant: results are indexed by item).
+__global__ void worklist_kernel(ProblemDev P, int mask) {
+  int* lists[3] = {wl_list(P, WL_TILES), wl_list(P, WL_PATCHES), wl_list(P, WL_SOURCES)};
+  const int lane = threadIdx.x & 31;
+  const int total = P.n_tiles + P.n_patches + P.S;
+  for (int base = blockIdx.x * blockDim.x; base < total; base += gridDim.x * blockDim.x) {
+    const int i = base + threadIdx.x;
+    int which = -1, item = 0;
+    bool act = false;
+    if (i < P.n_tiles) {
+      which = WL_TILES;
+      item = i;
+      act = (P.flags[P.patches[P.tiles[i].patch].source] & mask) != 0;
+    } else if (i < P.n_tiles + P.n_patches) {
+      which = WL_PATCHES;
+      item = i - P.n_tiles;
+      act = (P.flags[P.patches[item].source] & mask) != 0;
+    } else if (i < total) {
+      which = WL_SOURCES;
+      item = i - P.n_tiles - P.n_patches;
+      act = (P.flags[item] & mask) != 0;
+    }
+#pragma unroll
+    for (int w = 0; w < 3; ++w) {
+      const bool mine = act && which == w;
+      const unsigned m = __ballot_sync(0xffffffffu, mine);
+      if (!m) continue;
+      const int leader = __ffs(m) - 1;
+      int pos = 0;
+      if (lane == leader) pos = atomicAdd(P.wl_count + w, __popc(m));
+      pos = __shfl_sync(0xffffffffu, pos, leader);
+      if (mine) lists[w][pos + __popc(m & ((1u << lane) - 1u))] = item;
+    }
+  }
+}
+
+cudaError_t launch_worklists(const ProblemDev& P, int mask, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(P.wl_count, 0, sizeof(int) * 4, st);
+  if (e != cudaSuccess) return e;
+  const int total = P.n_tiles + P.n_patches + P.S;
+  const int blocks = std::max(1, std::min((total + 255) / 256, P.n_sm * 4));
+  worklist_kernel<<<blocks, 256, 0, st>>>(P, mask);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_assemble(const ProblemDev& P, const double* theta, bool full, double* elbo, double* grad,
+                            double* hess, cudaStream_t st) {
+  const int blocks = std::max(1, std::min(P.S, P.n_sm * 4));
+  assemble_kernel<<<blocks, 128, 0, st>>>(P, theta, full ? 1 : 0, elbo, grad, hess);
   return cudaGetLastError();
 }
 

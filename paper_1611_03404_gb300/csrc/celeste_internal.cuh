@@ -75,6 +75,9 @@ struct TileDev {
   int patch, start, count, pad;
 };
 
+// Worklists (offsets into ProblemDev::wl and indices of ProblemDev::wl_count).
+constexpr int WL_TILES = 0, WL_PATCHES = 1, WL_SOURCES = 2;
+
 // Device view of a bound problem (passed by value to kernels).
 struct ProblemDev {
   const ImageDev* images;
@@ -91,13 +94,19 @@ struct ProblemDev {
   float* partials;               // [n_tiles][NACC]
   float* vpartials;              // [n_tiles]
   int* flags;                    // [S] per-source work flags
+  int* wl;                       // worklists built from the flags: tiles [n_tiles], patches [n_patches], sources [S]
+  int* wl_count;                 // [4]: number of tiles, patches, sources in the worklists
   int* err;                      // [4] device error words
   unsigned long long* counters;  // [4]: full-kernel pixels, value-kernel pixels
-  int S, n_patches, n_tiles, tile_pixels;
+  int S, n_patches, n_tiles, tile_pixels, n_sm;
   double priors[5];
   double log_var_r, log_var_c, log_phi, log1m_phi, logit_phi;   // logs of the priors (host-computed)
   float nu[NMIX], tau[NMIX];     // exp (0..5) then deV (6..13)
 };
+
+__device__ inline int* wl_list(const ProblemDev& P, int which) {
+  return P.wl + (which == WL_TILES ? 0 : which == WL_PATCHES ? P.n_tiles : P.n_tiles + P.n_patches);
+}
 
 // Work flags per source.
 constexpr int FLAG_FULL = 1;     // evaluate value + gradient + Hessian
@@ -306,6 +315,12 @@ __device__ inline void mbar_init(uint64_t* bar, uint32_t count) {
   uint32_t addr = (uint32_t)__cvta_generic_to_shared(bar);
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(addr), "r"(count) : "memory");
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Orders this thread's earlier generic-proxy accesses to shared memory before later async-proxy
+// (bulk copy) accesses; issued before a bulk copy overwrites a buffer that was just read.
+__device__ inline void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
 // Arrive on `bar` expecting `bytes` of asynchronous copies to complete on it.

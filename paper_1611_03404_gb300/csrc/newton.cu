@@ -6,7 +6,9 @@
 // solved in float64 the More-Sorensen way (trsolve.cuh: tridiagonal reduction, Sturm
 // multisection, safeguarded Newton on 1/|p(lambda)| - 1/delta, hard case).  The outer iteration
 // follows Nocedal & Wright Algorithm 4.1.
+#include <algorithm>
 #include <cmath>
+#include <cstring>
 
 #include "celeste_internal.cuh"
 #include "kernels.h"
@@ -195,6 +197,37 @@ __global__ void newton_finish_kernel(NewtonDev N, int32_t* iters, int32_t* statu
   if (elbo) elbo[s] = N.L[s];
 }
 
+// Kernels launched by one Newton iteration (newton_iteration below).
+constexpr int NEWTON_KERNELS_PER_ITER = 10;
+
+// The launches of one Newton iteration: subproblem step, value at the trial point, accept/reject,
+// full evaluation at the accepted points.  ev (4 events, or null) brackets the value and the full
+// evaluation; inside a stream capture they become event-record nodes.
+static cudaError_t newton_iteration(const ProblemDev& D, const NewtonDev& N, cudaStream_t st, cudaEvent_t* ev,
+                                    bool capturing) {
+  auto mark = [&](int k) -> cudaError_t {
+    if (!ev) return cudaSuccess;
+    return capturing ? cudaEventRecordWithFlags(ev[k], st, cudaEventRecordExternal) : cudaEventRecord(ev[k], st);
+  };
+  const int S = N.S;
+  cudaError_t e;
+  tr_step_kernel<<<(S + TR_WARPS - 1) / TR_WARPS, 32 * TR_WARPS, 0, st>>>(N, D.flags);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = launch_worklists(D, FLAG_VALUE, st)) != cudaSuccess) return e;
+  if ((e = mark(0)) != cudaSuccess) return e;
+  if ((e = launch_value(D, N.trial, true, st)) != cudaSuccess) return e;
+  if ((e = mark(1)) != cudaSuccess) return e;
+  if ((e = launch_assemble_value(D, N.trial, N.theta, N.Ltrial, st)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(N.count, 0, sizeof(int), st)) != cudaSuccess) return e;
+  tr_update_kernel<<<(S + 127) / 128, 128, 0, st>>>(N, D.flags);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = launch_worklists(D, FLAG_FULL, st)) != cudaSuccess) return e;
+  if ((e = mark(2)) != cudaSuccess) return e;
+  if ((e = launch_full(D, N.theta, st)) != cudaSuccess) return e;
+  if ((e = mark(3)) != cudaSuccess) return e;
+  return launch_assemble(D, N.theta, true, N.L, N.gL, N.HL, st);
+}
+
 }  // namespace celeste
 
 using namespace celeste;
@@ -231,42 +264,106 @@ extern "C" int celeste_newton_batch(celeste_problem* p, double* theta, const cel
   const ProblemDev& D = p->dev;
   cudaStream_t st = (cudaStream_t)stream;
   const int S = p->S;
+  const int K = std::max(1, std::min(o.graph_iters > 0 ? o.graph_iters : 4, max_iter));
+  const bool prof = p->prof_on;
   cudaError_t e;
-  auto full_eval = [&](const double* th) -> cudaError_t {
-    const int m0 = prof_mark(p, st);
-    cudaError_t e2 = launch_full(D, th, st);
-    const int m1 = prof_mark(p, st);
-    if (p->prof_on) p->prof_full.push_back({m0, m1});
+  // events bracketing each iteration's value and full evaluation (profiling only)
+  while (prof && p->iter_events.size() < (size_t)(4 * K)) {
+    cudaEvent_t ev;
+    if ((e = cudaEventCreate(&ev)) != cudaSuccess) return cuda_fail(e, "event create");
+    p->iter_events.push_back(ev);
+  }
+  auto read_events = [&](int n_iter) -> cudaError_t {
+    if (!prof) return cudaSuccess;
+    for (int k = 0; k < n_iter; ++k) {
+      float tv = 0.f, tf = 0.f;
+      cudaError_t e2 = cudaEventElapsedTime(&tv, p->iter_events[4 * k], p->iter_events[4 * k + 1]);
+      if (e2 == cudaSuccess) e2 = cudaEventElapsedTime(&tf, p->iter_events[4 * k + 2], p->iter_events[4 * k + 3]);
+      if (e2 != cudaSuccess) return e2;
+      p->prof_value_acc += tv;
+      p->prof_full_acc += tf;
+    }
+    p->prof_value_n += n_iter;
+    p->prof_full_n += n_iter;
+    p->prof_iters += n_iter;
+    p->prof_launches += (long long)n_iter * NEWTON_KERNELS_PER_ITER;
+    return cudaSuccess;
+  };
+  auto read_active = [&](int& active) -> cudaError_t {
+    cudaError_t e2 = cudaMemcpyAsync(&active, N.count, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(st);
     return e2;
   };
-  auto value_eval = [&](const double* th) -> cudaError_t {
-    const int m0 = prof_mark(p, st);
-    cudaError_t e2 = launch_value(D, th, FLAG_VALUE, true, st);
-    const int m1 = prof_mark(p, st);
-    if (p->prof_on) p->prof_value.push_back({m0, m1});
-    return e2;
-  };
+
   newton_init_kernel<<<(S + 127) / 128, 128, 0, st>>>(N, D.flags);
-  if ((e = full_eval(theta)) != cudaSuccess) return cuda_fail(e, "full eval");
-  if ((e = launch_assemble(D, theta, true, FLAG_FULL, N.L, N.gL, N.HL, st)) != cudaSuccess) return cuda_fail(e, "assemble");
-  for (int it = 0; it < max_iter; ++it) {
-    tr_step_kernel<<<(S + TR_WARPS - 1) / TR_WARPS, 32 * TR_WARPS, 0, st>>>(N, D.flags);
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "tr_step");
-    if ((e = value_eval(N.trial)) != cudaSuccess) return cuda_fail(e, "trial eval");
-    if ((e = launch_assemble_value(D, N.trial, theta, FLAG_VALUE, N.Ltrial, st)) != cudaSuccess)
-      return cuda_fail(e, "trial assemble");
-    if ((e = cudaMemsetAsync(N.count, 0, sizeof(int), st)) != cudaSuccess) return cuda_fail(e, "count reset");
-    tr_update_kernel<<<(S + 127) / 128, 128, 0, st>>>(N, D.flags);
-    if ((e = full_eval(theta)) != cudaSuccess) return cuda_fail(e, "full eval");
-    if ((e = launch_assemble(D, theta, true, FLAG_FULL, N.L, N.gL, N.HL, st)) != cudaSuccess)
-      return cuda_fail(e, "assemble");
-    int active = 0;
-    if ((e = cudaMemcpyAsync(&active, N.count, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
-      return cuda_fail(e, "count read");
-    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "newton iteration");
-    prof_count(p, 6);
-    if (p->prof_on) p->prof_iters += 1;
-    if (active == 0) break;
+  if ((e = launch_worklists(D, FLAG_FULL, st)) != cudaSuccess) return cuda_fail(e, "worklists");
+  {
+    const int m0 = prof_mark(p, st);
+    if ((e = launch_full(D, theta, st)) != cudaSuccess) return cuda_fail(e, "full eval");
+    const int m1 = prof_mark(p, st);
+    if (prof) p->prof_full.push_back({m0, m1});
+  }
+  if ((e = launch_assemble(D, theta, true, N.L, N.gL, N.HL, st)) != cudaSuccess) return cuda_fail(e, "assemble");
+  prof_count(p, 5);
+
+  int it = 0, active = S;
+  if (K > 1) {
+    // (re)capture K iterations unless the graph kept from an earlier call has the same arguments
+    struct {
+      NewtonDev N;
+      const char* base;
+      int K, prof;
+    } key;
+    std::memset(&key, 0, sizeof(key));
+    key.N = N;
+    key.base = p->base;
+    key.K = K;
+    key.prof = prof ? 1 : 0;
+    const unsigned char* kb = reinterpret_cast<const unsigned char*>(&key);
+    if (!p->newton_exec || p->newton_key.size() != sizeof(key) ||
+        std::memcmp(p->newton_key.data(), kb, sizeof(key)) != 0) {
+      if (p->newton_exec) {
+        cudaGraphExecDestroy(p->newton_exec);
+        p->newton_exec = nullptr;
+      }
+      p->newton_key.clear();
+      if (!p->capture_stream &&
+          (e = cudaStreamCreateWithFlags(&p->capture_stream, cudaStreamNonBlocking)) != cudaSuccess)
+        return cuda_fail(e, "capture stream");
+      cudaStream_t cs = p->capture_stream;
+      if ((e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+        return cuda_fail(e, "begin capture");
+      cudaError_t ec = cudaSuccess;
+      for (int k = 0; k < K && ec == cudaSuccess; ++k)
+        ec = newton_iteration(D, N, cs, prof ? &p->iter_events[4 * k] : nullptr, true);
+      cudaGraph_t graph = nullptr;
+      e = cudaStreamEndCapture(cs, &graph);
+      if (ec != cudaSuccess || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return cuda_fail(ec != cudaSuccess ? ec : e, "capture of the Newton iterations");
+      }
+      e = cudaGraphInstantiate(&p->newton_exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) {
+        p->newton_exec = nullptr;
+        return cuda_fail(e, "graph instantiate");
+      }
+      p->newton_key.assign(kb, kb + sizeof(key));
+    }
+    while (active > 0 && it + K <= max_iter) {
+      if ((e = cudaGraphLaunch(p->newton_exec, st)) != cudaSuccess) return cuda_fail(e, "graph launch");
+      if ((e = read_active(active)) != cudaSuccess) return cuda_fail(e, "newton iterations");
+      if ((e = read_events(K)) != cudaSuccess) return cuda_fail(e, "iteration events");
+      it += K;
+    }
+  }
+  // plain launches: every iteration when K == 1, else the iterations left over after the graphs
+  while (active > 0 && it < max_iter) {
+    if ((e = newton_iteration(D, N, st, prof ? &p->iter_events[0] : nullptr, false)) != cudaSuccess)
+      return cuda_fail(e, "newton iteration");
+    if ((e = read_active(active)) != cudaSuccess) return cuda_fail(e, "newton iteration");
+    if ((e = read_events(1)) != cudaSuccess) return cuda_fail(e, "iteration events");
+    ++it;
   }
   newton_finish_kernel<<<(S + 127) / 128, 128, 0, st>>>(N, iters_out, status_out, elbo_out);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "finish");

@@ -30,9 +30,10 @@ static void* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
 
 static size_t round256(size_t x) { return (x + 255) & ~size_t(255); }
 
-// Layout of the array for one problem: partial sums, flags, counters, tables, source moments.
+// Layout of the array for one problem: partial sums, flags, counters, tables, source moments,
+// worklists and their counts.
 struct NoallocLayout {
-  size_t partials, flags, counters, ptab, srcmom, total;
+  size_t partials, flags, counters, ptab, srcmom, wl, wl_count, total;
 };
 static NoallocLayout noalloc_layout(const celeste_problem* p) {
   NoallocLayout L;
@@ -47,6 +48,10 @@ static NoallocLayout noalloc_layout(const celeste_problem* p) {
   o += round256(sizeof(float) * TB_FLOATS * p->patches.size());
   L.srcmom = o;
   o += round256(sizeof(float2) * (size_t)p->n_pix);
+  L.wl = o;
+  o += round256(sizeof(int) * (p->tiles.size() + p->patches.size() + (size_t)p->S));
+  L.wl_count = o;
+  o += round256(sizeof(int) * 4);
   L.total = o;
   return L;
 }
@@ -94,14 +99,18 @@ extern "C" int celeste_elbo_batch_noalloc(celeste_problem* p, const double* thet
   D.counters = reinterpret_cast<unsigned long long*>(b + NL.counters);
   D.ptab = reinterpret_cast<float*>(b + NL.ptab);
   D.srcmom = reinterpret_cast<float2*>(b + NL.srcmom);
+  D.wl = reinterpret_cast<int*>(b + NL.wl);
+  D.wl_count = reinterpret_cast<int*>(b + NL.wl_count);
   cudaStream_t st = (cudaStream_t)stream;
   // The array keeps the previous call's contents: the counters must start at zero; the flags,
-  // tables, source moments and partial sums are fully rewritten below before they are read.
+  // worklists, tables, source moments and partial sums are fully rewritten below before they
+  // are read.
   cudaError_t e = cudaMemsetAsync(D.counters, 0, sizeof(unsigned long long) * 4, st);
   if (e != cudaSuccess) return cuda_fail(e, "clear counters");
   if ((e = launch_set_flags(D, FLAG_FULL, st)) != cudaSuccess) return cuda_fail(e, "set flags");
+  if ((e = launch_worklists(D, FLAG_FULL, st)) != cudaSuccess) return cuda_fail(e, "worklists");
   if ((e = launch_full(D, theta, st)) != cudaSuccess) return cuda_fail(e, "pixel kernel");
-  if ((e = launch_assemble(D, theta, true, FLAG_FULL, elbo, grad, hess, st)) != cudaSuccess)
+  if ((e = launch_assemble(D, theta, true, elbo, grad, hess, st)) != cudaSuccess)
     return cuda_fail(e, "assemble kernel");
   return CELESTE_OK;
 }

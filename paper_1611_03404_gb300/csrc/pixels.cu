@@ -19,6 +19,7 @@
 // brings the patch table and the tile's pixel records into shared memory with two TMA bulk
 // copies on one mbarrier.  Each thread evaluates its pixels; each warp reduce-scatters the 108
 // per-pixel contributions so that lane l keeps sums l, l+32, l+64, l+96 (4 registers, not 108).
+#include <algorithm>
 #include <utility>
 
 #include "celeste_internal.cuh"
@@ -62,21 +63,22 @@ __device__ __forceinline__ float warp_reduce_scatter32(float (&v)[32], int lane)
   return v[0];
 }
 
-// Stage the patch table and the tile's pixel records (one mbarrier, two bulk copies).
+// Stage the patch table and the tile's pixel records (one mbarrier, two bulk copies). The barrier
+// is initialised once per CTA; `phase` is the parity of this use. The caller has synchronised the
+// CTA since the buffers were last read.
 __device__ __forceinline__ bool stage_tile(const ProblemDev& P, const TileDev& t, const PatchDev& pt, float* tab,
-                                           float4* spix, uint64_t* bar, int tid) {
-  if (tid == 0) mbar_init(bar, 1);
-  __syncthreads();
+                                           float4* spix, uint64_t* bar, uint32_t phase, int tid) {
   if (tid == 0) {
+    fence_proxy_async_smem();
     const uint32_t tb = TB_FLOATS * 4u, pb = (uint32_t)t.count * 16u;
     mbar_expect_tx(bar, tb + pb);
     bulk_copy(tab, P.ptab + (size_t)t.patch * TB_FLOATS, tb, bar);
     bulk_copy(spix, P.pix + pt.pix_off + t.start, pb, bar);
   }
-  bool ok = mbar_wait(bar, 0, WAIT_BUDGET);
+  bool ok = mbar_wait(bar, phase, WAIT_BUDGET);
   if (!ok) {
     atomicExch(P.err + ERR_TIMEOUT, 1);
-    mbar_wait(bar, 0, WAIT_BUDGET);   // give the copies in flight a last chance before leaving
+    mbar_wait(bar, phase, WAIT_BUDGET);   // give the copies in flight a last chance before leaving
   }
   return __syncthreads_and(ok);
 }
@@ -137,13 +139,19 @@ __global__ void __launch_bounds__(BLOCK) elbo_full_kernel(ProblemDev P) {
   __shared__ __align__(8) uint64_t bar;
   __shared__ float red[BLOCK / 32][128];
 
-  const TileDev t = P.tiles[blockIdx.x];
-  const PatchDev pt = P.patches[t.patch];
-  if (!(P.flags[pt.source] & FLAG_FULL)) return;
+  const int n_items = P.wl_count[WL_TILES];
+  const int* items = wl_list(P, WL_TILES);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  uint32_t phase = 0;
+  for (int w = blockIdx.x; w < n_items; w += gridDim.x, phase ^= 1u) {
+  const int tile = items[w];
+  const TileDev t = P.tiles[tile];
+  const PatchDev pt = P.patches[t.patch];
   if (tid == 0) atomicAdd(P.counters + 0, (unsigned long long)t.count);
-  if (!stage_tile(P, t, pt, tab, spix, &bar, tid)) {
-    if (tid < NACC) P.partials[(size_t)blockIdx.x * NACC + tid] = __int_as_float(0x7fc00000);
+  if (!stage_tile(P, t, pt, tab, spix, &bar, phase, tid)) {
+    if (tid < NACC) P.partials[(size_t)tile * NACC + tid] = __int_as_float(0x7fc00000);
     return;
   }
   const SNConst c = *reinterpret_cast<const SNConst*>(&tab[TB_SNC]);
@@ -349,7 +357,9 @@ __global__ void __launch_bounds__(BLOCK) elbo_full_kernel(ProblemDev P) {
     float v = 0.f;
 #pragma unroll
     for (int w = 0; w < BLOCK / 32; ++w) v += red[w][tid];
-    P.partials[(size_t)blockIdx.x * NACC + tid] = v;
+    P.partials[(size_t)tile * NACC + tid] = v;
+  }
+  __syncthreads();   // tab, spix and red are refilled for the next tile
   }
 }
 
@@ -359,19 +369,25 @@ __global__ void __launch_bounds__(BLOCK) elbo_full_kernel(ProblemDev P) {
 //           last full evaluation (its E[G], Var[G] kept in srcmom): the change of the ELBO's pixel
 //           part without the rounding of two large sums.
 template <int PPT>
-__global__ void __launch_bounds__(BLOCK) elbo_value_kernel(ProblemDev P, int flag_mask, int diff) {
+__global__ void __launch_bounds__(BLOCK) elbo_value_kernel(ProblemDev P, int diff) {
   __shared__ __align__(16) float tab[TB_FLOATS];
   __shared__ __align__(16) float4 spix[BLOCK * PPT];
   __shared__ __align__(8) uint64_t bar;
   __shared__ float red[BLOCK / 32];
 
-  const TileDev t = P.tiles[blockIdx.x];
-  const PatchDev pt = P.patches[t.patch];
-  if (!(P.flags[pt.source] & flag_mask)) return;
+  const int n_items = P.wl_count[WL_TILES];
+  const int* items = wl_list(P, WL_TILES);
   const int tid = threadIdx.x;
+  if (tid == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  uint32_t phase = 0;
+  for (int w = blockIdx.x; w < n_items; w += gridDim.x, phase ^= 1u) {
+  const int tile = items[w];
+  const TileDev t = P.tiles[tile];
+  const PatchDev pt = P.patches[t.patch];
   if (tid == 0) atomicAdd(P.counters + 1, (unsigned long long)t.count);
-  if (!stage_tile(P, t, pt, tab, spix, &bar, tid)) {
-    if (tid == 0) P.vpartials[blockIdx.x] = __int_as_float(0x7fc00000);
+  if (!stage_tile(P, t, pt, tab, spix, &bar, phase, tid)) {
+    if (tid == 0) P.vpartials[tile] = __int_as_float(0x7fc00000);
     return;
   }
   const SNConst c = *reinterpret_cast<const SNConst*>(&tab[TB_SNC]);
@@ -429,34 +445,43 @@ __global__ void __launch_bounds__(BLOCK) elbo_value_kernel(ProblemDev P, int fla
     float v = 0.f;
 #pragma unroll
     for (int w = 0; w < BLOCK / 32; ++w) v += red[w];
-    P.vpartials[blockIdx.x] = v;
+    P.vpartials[tile] = v;
+  }
+  __syncthreads();   // tab, spix and red are refilled for the next tile
   }
 }
 
 // ------------------------------------------------------------------------------ launchers
+// Persistent grids: a fixed number of CTAs per SM walks the tile worklist, whose length is known
+// only on the device.
+constexpr int FULL_CTAS_PER_SM = 4;    // 128 registers x 128 threads: 4 CTAs fill the register file
+constexpr int VALUE_CTAS_PER_SM = 8;
+
 cudaError_t launch_full(const ProblemDev& P, const double* theta, cudaStream_t st) {
   if (P.n_tiles == 0) return cudaSuccess;
-  cudaError_t e = launch_tables(P, theta, FLAG_FULL, true, st);
+  cudaError_t e = launch_tables(P, theta, true, st);
   if (e != cudaSuccess) return e;
+  const int g = std::max(1, std::min(P.n_tiles, P.n_sm * FULL_CTAS_PER_SM));
   switch (P.tile_pixels) {
-    case 128: elbo_full_kernel<1><<<P.n_tiles, BLOCK, 0, st>>>(P); break;
-    case 256: elbo_full_kernel<2><<<P.n_tiles, BLOCK, 0, st>>>(P); break;
-    case 512: elbo_full_kernel<4><<<P.n_tiles, BLOCK, 0, st>>>(P); break;
-    default: elbo_full_kernel<8><<<P.n_tiles, BLOCK, 0, st>>>(P); break;
+    case 128: elbo_full_kernel<1><<<g, BLOCK, 0, st>>>(P); break;
+    case 256: elbo_full_kernel<2><<<g, BLOCK, 0, st>>>(P); break;
+    case 512: elbo_full_kernel<4><<<g, BLOCK, 0, st>>>(P); break;
+    default: elbo_full_kernel<8><<<g, BLOCK, 0, st>>>(P); break;
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_value(const ProblemDev& P, const double* theta, int flag_mask, bool diff, cudaStream_t st) {
+cudaError_t launch_value(const ProblemDev& P, const double* theta, bool diff, cudaStream_t st) {
   if (P.n_tiles == 0) return cudaSuccess;
-  cudaError_t e = launch_tables(P, theta, flag_mask, false, st);
+  cudaError_t e = launch_tables(P, theta, false, st);
   if (e != cudaSuccess) return e;
   const int d = diff ? 1 : 0;
+  const int g = std::max(1, std::min(P.n_tiles, P.n_sm * VALUE_CTAS_PER_SM));
   switch (P.tile_pixels) {
-    case 128: elbo_value_kernel<1><<<P.n_tiles, BLOCK, 0, st>>>(P, flag_mask, d); break;
-    case 256: elbo_value_kernel<2><<<P.n_tiles, BLOCK, 0, st>>>(P, flag_mask, d); break;
-    case 512: elbo_value_kernel<4><<<P.n_tiles, BLOCK, 0, st>>>(P, flag_mask, d); break;
-    default: elbo_value_kernel<8><<<P.n_tiles, BLOCK, 0, st>>>(P, flag_mask, d); break;
+    case 128: elbo_value_kernel<1><<<g, BLOCK, 0, st>>>(P, d); break;
+    case 256: elbo_value_kernel<2><<<g, BLOCK, 0, st>>>(P, d); break;
+    case 512: elbo_value_kernel<4><<<g, BLOCK, 0, st>>>(P, d); break;
+    default: elbo_value_kernel<8><<<g, BLOCK, 0, st>>>(P, d); break;
   }
   return cudaGetLastError();
 }

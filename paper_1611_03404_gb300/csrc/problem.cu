@@ -294,6 +294,8 @@ void build_layout(celeste_problem* p) {
   L.flags = take(sizeof(int) * S);
   L.err = take(sizeof(int) * 4);
   L.counters = take(sizeof(unsigned long long) * 4);
+  L.wl = take(sizeof(int) * (p->tiles.size() + NPch + S + 1));
+  L.wl_count = take(sizeof(int) * 4);
   // trust-region state
   L.nt_f = take(sizeof(double) * S);
   L.nt_g = take(sizeof(double) * NP * S);
@@ -347,6 +349,12 @@ extern "C" int celeste_problem_bind(celeste_problem* p, void* workspace, size_t 
   if ((e = cudaMemsetAsync(base + L.err, 0, sizeof(int) * 4, st)) != cudaSuccess) return cuda_fail(e, "clear err");
   if ((e = cudaMemsetAsync(base + L.counters, 0, sizeof(unsigned long long) * 4, st)) != cudaSuccess)
     return cuda_fail(e, "clear counters");
+  if ((e = cudaMemsetAsync(base + L.wl_count, 0, sizeof(int) * 4, st)) != cudaSuccess)
+    return cuda_fail(e, "clear worklists");
+  int dev_id = 0, n_sm = 0;
+  if ((e = cudaGetDevice(&dev_id)) != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if ((e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev_id)) != cudaSuccess)
+    return cuda_fail(e, "SM count");
 
   ProblemDev& D = p->dev;
   D.images = reinterpret_cast<const ImageDev*>(base + L.images);
@@ -365,6 +373,9 @@ extern "C" int celeste_problem_bind(celeste_problem* p, void* workspace, size_t 
   D.flags = reinterpret_cast<int*>(base + L.flags);
   D.err = reinterpret_cast<int*>(base + L.err);
   D.counters = reinterpret_cast<unsigned long long*>(base + L.counters);
+  D.wl = reinterpret_cast<int*>(base + L.wl);
+  D.wl_count = reinterpret_cast<int*>(base + L.wl_count);
+  D.n_sm = std::max(n_sm, 1);
   D.S = p->S;
   D.n_patches = (int)p->patches.size();
   D.n_tiles = (int)p->tiles.size();
@@ -393,6 +404,9 @@ extern "C" int celeste_problem_bind(celeste_problem* p, void* workspace, size_t 
 
 celeste_problem::~celeste_problem() {
   for (cudaEvent_t ev : prof_events) cudaEventDestroy(ev);
+  for (cudaEvent_t ev : iter_events) cudaEventDestroy(ev);
+  if (newton_exec) cudaGraphExecDestroy(newton_exec);
+  if (capture_stream) cudaStreamDestroy(capture_stream);
 }
 
 extern "C" void celeste_problem_destroy(celeste_problem* p) { delete p; }
@@ -421,6 +435,8 @@ extern "C" int celeste_profile_start(celeste_problem* p) {
   p->prof_value.clear();
   p->prof_launches = 0;
   p->prof_iters = 0;
+  p->prof_full_acc = p->prof_value_acc = 0.0;
+  p->prof_full_n = p->prof_value_n = 0;
   return CELESTE_OK;
 }
 
@@ -443,8 +459,10 @@ extern "C" int celeste_profile_stop(celeste_problem* p, celeste_profile_stats* o
   };
   if ((e = span(p->prof_full, out->full_ms)) != cudaSuccess) return cuda_fail(e, "full-kernel events");
   if ((e = span(p->prof_value, out->value_ms)) != cudaSuccess) return cuda_fail(e, "value-kernel events");
-  out->full_launches = (int64_t)p->prof_full.size();
-  out->value_launches = (int64_t)p->prof_value.size();
+  out->full_ms += p->prof_full_acc;
+  out->value_ms += p->prof_value_acc;
+  out->full_launches = (int64_t)p->prof_full.size() + p->prof_full_n;
+  out->value_launches = (int64_t)p->prof_value.size() + p->prof_value_n;
   unsigned long long c[4];
   if ((e = cudaMemcpy(c, p->dev.counters, sizeof(c), cudaMemcpyDeviceToHost)) != cudaSuccess)
     return cuda_fail(e, "read counters");

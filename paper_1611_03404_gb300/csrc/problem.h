@@ -10,6 +10,7 @@ namespace celeste {
 
 struct WsLayout {
   size_t images, patches, tiles, src_patch, nbr, u0, psf_coef, psf, pix, srcmom, ptab, partials, vpartials, flags, err, counters;
+  size_t wl, wl_count;
   size_t nt_f, nt_g, nt_H, nt_trial, nt_pred, nt_ftrial, nt_state, nt_count;
   size_t total;
 };
@@ -46,6 +47,13 @@ struct celeste_problem {
   size_t prof_used = 0;
   std::vector<std::pair<int, int>> prof_full, prof_value;
   long long prof_launches = 0, prof_iters = 0;
+  double prof_full_acc = 0.0, prof_value_acc = 0.0;   // ms of event pairs already read back
+  long long prof_full_n = 0, prof_value_n = 0;
+  // Newton iterations as a CUDA graph (celeste_newton_batch), kept while its arguments repeat
+  cudaStream_t capture_stream = nullptr;
+  cudaGraphExec_t newton_exec = nullptr;
+  std::vector<unsigned char> newton_key;
+  std::vector<cudaEvent_t> iter_events;               // 4 per captured iteration
   ~celeste_problem();
 };
 

@@ -10,6 +10,8 @@
 // with Sigma_g = scale^2 R(angle) diag(1, axis^2) R(angle)^T (the galaxy shape of the paper's
 // Sec. "The Celeste Model") mapped to pixels by the WCS matrix A.  Also the per-patch brightness
 // constants (lognormal moments of the band flux times the type probabilities).
+#include <algorithm>
+
 #include "celeste_internal.cuh"
 #include "kernels.h"
 
@@ -44,12 +46,14 @@ __device__ inline void galaxy_shape_f(double eta, double phi, double kappa, GalS
 }
 
 // full = 1: galaxy derivative entries too; full = 0: precision and normaliser only.
-__global__ void __launch_bounds__(64) table_kernel(ProblemDev P, const double* __restrict__ theta, int flag_mask,
-                                                  int full) {
-  const int patch = blockIdx.x;
-  const PatchDev pt = P.patches[patch];
-  if (!(P.flags[pt.source] & flag_mask)) return;
+// One 64-thread CTA per patch of the patch worklist (grid-stride).
+__global__ void __launch_bounds__(64) table_kernel(ProblemDev P, const double* __restrict__ theta, int full) {
+  const int n_items = P.wl_count[WL_PATCHES];
+  const int* items = wl_list(P, WL_PATCHES);
   const int tid = threadIdx.x;
+  for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
+  const int patch = items[w];
+  const PatchDev pt = P.patches[patch];
   const ImageDev im = P.images[pt.image];
   const double* th = theta + (size_t)pt.source * NP;
   float* out = P.ptab + (size_t)patch * TB_FLOATS;
@@ -115,11 +119,13 @@ __global__ void __launch_bounds__(64) table_kernel(ProblemDev P, const double* _
     const float* cf = reinterpret_cast<const float*>(&c);
     for (int q = 0; q < (int)(sizeof(SNConst) / sizeof(float)); ++q) out[TB_SNC + q] = cf[q];
   }
+  }
 }
 
-cudaError_t launch_tables(const ProblemDev& P, const double* theta, int flag_mask, bool full, cudaStream_t st) {
+cudaError_t launch_tables(const ProblemDev& P, const double* theta, bool full, cudaStream_t st) {
   if (P.n_patches == 0) return cudaSuccess;
-  table_kernel<<<P.n_patches, 64, 0, st>>>(P, theta, flag_mask, full ? 1 : 0);
+  const int blocks = std::max(1, std::min(P.n_patches, P.n_sm * 16));
+  table_kernel<<<blocks, 64, 0, st>>>(P, theta, full ? 1 : 0);
   return cudaGetLastError();
 }
 

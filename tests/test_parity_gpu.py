@@ -165,3 +165,25 @@ def compare_optimum(got, ref, tol=1e-4):
     if a_gal < 1 - 1e-3:
         idx = [7, 8] + list(range(11, 19))
         assert np.all(np.abs(got[idx] - ref[idx]) <= tol * np.maximum(1, np.abs(ref[idx])))
+
+
+def test_newton_graph_matches_plain_launches(P):
+    """Iterations run as CUDA graphs (several per host check, the graph kept across calls) give
+    bit-identical results to one plain launch sequence per iteration, also when max_iter is not a
+    multiple of the graph length and when sources stop mid-graph."""
+    sc = synth.tiny(seed=5, n_sources=12, n_images=3, H=120, W=130, radius=(6, 12))
+    dev = torch.device("cuda:0")
+    prob = P.Problem(sc, device=dev, tile_pixels=128)
+    start = torch.as_tensor(sc.theta0, device=dev).contiguous()
+    prob.render_background(start.clone())
+    runs = []
+    for graph_iters, max_iter in ((1, 50), (4, 50), (4, 50), (3, 7), (1, 7)):
+        th = start.clone()
+        delta, iters, status, elbo = prob.newton_batch(th, max_iter=max_iter, graph_iters=graph_iters)
+        torch.cuda.synchronize()
+        runs.append((max_iter, th.cpu().numpy(), delta.cpu().numpy(), iters.cpu().numpy(), status.cpu().numpy(),
+                     elbo.cpu().numpy()))
+    for a, b in ((0, 1), (0, 2), (3, 4)):
+        for x, y in zip(runs[a][1:], runs[b][1:]):
+            np.testing.assert_array_equal(x, y)
+    assert runs[3][3].max() <= 7
