@@ -76,11 +76,7 @@ __global__ void __launch_bounds__(32 * TR_WARPS) tr_step_kernel(NewtonDev N, int
   // f = -L, g = -gL, B = -HL
   const double gk = lane < NP ? -gL[lane] : 0.0;
   bool finite = isfinite(N.L[s]) && isfinite(gk);
-  for (int i = lane; i < NP * NP; i += 32) {
-    const double b = -HL[i];
-    finite = finite && isfinite(b);
-    S.A[(i / NP) * TR_LD + (i % NP)] = b;
-  }
+  for (int i = lane; i < NP * NP; i += 32) finite = finite && isfinite(HL[i]);
   finite = __all_sync(0xffffffffu, finite);
   if (!finite) {
     if (lane == 0) {
@@ -99,11 +95,12 @@ __global__ void __launch_bounds__(32 * TR_WARPS) tr_step_kernel(NewtonDev N, int
     }
     return;
   }
-  __syncwarp();
   const double delta = N.delta[s];
   double pk, pred;
   int hard;
-  tr_solve_warp(S, gk, delta, pk, pred, hard);
+  // the Newton step is tried first where the previous step was interior
+  const bool try_newton = st[ST_ITERS] > 0 && !st[ST_BOUNDARY];
+  tr_solve_warp(S, HL, -1.0, gk, delta, try_newton, pk, pred, hard);
   const double pnorm = sqrt(warp_sum(lane < NP ? pk * pk : 0.0));
   if (lane < NP) N.trial[(size_t)s * NP + lane] = N.theta[(size_t)s * NP + lane] + pk;
   if (lane == 0) {
@@ -131,12 +128,10 @@ __global__ void __launch_bounds__(32 * TR_WARPS) tr_solve_batch_kernel(const dou
   const int q = blockIdx.x * TR_WARPS + warp;
   if (q >= n) return;
   TrSmem& S = sm[warp];
-  for (int i = lane; i < NP * NP; i += 32) S.A[(i / NP) * TR_LD + (i % NP)] = B[(size_t)q * NP * NP + i];
   const double gk = lane < NP ? g[(size_t)q * NP + lane] : 0.0;
-  __syncwarp();
   double pk, pr;
   int hc;
-  tr_solve_warp(S, gk, delta[q], pk, pr, hc);
+  tr_solve_warp(S, B + (size_t)q * NP * NP, 1.0, gk, delta[q], true, pk, pr, hc);
   if (lane < NP) p[(size_t)q * NP + lane] = pk;
   if (lane == 0) {
     if (pred) pred[q] = pr;

@@ -4,9 +4,15 @@
 // lambda >= max(0, -lambda_min(B)), lambda (|p| - delta) = 0, plus the "hard case" where g has no
 // component along the eigenvector of lambda_min.
 //
-// GB300 float64 throughput is low, so instead of a full eigendecomposition the matrix is reduced
-// once to tridiagonal form T = Q^T B Q by Householder reflections (lane-parallel), after which
-// every solve with T + lambda I is an O(n) LDL^T recurrence:
+// On GB300 one warp's float64 work is bounded by the number of FP64 instructions it issues (the
+// FP64 pipe of an SM sub-partition retires a warp-wide FMA only every several tens of cycles), so
+// the solver keeps that count low:
+//   * Newton step first: where the caller expects it (the previous step was interior), B is
+//     factored B = L D L^T in place (lane i owns row i); if every pivot is positive and
+//     |B^-1 g| <= delta the Newton step is the solution and nothing else runs;
+//   * otherwise B is reduced once to tridiagonal form T = Q^T B Q by Householder reflections
+//     (lane-parallel; g is reflected in the same reductions), after which every solve with
+//     T + lambda I is an O(n) LDL^T recurrence:
 //   * positive definiteness of B  <=>  all LDL^T pivots of T positive (Sylvester);
 //   * lambda_min(T): a float32 Sturm-sequence multisection bracket (each lane tests its own shift),
 //     refined in float64 by inverse iteration and the Rayleigh quotient;
@@ -21,13 +27,16 @@
 namespace celeste {
 
 constexpr int TR_N = NP;          // 27
-constexpr int TR_LD = NP + 1;     // padded row length of the matrix in shared memory
+constexpr int TR_LD = NP;         // row length of the matrix in shared memory (27 doubles: the
+                                  // rows of a warp's lanes start on distinct bank pairs)
 
 struct TrSmem {
-  double A[TR_N * TR_LD];         // B on entry; Householder vectors below the diagonal afterwards
+  double A[TR_N * TR_LD];         // B; its L D L^T factors, or the Householder vectors below
+                                  // the diagonal after the reduction
+  double beta[TR_N];              // reflection coefficients
   double v[32], w[32];            // per-step temporaries
   double d[TR_N], off[TR_N];      // T: diagonal, off[i] = T[i][i-1]
-  double beta[TR_N];              // reflection coefficients
+  double o2[TR_N];                // off[i]^2
   double gh[TR_N], y[TR_N], z[TR_N];
   double D[TR_N], L[TR_N];        // LDL^T of T + lambda I (D holds the reciprocal pivots)
   double sc[4];                   // broadcast scalars
@@ -47,11 +56,10 @@ __device__ inline bool tr_ldl(TrSmem& S, double lambda) {
   double r = 1.0 / Dp;
   S.D[0] = r;
   for (int i = 1; i < TR_N; ++i) {
-    const double l = S.off[i] * r;
-    Dp = S.d[i] + lambda - l * S.off[i];
+    S.L[i] = S.off[i] * r;                 // off the pivot chain
+    Dp = fma(-S.o2[i], r, S.d[i] + lambda);
     pd = pd && Dp > 0.0;
     r = 1.0 / Dp;
-    S.L[i] = l;
     S.D[i] = r;
   }
   return pd;
@@ -66,9 +74,17 @@ __device__ inline void tr_ldl_solve(const TrSmem& S, const double* b, double* x)
 }
 
 __device__ inline double tr_norm(const double* x) {
-  double s = 0.0;
-  for (int i = 0; i < TR_N; ++i) s += x[i] * x[i];
-  return sqrt(s);
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;   // four chains instead of one
+#pragma unroll
+  for (int i = 0; i + 3 < TR_N; i += 4) {
+    s0 = fma(x[i], x[i], s0);
+    s1 = fma(x[i + 1], x[i + 1], s1);
+    s2 = fma(x[i + 2], x[i + 2], s2);
+    s3 = fma(x[i + 3], x[i + 3], s3);
+  }
+#pragma unroll
+  for (int i = TR_N & ~3; i < TR_N; ++i) s0 = fma(x[i], x[i], s0);
+  return sqrt((s0 + s1) + (s2 + s3));
 }
 
 // Number of eigenvalues of T below x (negative pivots of T - x I).
@@ -204,14 +220,76 @@ __device__ inline void tr_newton_lambda(TrSmem& S, double lambda, double lo, dou
   }
 }
 
-// Solves the subproblem for the matrix in S.A and the gradient g_i held by lane i (0 for lanes
-// >= 27).  On return lane i < 27 holds p_i; pred = -(g.p + p.B.p/2); hard = hard case taken.
-__device__ inline void tr_solve_warp(TrSmem& S, double gi, double delta, double& p_i, double& pred, int& hard) {
+// Loads B (scaled by bsign) into S.A, lane-parallel and coalesced.
+__device__ inline void tr_load(TrSmem& S, const double* __restrict__ B, double bsign) {
+  for (int i = threadIdx.x & 31; i < TR_N * TR_N; i += 32) S.A[i] = bsign * B[i];
+  __syncwarp();
+}
+
+// Newton step p = -B^-1 g by L D L^T of S.A in place (lane i owns row i; the rows are kept full,
+// so row k holds the current a_kj when step k needs it).  Returns false if a pivot is not
+// positive; otherwise lane i < 27 holds p_i.
+__device__ inline bool tr_newton_step(TrSmem& S, double gi, double& p_i) {
+  const int lane = threadIdx.x & 31;
+  const bool row = lane < TR_N;
+  double* ar = S.A + lane * TR_LD;
+  for (int k = 0; k < TR_N; ++k) {
+    const double dk = S.A[k * TR_LD + k];
+    if (!(dk > 0.0)) return false;   // same value in every lane
+    const double r = 1.0 / dk;
+    const bool act = row && lane > k;
+    const double li = act ? ar[k] * r : 0.0;
+    __syncwarp();
+    if (act) {
+      for (int j = k + 1; j < TR_N; ++j) ar[j] = fma(-li, S.A[k * TR_LD + j], ar[j]);
+      ar[k] = li;   // L below the diagonal
+    }
+    if (lane == k) S.D[k] = r;
+    __syncwarp();
+  }
+  // L y = -g (column by column), y *= D^-1, L^T x = y (from the bottom)
+  double y = row ? -gi : 0.0;
+  for (int k = 0; k < TR_N - 1; ++k) {
+    const double yk = __shfl_sync(0xffffffffu, y, k);
+    if (row && lane > k) y = fma(-ar[k], yk, y);
+  }
+  if (row) y *= S.D[lane];
+  for (int k = TR_N - 1; k > 0; --k) {
+    const double xk = __shfl_sync(0xffffffffu, y, k);
+    if (lane < k) y = fma(-S.A[k * TR_LD + lane], xk, y);
+  }
+  p_i = row ? y : 0.0;
+  return true;
+}
+
+// Solves the subproblem for B (device, row-major 27 x 27, times bsign) and the gradient g_i held by
+// lane i (0 for lanes >= 27).  On return lane i < 27 holds p_i; pred = -(g.p + p.B.p/2); hard =
+// hard case taken.  try_newton: attempt the Newton step first.
+__device__ inline void tr_solve_warp(TrSmem& S, const double* __restrict__ Bsrc, double bsign, double gi, double delta,
+                                     bool try_newton, double& p_i, double& pred, int& hard) {
   const int lane = threadIdx.x & 31;
   const int n = TR_N;
-  // ---- Householder tridiagonalisation, lane i owns row i
+  const bool row = lane < n;
+  const double gnorm = sqrt(tr_warp_sum(gi * gi));
+  if (try_newton) {
+    tr_load(S, Bsrc, bsign);
+    double pn;
+    if (tr_newton_step(S, gi, pn)) {
+      const double pp = tr_warp_sum(pn * pn);
+      if (sqrt(pp) <= delta) {
+        p_i = pn;
+        pred = -0.5 * tr_warp_sum(gi * pn);   // -(g.p + p.B.p/2) with B p = -g
+        hard = 0;
+        return;
+      }
+    }
+  }
+  tr_load(S, Bsrc, bsign);
+  // ---- Householder tridiagonalisation, lane i owns row i (in shared memory); gh = Q^T g is
+  //      reflected along, its reductions paired with the reduction's own
+  double gh = row ? gi : 0.0;
   for (int k = 0; k < n - 2; ++k) {
-    const double xi = lane > k && lane < n ? S.A[lane * TR_LD + k] : 0.0;
+    const double xi = lane > k && row ? S.A[lane * TR_LD + k] : 0.0;
     const double s2 = tr_warp_sum(xi * xi);
     const double x0 = S.A[(k + 1) * TR_LD + k];
     if (s2 == 0.0) {
@@ -225,20 +303,36 @@ __device__ inline void tr_solve_warp(TrSmem& S, double gi, double delta, double&
     const double alpha = -copysign(sqrt(s2), x0);
     const double vi = lane == k + 1 ? x0 - alpha : xi;
     const double beta = 1.0 / (s2 - alpha * x0);   // 2 / v.v with v.v = 2 (s2 - alpha x0)
-    if (lane > k && lane < n) S.v[lane] = vi;
+    S.v[lane] = vi;
     __syncwarp();
-    double pi = 0.0;
-    if (lane > k && lane < n) {
-      for (int j = k + 1; j < n; ++j) pi += S.A[lane * TR_LD + j] * S.v[j];
-      pi *= beta;
+    double u[4] = {0.0, 0.0, 0.0, 0.0};
+    if (lane > k && row) {
+      const double* ar = S.A + lane * TR_LD;
+      int j = k + 1;
+      for (; j + 3 < n; j += 4) {
+        u[0] = fma(ar[j], S.v[j], u[0]);
+        u[1] = fma(ar[j + 1], S.v[j + 1], u[1]);
+        u[2] = fma(ar[j + 2], S.v[j + 2], u[2]);
+        u[3] = fma(ar[j + 3], S.v[j + 3], u[3]);
+      }
+      for (; j < n; ++j) u[0] = fma(ar[j], S.v[j], u[0]);
     }
-    const double K = 0.5 * beta * tr_warp_sum(lane > k && lane < n ? vi * pi : 0.0);
+    const double pi = beta * ((u[0] + u[1]) + (u[2] + u[3]));
+    double vp = vi * pi, vg = vi * gh;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      vp += __shfl_xor_sync(0xffffffffu, vp, o);
+      vg += __shfl_xor_sync(0xffffffffu, vg, o);
+    }
+    const double K = 0.5 * beta * vp;
     const double wi = pi - K * vi;
-    if (lane > k && lane < n) S.w[lane] = wi;
+    gh = fma(-beta * vg, vi, gh);
+    S.w[lane] = wi;
     __syncwarp();
-    if (lane > k && lane < n) {
-      for (int j = k + 1; j < n; ++j) S.A[lane * TR_LD + j] -= vi * S.w[j] + wi * S.v[j];
-      S.A[lane * TR_LD + k] = vi;   // keep the reflection vector
+    if (lane > k && row) {
+      double* ar = S.A + lane * TR_LD;
+      for (int j = k + 1; j < n; ++j) ar[j] = fma(-vi, S.w[j], fma(-wi, S.v[j], ar[j]));
+      ar[k] = vi;   // keep the reflection vector
     }
     if (lane == 0) {
       S.beta[k] = beta;
@@ -246,20 +340,16 @@ __device__ inline void tr_solve_warp(TrSmem& S, double gi, double delta, double&
     }
     __syncwarp();
   }
-  if (lane < n) S.d[lane] = S.A[lane * TR_LD + lane];
+  if (row) {
+    S.d[lane] = S.A[lane * TR_LD + lane];
+    S.gh[lane] = gh;
+  }
   if (lane == 0) {
     S.off[n - 1] = S.A[(n - 1) * TR_LD + n - 2];
     S.off[0] = 0.0;
   }
-  // ---- gh = Q^T g
-  double gh = lane < n ? gi : 0.0;
-  for (int k = 0; k < n - 2; ++k) {
-    const double vk = lane > k && lane < n ? S.A[lane * TR_LD + k] : 0.0;
-    const double t = tr_warp_sum(vk * gh);
-    gh -= S.beta[k] * vk * t;
-  }
-  if (lane < n) S.gh[lane] = gh;
-  const double gnorm = sqrt(tr_warp_sum(gi * gi));
+  __syncwarp();
+  if (row) S.o2[lane] = S.off[lane] * S.off[lane];
   __syncwarp();
 
   // ---- positive definite and interior?
@@ -313,8 +403,8 @@ __device__ inline void tr_solve_warp(TrSmem& S, double gi, double delta, double&
         for (int i = 0; i < n; ++i) S.z[i] = 1.0;
         for (int r = 0; r < 4; ++r) {
           tr_ldl_solve(S, S.z, S.z);
-          const double nz = tr_norm(S.z);
-          for (int i = 0; i < n; ++i) S.z[i] /= nz;
+          const double rz = 1.0 / tr_norm(S.z);
+          for (int i = 0; i < n; ++i) S.z[i] *= rz;
         }
         double lmin = 0.0, zg = 0.0;
         for (int i = 0; i < n; ++i) {
@@ -354,17 +444,17 @@ __device__ inline void tr_solve_warp(TrSmem& S, double gi, double delta, double&
   }
   hard = S.flag[2];
   // ---- p = Q y, and the model value through T: g.p = gh.y, p.B.p = y.T.y
-  double yi = lane < n ? S.y[lane] : 0.0;
+  double yi = row ? S.y[lane] : 0.0;
   double Ty = 0.0;
-  if (lane < n) {
+  if (row) {
     Ty = S.d[lane] * yi + (lane > 0 ? S.off[lane] * S.y[lane - 1] : 0.0) +
          (lane + 1 < n ? S.off[lane + 1] * S.y[lane + 1] : 0.0);
   }
-  const double gy = tr_warp_sum(lane < n ? S.gh[lane] * yi : 0.0);
+  const double gy = tr_warp_sum(row ? S.gh[lane] * yi : 0.0);
   const double yTy = tr_warp_sum(yi * Ty);
   pred = -(gy + 0.5 * yTy);
   for (int k = n - 3; k >= 0; --k) {
-    const double vk = lane > k && lane < n ? S.A[lane * TR_LD + k] : 0.0;
+    const double vk = lane > k && row ? S.A[lane * TR_LD + k] : 0.0;
     const double t = tr_warp_sum(vk * yi);
     yi -= S.beta[k] * vk * t;
   }
