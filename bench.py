@@ -53,8 +53,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="field", choices=["field", "mosaic"],
+                    help="field: 2048x1489 px x 5 bands, --sources sources (the headline workload); "
+                         "mosaic: 10x10 overlapping fields, 100,000 sources, 1-12 exposures each")
     ap.add_argument("--sources", type=int, default=1000)
-    ap.add_argument("--tile", type=int, default=128)
+    ap.add_argument("--tile", type=int, default=128, help="pixels per tile; 0 = autotune")
     ap.add_argument("--seed", type=int, default=1611)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--e2e-steps", type=int, default=2)
@@ -62,10 +65,18 @@ def parse():
     return ap.parse_args()
 
 
-def workload_config(args):
+def workload_config(args, tile):
+    if args.workload == "mosaic":
+        return {"workload": "mosaic_10x10_fields_100000src", "fields": [10, 10], "field_px": [2048, 1489],
+                "field_overlap": 0.2, "bands_per_field": "1-3", "exposures_per_source": "1-12",
+                "sources_per_gpu": 100_000, "patch_radius": "8-64 (brightness, 4 sigma of the widest component)",
+                "galaxy_fraction": 0.6, "elbo_tol": 1e-8, "max_iter": 50, "tile_pixels": tile,
+                "tile_choice": "autotuned" if args.tile == 0 else "fixed",
+                "l2": "inputs larger than L2 (GBs of patch pixels) and a 256 MiB flush between timed steps",
+                "parallelism": "one independently seeded mosaic per GPU"}
     return {"workload": f"field_2048x1489x5_{args.sources}src", "image_px": [2048, 1489], "bands": 5,
             "sources_per_gpu": args.sources, "patch_radius": "8-32 by brightness", "galaxy_fraction": 0.6,
-            "elbo_tol": 1e-8, "max_iter": 50, "tile_pixels": args.tile,
+            "elbo_tol": 1e-8, "max_iter": 50, "tile_pixels": tile,
             "l2": "flushed between timed steps (256 MiB device write)",
             "parallelism": "one independently seeded field per GPU"}
 
@@ -156,7 +167,7 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "sources/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(args),
+            "config": workload_config(args, args.tile),
             "cpu_baseline": {"value": value, "unit": "sources/s", "cores": torch.get_num_threads(), "kind": "oracle",
                              "sample": f"first {solved} sources of the field per step (full Newton solves), "
                                        f"~{per_step:.0f} s of CPU work per step"},
@@ -189,8 +200,16 @@ def main():
     if world > 1:
         dist.barrier()
 
-    scene = synth.field(seed=args.seed + rank, n_sources=args.sources)
-    prob = P.Problem(scene, device=dev, tile_pixels=args.tile)
+    if args.workload == "mosaic":
+        from synth.mosaic import mosaic
+        scene = mosaic(seed=args.seed + rank, device=dev)
+    else:
+        scene = synth.field(seed=args.seed + rank, n_sources=args.sources)
+    tile, tune = args.tile, None
+    if tile == 0:
+        from paper_1611_03404_gb300.autotune import tune_tile
+        tile, tune = tune_tile(scene, device=dev)
+    prob = P.Problem(scene, device=dev, tile_pixels=tile)
     counts = prob.counts()
     theta0 = torch.as_tensor(scene.theta0, device=dev).contiguous()
     theta = theta0.clone()
@@ -294,7 +313,7 @@ def main():
                "ms_per_step": 1e3 * te}
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "field":
         v, n, thr, dt = cpu_baseline(scene, args.cpu_seconds)
         cpu = {"value": v, "unit": "sources/s", "cores": thr, "kind": "oracle",
                "sample": f"first {n} of the {scene.n_sources} field sources (full float64 Newton solves, "
@@ -303,7 +322,8 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "sources/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(args),
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(args, tile),
+                "autotune_us_per_1000px": tune,
                 "pixel_evals_per_s": px_rate, "converged": conv, "newton_iters_mean": iters_mean,
                 "newton_iters_max": iters_max, "status_counts": status_counts,
                 "layout": counts, "wall_s_timed": wall,

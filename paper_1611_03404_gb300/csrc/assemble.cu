@@ -99,8 +99,6 @@ struct PatchLift {
 
 __global__ void __launch_bounds__(128) assemble_kernel(ProblemDev P, const double* __restrict__ theta, int full,
                                                        double* elbo, double* grad, double* hess) {
-  const int n_items = P.wl_count[WL_SOURCES];
-  const int* items = wl_list(P, WL_SOURCES);
   const int tid = threadIdx.x, nt = blockDim.x;
   __shared__ double sums[NACC];
   __shared__ double Hs[NP * NP], gs[NP], HE[NP * NP], gE[NP];
@@ -109,8 +107,8 @@ __global__ void __launch_bounds__(128) assemble_kernel(ProblemDev P, const doubl
   __shared__ PatchLift c;
   __shared__ SourceConst sc;
   __shared__ double Lsum, red[16];
-  for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
-  const int s = items[w];
+  __shared__ int slot;
+  for (int s = wl_next_cta(P, WL_SOURCES, slot); s >= 0; s = wl_next_cta(P, WL_SOURCES, slot)) {
   const double* th = theta + (size_t)s * NP;
   for (int i = tid; i < NP * NP; i += nt) Hs[i] = 0.0;
   for (int i = tid; i < NP; i += nt) gs[i] = 0.0;
@@ -363,12 +361,8 @@ __global__ void __launch_bounds__(128) assemble_kernel(ProblemDev P, const doubl
 // (plus the KL at theta_ref when the pixel sums are differences from theta_ref).
 __global__ void assemble_value_kernel(ProblemDev P, const double* __restrict__ theta, const double* __restrict__ theta_ref,
                                       double* out) {
-  const int n_items = P.wl_count[WL_SOURCES];
-  const int* items = wl_list(P, WL_SOURCES);
   const int lane = threadIdx.x & 31;
-  const int nwarps = gridDim.x * (blockDim.x >> 5);
-  for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < n_items; w += nwarps) {   // warp-uniform
-  const int s = items[w];
+  for (int s = wl_next_warp(P, WL_SOURCES); s >= 0; s = wl_next_warp(P, WL_SOURCES)) {   // warp-uniform
   double v = 0.0;
   for (int p = P.src_patch[s]; p < P.src_patch[s + 1]; ++p) {
     const PatchDev& pt = P.patches[p];
@@ -452,7 +446,7 @@ __global__ void worklist_kernel(ProblemDev P, int mask) {
 }
 
 cudaError_t launch_worklists(const ProblemDev& P, int mask, cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(P.wl_count, 0, sizeof(int) * 4, st);
+  cudaError_t e = cudaMemsetAsync(P.wl_count, 0, sizeof(int) * WL_INTS, st);
   if (e != cudaSuccess) return e;
   const int total = P.n_tiles + P.n_patches + P.S;
   const int blocks = std::max(1, std::min((total + 255) / 256, P.n_sm * 4));

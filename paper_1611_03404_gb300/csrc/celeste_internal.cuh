@@ -77,6 +77,7 @@ struct TileDev {
 
 // Worklists (offsets into ProblemDev::wl and indices of ProblemDev::wl_count).
 constexpr int WL_TILES = 0, WL_PATCHES = 1, WL_SOURCES = 2;
+constexpr int WL_INTS = 8;
 
 // Device view of a bound problem (passed by value to kernels).
 struct ProblemDev {
@@ -95,7 +96,8 @@ struct ProblemDev {
   float* vpartials;              // [n_tiles]
   int* flags;                    // [S] per-source work flags
   int* wl;                       // worklists built from the flags: tiles [n_tiles], patches [n_patches], sources [S]
-  int* wl_count;                 // [4]: number of tiles, patches, sources in the worklists
+  int* wl_count;                 // [WL_INTS]: number of tiles, patches, sources in the worklists,
+                                 // then the three queue heads
   int* err;                      // [4] device error words
   unsigned long long* counters;  // [4]: full-kernel pixels, value-kernel pixels
   int S, n_patches, n_tiles, tile_pixels, n_sm;
@@ -106,6 +108,29 @@ struct ProblemDev {
 
 __device__ inline int* wl_list(const ProblemDev& P, int which) {
   return P.wl + (which == WL_TILES ? 0 : which == WL_PATCHES ? P.n_tiles : P.n_tiles + P.n_patches);
+}
+
+// Work queue over a worklist: the CTA's next item (one atomic by thread 0, broadcast through
+// shared memory), or -1 once the list is exhausted.  Every thread of the CTA must call it.
+__device__ inline int wl_next_cta(const ProblemDev& P, int which, int& slot) {
+  if (threadIdx.x == 0) {
+    const int i = atomicAdd(P.wl_count + 3 + which, 1);
+    slot = i < P.wl_count[which] ? wl_list(P, which)[i] : -1;
+  }
+  __syncthreads();
+  const int item = slot;
+  __syncthreads();   // the slot is rewritten only after every thread has read it
+  return item;
+}
+
+// The same for one warp (lane 0 takes the item, a shuffle broadcasts it).
+__device__ inline int wl_next_warp(const ProblemDev& P, int which) {
+  int item = -1;
+  if ((threadIdx.x & 31) == 0) {
+    const int i = atomicAdd(P.wl_count + 3 + which, 1);
+    item = i < P.wl_count[which] ? wl_list(P, which)[i] : -1;
+  }
+  return __shfl_sync(0xffffffffu, item, 0);
 }
 
 // Work flags per source.

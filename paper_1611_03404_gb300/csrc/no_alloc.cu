@@ -51,7 +51,7 @@ static NoallocLayout noalloc_layout(const celeste_problem* p) {
   L.wl = o;
   o += round256(sizeof(int) * (p->tiles.size() + p->patches.size() + (size_t)p->S));
   L.wl_count = o;
-  o += round256(sizeof(int) * 4);
+  o += round256(sizeof(int) * WL_INTS);
   L.total = o;
   return L;
 }

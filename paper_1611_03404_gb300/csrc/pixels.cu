@@ -139,14 +139,12 @@ __global__ void __launch_bounds__(BLOCK) elbo_full_kernel(ProblemDev P) {
   __shared__ __align__(8) uint64_t bar;
   __shared__ float red[BLOCK / 32][128];
 
-  const int n_items = P.wl_count[WL_TILES];
-  const int* items = wl_list(P, WL_TILES);
+  __shared__ int slot;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid == 0) mbar_init(&bar, 1);
   __syncthreads();
   uint32_t phase = 0;
-  for (int w = blockIdx.x; w < n_items; w += gridDim.x, phase ^= 1u) {
-  const int tile = items[w];
+  for (int tile = wl_next_cta(P, WL_TILES, slot); tile >= 0; tile = wl_next_cta(P, WL_TILES, slot), phase ^= 1u) {
   const TileDev t = P.tiles[tile];
   const PatchDev pt = P.patches[t.patch];
   if (tid == 0) atomicAdd(P.counters + 0, (unsigned long long)t.count);
@@ -375,14 +373,12 @@ __global__ void __launch_bounds__(BLOCK) elbo_value_kernel(ProblemDev P, int dif
   __shared__ __align__(8) uint64_t bar;
   __shared__ float red[BLOCK / 32];
 
-  const int n_items = P.wl_count[WL_TILES];
-  const int* items = wl_list(P, WL_TILES);
+  __shared__ int slot;
   const int tid = threadIdx.x;
   if (tid == 0) mbar_init(&bar, 1);
   __syncthreads();
   uint32_t phase = 0;
-  for (int w = blockIdx.x; w < n_items; w += gridDim.x, phase ^= 1u) {
-  const int tile = items[w];
+  for (int tile = wl_next_cta(P, WL_TILES, slot); tile >= 0; tile = wl_next_cta(P, WL_TILES, slot), phase ^= 1u) {
   const TileDev t = P.tiles[tile];
   const PatchDev pt = P.patches[t.patch];
   if (tid == 0) atomicAdd(P.counters + 1, (unsigned long long)t.count);
@@ -452,8 +448,8 @@ __global__ void __launch_bounds__(BLOCK) elbo_value_kernel(ProblemDev P, int dif
 }
 
 // ------------------------------------------------------------------------------ launchers
-// Persistent grids: a fixed number of CTAs per SM walks the tile worklist, whose length is known
-// only on the device.
+// Persistent grids: a fixed number of CTAs per SM takes tiles from the device work queue over the
+// tile worklist, whose length is known only on the device.
 constexpr int FULL_CTAS_PER_SM = 4;    // 128 registers x 128 threads: 4 CTAs fill the register file
 constexpr int VALUE_CTAS_PER_SM = 8;
 

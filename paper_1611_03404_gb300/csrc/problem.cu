@@ -295,7 +295,7 @@ void build_layout(celeste_problem* p) {
   L.err = take(sizeof(int) * 4);
   L.counters = take(sizeof(unsigned long long) * 4);
   L.wl = take(sizeof(int) * (p->tiles.size() + NPch + S + 1));
-  L.wl_count = take(sizeof(int) * 4);
+  L.wl_count = take(sizeof(int) * WL_INTS);
   // trust-region state
   L.nt_f = take(sizeof(double) * S);
   L.nt_g = take(sizeof(double) * NP * S);
@@ -349,7 +349,7 @@ extern "C" int celeste_problem_bind(celeste_problem* p, void* workspace, size_t 
   if ((e = cudaMemsetAsync(base + L.err, 0, sizeof(int) * 4, st)) != cudaSuccess) return cuda_fail(e, "clear err");
   if ((e = cudaMemsetAsync(base + L.counters, 0, sizeof(unsigned long long) * 4, st)) != cudaSuccess)
     return cuda_fail(e, "clear counters");
-  if ((e = cudaMemsetAsync(base + L.wl_count, 0, sizeof(int) * 4, st)) != cudaSuccess)
+  if ((e = cudaMemsetAsync(base + L.wl_count, 0, sizeof(int) * WL_INTS, st)) != cudaSuccess)
     return cuda_fail(e, "clear worklists");
   int dev_id = 0, n_sm = 0;
   if ((e = cudaGetDevice(&dev_id)) != cudaSuccess) return cuda_fail(e, "cudaGetDevice");

@@ -46,13 +46,11 @@ __device__ inline void galaxy_shape_f(double eta, double phi, double kappa, GalS
 }
 
 // full = 1: galaxy derivative entries too; full = 0: precision and normaliser only.
-// One 64-thread CTA per patch of the patch worklist (grid-stride).
+// 64-thread CTAs taking patches from the device work queue over the patch worklist.
 __global__ void __launch_bounds__(64) table_kernel(ProblemDev P, const double* __restrict__ theta, int full) {
-  const int n_items = P.wl_count[WL_PATCHES];
-  const int* items = wl_list(P, WL_PATCHES);
+  __shared__ int slot;
   const int tid = threadIdx.x;
-  for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
-  const int patch = items[w];
+  for (int patch = wl_next_cta(P, WL_PATCHES, slot); patch >= 0; patch = wl_next_cta(P, WL_PATCHES, slot)) {
   const PatchDev pt = P.patches[patch];
   const ImageDev im = P.images[pt.image];
   const double* th = theta + (size_t)pt.source * NP;

@@ -146,25 +146,41 @@ def test_newton_matches_oracle_optimum(P):
     compare_optimum(got, ref["theta"])
 
 
-def compare_optimum(got, ref, tol=1e-4):
+def stop_slack(H, L, ftol=1e-8):
+    """Per free parameter, how far the ELBO-tolerance stopping rule leaves the optimum undetermined:
+    Newton stops once the predicted gain is below ftol |L|, and along parameter i that gain stays
+    below ftol |L| within sqrt(2 ftol |L| [(-H)^-1]_ii) of the maximum.  Three times that."""
+    try:
+        cov = np.linalg.inv(-H)
+        d = np.clip(np.diag(cov), 0.0, None)
+    except np.linalg.LinAlgError:
+        return np.zeros(len(H))
+    return 3.0 * np.sqrt(2.0 * ftol * abs(L) * d)
+
+
+def compare_optimum(got, ref, tol=1e-4, slack=None):
     """Per-parameter comparison in the constrained space; a type's own parameters only count when
     that type has posterior probability > 1e-3, and the angle (mod pi) only when the axis ratio
-    is below 1 - 1e-3 (otherwise they are unidentified)."""
+    is below 1 - 1e-3 (otherwise they are unidentified).  `slack` (free-parameter units, from
+    stop_slack) widens each bound by what the ELBO stopping tolerance leaves undetermined along
+    weakly curved directions, mapped through the parameter's transform."""
     sig = lambda x: 1 / (1 + math.exp(-x))
+    dsig = lambda x: sig(x) * (1 - sig(x))
+    sl = np.zeros(27) if slack is None else np.asarray(slack)
     a_gal = sig(ref[6])
-    assert abs(sig(got[6]) - a_gal) <= tol
-    assert np.abs(got[0:2] - ref[0:2]).max() <= tol
+    assert abs(sig(got[6]) - a_gal) <= tol + dsig(ref[6]) * sl[6]
+    assert np.all(np.abs(got[0:2] - ref[0:2]) <= tol + sl[0:2])
     if a_gal > 1e-3:
-        assert abs(sig(got[2]) - sig(ref[2])) <= tol
-        assert abs(sig(got[3]) - sig(ref[3])) <= tol
-        assert abs(math.exp(got[5]) - math.exp(ref[5])) <= tol * math.exp(ref[5])
+        assert abs(sig(got[2]) - sig(ref[2])) <= tol + dsig(ref[2]) * sl[2]
+        assert abs(sig(got[3]) - sig(ref[3])) <= tol + dsig(ref[3]) * sl[3]
+        assert abs(math.exp(got[5]) - math.exp(ref[5])) <= (tol + sl[5]) * math.exp(ref[5])
         if sig(ref[3]) < 1 - 1e-3:
-            assert abs(math.remainder(got[4] - ref[4], math.pi)) <= tol
+            assert abs(math.remainder(got[4] - ref[4], math.pi)) <= tol + sl[4]
         idx = [9, 10] + list(range(19, 27))
-        assert np.all(np.abs(got[idx] - ref[idx]) <= tol * np.maximum(1, np.abs(ref[idx])))
+        assert np.all(np.abs(got[idx] - ref[idx]) <= tol * np.maximum(1, np.abs(ref[idx])) + sl[idx])
     if a_gal < 1 - 1e-3:
         idx = [7, 8] + list(range(11, 19))
-        assert np.all(np.abs(got[idx] - ref[idx]) <= tol * np.maximum(1, np.abs(ref[idx])))
+        assert np.all(np.abs(got[idx] - ref[idx]) <= tol * np.maximum(1, np.abs(ref[idx])) + sl[idx])
 
 
 def test_newton_graph_matches_plain_launches(P):
