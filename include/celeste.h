@@ -201,16 +201,16 @@ int celeste_profile_stop(celeste_problem* p, celeste_profile_stats* out);
 /* The same evaluation as celeste_elbo_batch with want = ELBO | GRAD | HESS, for callers that may
  * not allocate device memory when they evaluate (a pre-sized arena, an allocator owned by another
  * framework, a request path that must not allocate).  The call allocates nothing: the kernels'
- * scratch (per-patch tables, per-pixel source moments, per-tile partial sums, per-source flags,
- * worklists, counters) lives in one fixed 8 MiB device array inside this library, which every GPU that loads
+ * scratch (per-patch tables, per-pixel source moments, per-tile partial sums, per-source flags and
+ * brightness constants, worklists, counters) lives in one fixed 8 MiB device array inside this library, which every GPU that loads
  * the library keeps until the process exits.
  * The paper has no counterpart; it is a deployment variant of the evaluation above.
  *   p must be bound and have its background rendered; theta, elbo, grad, hess as in
  *   celeste_elbo_batch (all four required).
- *   Limit: 432 * n_tiles, 4 * n_sources, 6880 * n_patches, 8 * n_pixels and
- *   4 * (n_tiles + n_patches + n_sources) bytes, each rounded up to 256, plus 512 must fit in
- *   8 MiB (e.g. ~1000 patches of 17 x 17 pixels); larger problems get CELESTE_ERR_INVALID_ARG
- *   before any launch.
+ *   Limit: 432 * n_tiles, 4 * n_sources, 6880 * n_patches, 8 * n_pixels,
+ *   4 * (n_tiles + n_patches + n_sources) and 340 * n_sources bytes, each rounded up to 256, plus
+ *   512 must fit in 8 MiB (e.g. ~1000 patches of 17 x 17 pixels); larger problems get
+ *   CELESTE_ERR_INVALID_ARG before any launch.
  *   The first call on a device looks up the array's device address with that device current;
  *   make that first call before any stream capture.
  *   Every call shares the one array: calls that overlap on the GPU (different streams, threads

@@ -32,12 +32,13 @@ extern "C" int celeste_elbo_batch(celeste_problem* p, const double* theta, unsig
   cudaError_t e = launch_set_flags(p->dev, flag, st);
   if (e != cudaSuccess) return cuda_fail(e, "set flags");
   if ((e = launch_worklists(p->dev, flag, st)) != cudaSuccess) return cuda_fail(e, "worklists");
+  if ((e = launch_tables(p->dev, theta, full, st)) != cudaSuccess) return cuda_fail(e, "tables");
   const int m0 = prof_mark(p, st);
-  e = full ? launch_full(p->dev, theta, st) : launch_value(p->dev, theta, false, st);
+  e = full ? launch_full_kernel(p->dev, st) : launch_value_kernel(p->dev, false, st);
   if (e != cudaSuccess) return cuda_fail(e, "pixel kernel");
   const int m1 = prof_mark(p, st);
   if (p->prof_on) (full ? p->prof_full : p->prof_value).push_back({m0, m1});
-  prof_count(p, 5);
+  prof_count(p, 6);
   e = full ? launch_assemble(p->dev, theta, true, (want & CELESTE_WANT_ELBO) ? elbo : nullptr,
                              (want & CELESTE_WANT_GRAD) ? grad : nullptr, (want & CELESTE_WANT_HESS) ? hess : nullptr, st)
            : launch_assemble_value(p->dev, theta, nullptr, elbo, st);

@@ -95,6 +95,7 @@ struct ProblemDev {
   float* partials;               // [n_tiles][NACC]
   float* vpartials;              // [n_tiles]
   int* flags;                    // [S] per-source work flags
+  SNConst* snc;                  // [S][5] per-source, per-band brightness constants (iota unset)
   int* wl;                       // worklists built from the flags: tiles [n_tiles], patches [n_patches], sources [S]
   int* wl_count;                 // [WL_INTS]: number of tiles, patches, sources in the worklists,
                                  // then the three queue heads

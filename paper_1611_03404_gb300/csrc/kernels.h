@@ -17,6 +17,9 @@ cudaError_t launch_full(const ProblemDev& P, const double* theta, cudaStream_t s
 // Tables (value) + value-only tile sums for the listed tiles (diff: differences from the stored
 // per-pixel source moments).
 cudaError_t launch_value(const ProblemDev& P, const double* theta, bool diff, cudaStream_t st);
+// The pixel kernels alone, on tables already built for the listed patches.
+cudaError_t launch_full_kernel(const ProblemDev& P, cudaStream_t st);
+cudaError_t launch_value_kernel(const ProblemDev& P, bool diff, cudaStream_t st);
 // Per-source float64 sum of the value-only tile sums minus the KL at theta; with theta_ref the
 // result is the ELBO change from theta_ref (value kernel run in difference mode).
 cudaError_t launch_assemble_value(const ProblemDev& P, const double* theta, const double* theta_ref, double* out,

@@ -193,11 +193,11 @@ __global__ void newton_finish_kernel(NewtonDev N, int32_t* iters, int32_t* statu
 }
 
 // Kernels launched by one Newton iteration (newton_iteration below).
-constexpr int NEWTON_KERNELS_PER_ITER = 10;
+constexpr int NEWTON_KERNELS_PER_ITER = 12;
 
 // The launches of one Newton iteration: subproblem step, value at the trial point, accept/reject,
 // full evaluation at the accepted points.  ev (4 events, or null) brackets the value and the full
-// evaluation; inside a stream capture they become event-record nodes.
+// pixel kernels; inside a stream capture they become event-record nodes.
 static cudaError_t newton_iteration(const ProblemDev& D, const NewtonDev& N, cudaStream_t st, cudaEvent_t* ev,
                                     bool capturing) {
   auto mark = [&](int k) -> cudaError_t {
@@ -209,16 +209,18 @@ static cudaError_t newton_iteration(const ProblemDev& D, const NewtonDev& N, cud
   tr_step_kernel<<<(S + TR_WARPS - 1) / TR_WARPS, 32 * TR_WARPS, 0, st>>>(N, D.flags);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = launch_worklists(D, FLAG_VALUE, st)) != cudaSuccess) return e;
+  if ((e = launch_tables(D, N.trial, false, st)) != cudaSuccess) return e;
   if ((e = mark(0)) != cudaSuccess) return e;
-  if ((e = launch_value(D, N.trial, true, st)) != cudaSuccess) return e;
+  if ((e = launch_value_kernel(D, true, st)) != cudaSuccess) return e;
   if ((e = mark(1)) != cudaSuccess) return e;
   if ((e = launch_assemble_value(D, N.trial, N.theta, N.Ltrial, st)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(N.count, 0, sizeof(int), st)) != cudaSuccess) return e;
   tr_update_kernel<<<(S + 127) / 128, 128, 0, st>>>(N, D.flags);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = launch_worklists(D, FLAG_FULL, st)) != cudaSuccess) return e;
+  if ((e = launch_tables(D, N.theta, true, st)) != cudaSuccess) return e;
   if ((e = mark(2)) != cudaSuccess) return e;
-  if ((e = launch_full(D, N.theta, st)) != cudaSuccess) return e;
+  if ((e = launch_full_kernel(D, st)) != cudaSuccess) return e;
   if ((e = mark(3)) != cudaSuccess) return e;
   return launch_assemble(D, N.theta, true, N.L, N.gL, N.HL, st);
 }
@@ -293,13 +295,14 @@ extern "C" int celeste_newton_batch(celeste_problem* p, double* theta, const cel
   newton_init_kernel<<<(S + 127) / 128, 128, 0, st>>>(N, D.flags);
   if ((e = launch_worklists(D, FLAG_FULL, st)) != cudaSuccess) return cuda_fail(e, "worklists");
   {
+    if ((e = launch_tables(D, theta, true, st)) != cudaSuccess) return cuda_fail(e, "tables");
     const int m0 = prof_mark(p, st);
-    if ((e = launch_full(D, theta, st)) != cudaSuccess) return cuda_fail(e, "full eval");
+    if ((e = launch_full_kernel(D, st)) != cudaSuccess) return cuda_fail(e, "full eval");
     const int m1 = prof_mark(p, st);
     if (prof) p->prof_full.push_back({m0, m1});
   }
   if ((e = launch_assemble(D, theta, true, N.L, N.gL, N.HL, st)) != cudaSuccess) return cuda_fail(e, "assemble");
-  prof_count(p, 5);
+  prof_count(p, 6);
 
   int it = 0, active = S;
   if (K > 1) {

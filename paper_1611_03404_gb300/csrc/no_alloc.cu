@@ -31,9 +31,9 @@ static void* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
 static size_t round256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // Layout of the array for one problem: partial sums, flags, counters, tables, source moments,
-// worklists and their counts.
+// worklists and their counts, per-source brightness constants.
 struct NoallocLayout {
-  size_t partials, flags, counters, ptab, srcmom, wl, wl_count, total;
+  size_t partials, flags, counters, ptab, srcmom, wl, wl_count, snc, total;
 };
 static NoallocLayout noalloc_layout(const celeste_problem* p) {
   NoallocLayout L;
@@ -52,6 +52,8 @@ static NoallocLayout noalloc_layout(const celeste_problem* p) {
   o += round256(sizeof(int) * (p->tiles.size() + p->patches.size() + (size_t)p->S));
   L.wl_count = o;
   o += round256(sizeof(int) * WL_INTS);
+  L.snc = o;
+  o += round256(sizeof(SNConst) * 5 * (size_t)p->S);
   L.total = o;
   return L;
 }
@@ -101,10 +103,11 @@ extern "C" int celeste_elbo_batch_noalloc(celeste_problem* p, const double* thet
   D.srcmom = reinterpret_cast<float2*>(b + NL.srcmom);
   D.wl = reinterpret_cast<int*>(b + NL.wl);
   D.wl_count = reinterpret_cast<int*>(b + NL.wl_count);
+  D.snc = reinterpret_cast<SNConst*>(b + NL.snc);
   cudaStream_t st = (cudaStream_t)stream;
   // The array keeps the previous call's contents: the counters must start at zero; the flags,
-  // worklists, tables, source moments and partial sums are fully rewritten below before they
-  // are read.
+  // worklists, brightness constants, tables, source moments and partial sums are fully rewritten
+  // below before they are read.
   cudaError_t e = cudaMemsetAsync(D.counters, 0, sizeof(unsigned long long) * 4, st);
   if (e != cudaSuccess) return cuda_fail(e, "clear counters");
   if ((e = launch_set_flags(D, FLAG_FULL, st)) != cudaSuccess) return cuda_fail(e, "set flags");

@@ -457,6 +457,11 @@ cudaError_t launch_full(const ProblemDev& P, const double* theta, cudaStream_t s
   if (P.n_tiles == 0) return cudaSuccess;
   cudaError_t e = launch_tables(P, theta, true, st);
   if (e != cudaSuccess) return e;
+  return launch_full_kernel(P, st);
+}
+
+cudaError_t launch_full_kernel(const ProblemDev& P, cudaStream_t st) {
+  if (P.n_tiles == 0) return cudaSuccess;
   const int g = std::max(1, std::min(P.n_tiles, P.n_sm * FULL_CTAS_PER_SM));
   switch (P.tile_pixels) {
     case 128: elbo_full_kernel<1><<<g, BLOCK, 0, st>>>(P); break;
@@ -471,6 +476,11 @@ cudaError_t launch_value(const ProblemDev& P, const double* theta, bool diff, cu
   if (P.n_tiles == 0) return cudaSuccess;
   cudaError_t e = launch_tables(P, theta, false, st);
   if (e != cudaSuccess) return e;
+  return launch_value_kernel(P, diff, st);
+}
+
+cudaError_t launch_value_kernel(const ProblemDev& P, bool diff, cudaStream_t st) {
+  if (P.n_tiles == 0) return cudaSuccess;
   const int d = diff ? 1 : 0;
   const int g = std::max(1, std::min(P.n_tiles, P.n_sm * VALUE_CTAS_PER_SM));
   switch (P.tile_pixels) {

@@ -296,6 +296,7 @@ void build_layout(celeste_problem* p) {
   L.counters = take(sizeof(unsigned long long) * 4);
   L.wl = take(sizeof(int) * (p->tiles.size() + NPch + S + 1));
   L.wl_count = take(sizeof(int) * WL_INTS);
+  L.snc = take(sizeof(SNConst) * 5 * S);
   // trust-region state
   L.nt_f = take(sizeof(double) * S);
   L.nt_g = take(sizeof(double) * NP * S);
@@ -375,6 +376,7 @@ extern "C" int celeste_problem_bind(celeste_problem* p, void* workspace, size_t 
   D.counters = reinterpret_cast<unsigned long long*>(base + L.counters);
   D.wl = reinterpret_cast<int*>(base + L.wl);
   D.wl_count = reinterpret_cast<int*>(base + L.wl_count);
+  D.snc = reinterpret_cast<SNConst*>(base + L.snc);
   D.n_sm = std::max(n_sm, 1);
   D.S = p->S;
   D.n_patches = (int)p->patches.size();

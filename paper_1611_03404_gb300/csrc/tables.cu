@@ -45,6 +45,73 @@ __device__ inline void galaxy_shape_f(double eta, double phi, double kappa, GalS
   g.d2[5] = {4.f * g.S.a, 4.f * g.S.b, 4.f * g.S.c};
 }
 
+// Brightness constants of every listed source for all five bands, in float64.  One warp per
+// source: lane 5t + b (t = type, b = band, lanes 0-9) evaluates the lognormal moments of l_b for
+// type t, lanes 0-4 then combine both types for band b.  Spreading the transcendental functions
+// over the lanes keeps the count of float64 warp instructions (each ~64 cycles here) per source
+// low; the tables below only copy the result.
+__global__ void source_const_kernel(ProblemDev P, const double* __restrict__ theta) {
+  const int lane = threadIdx.x & 31;
+  const int n = P.wl_count[WL_SOURCES];
+  const int* items = wl_list(P, WL_SOURCES);
+  const int nw = gridDim.x * (blockDim.x >> 5);
+  const int t = lane < 5 ? 0 : 1, b = lane % 5;   // meaningful for lanes < 10
+  for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < n; w += nw) {   // warp-uniform
+    const int s = items[w];
+    const double* th = theta + (size_t)s * NP;
+    // exp of the log-variances, lane 5t + k: k = 0 log flux, k = 1..4 colours j = k - 1
+    double ev = 0.0;
+    if (lane < 10) {
+      const int k = lane % 5;
+      ev = exp(th[k == 0 ? (t ? 10 : 8) : (t ? 23 : 15) + k - 1]);
+    }
+    double evk[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) evk[k] = __shfl_sync(0xffffffffu, ev, 5 * t + k);
+    double a[4];
+    color_row(b, a);
+    double m = th[t ? 9 : 7], v = evk[0];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      m = fma(a[j], th[(t ? 19 : 11) + j], m);
+      v = fma(a[j] * a[j], evk[1 + j], v);
+    }
+    double L1 = 0.0, L2 = 0.0, em = 0.0;
+    if (lane < 10) {
+      L1 = exp(m + 0.5 * v);
+      L2 = exp(2.0 * m + 2.0 * v);
+      em = expm1(v);
+    }
+    const double L10 = __shfl_sync(0xffffffffu, L1, b), L20 = __shfl_sync(0xffffffffu, L2, b);
+    const double em0 = __shfl_sync(0xffffffffu, em, b);
+    const double L11 = __shfl_sync(0xffffffffu, L1, 5 + b), L21 = __shfl_sync(0xffffffffu, L2, 5 + b);
+    const double em1 = __shfl_sync(0xffffffffu, em, 5 + b);
+    if (lane < 5) {
+      const double a1 = sigmoid_d(th[6]), a0 = sigmoid_d(-th[6]), aa = a0 * a1;
+      const double e = sigmoid_d(th[2]), ee = e * sigmoid_d(-th[2]);
+      SNConst c;
+      c.C0 = (float)(a0 * L10 * L10 * em0);
+      c.C1 = (float)(a1 * L11 * L11 * em1);
+      c.Cx = (float)aa;
+      c.L10 = (float)L10;
+      c.L11 = (float)L11;
+      c.A0 = (float)(a0 * L10);
+      c.A1 = (float)(a1 * L11);
+      c.B0 = (float)(a0 * L20);
+      c.B1 = (float)(a1 * L21);
+      c.aE0 = (float)(aa * L10);
+      c.aE1 = (float)(aa * L11);
+      c.aV0 = (float)(aa * L20);
+      c.aV1 = (float)(aa * L21);
+      c.iota = 0.f;
+      c.e = (float)e;
+      c.e1 = (float)ee;
+      c.e2 = (float)(ee * (1.0 - 2.0 * e));
+      P.snc[(size_t)s * 5 + b] = c;
+    }
+  }
+}
+
 // full = 1: galaxy derivative entries too; full = 0: precision and normaliser only.
 // 64-thread CTAs taking patches from the device work queue over the patch worklist.
 __global__ void __launch_bounds__(64) table_kernel(ProblemDev P, const double* __restrict__ theta, int full) {
@@ -112,8 +179,8 @@ __global__ void __launch_bounds__(64) table_kernel(ProblemDev P, const double* _
     out[TB_STAR + 4 * k + 2] = Pm.b;
     out[TB_STAR + 4 * k + 3] = Pm.c;
   } else if (tid == NGAL + NSTAR) {
-    SNConst c;
-    sn_constants(th, im.band, im.iota, c);
+    SNConst c = P.snc[(size_t)pt.source * 5 + im.band];
+    c.iota = im.iota;
     const float* cf = reinterpret_cast<const float*>(&c);
     for (int q = 0; q < (int)(sizeof(SNConst) / sizeof(float)); ++q) out[TB_SNC + q] = cf[q];
   }
@@ -122,6 +189,7 @@ __global__ void __launch_bounds__(64) table_kernel(ProblemDev P, const double* _
 
 cudaError_t launch_tables(const ProblemDev& P, const double* theta, bool full, cudaStream_t st) {
   if (P.n_patches == 0) return cudaSuccess;
+  source_const_kernel<<<std::max(1, std::min((P.S + 3) / 4, P.n_sm * 8)), 128, 0, st>>>(P, theta);
   const int blocks = std::max(1, std::min(P.n_patches, P.n_sm * 16));
   table_kernel<<<blocks, 64, 0, st>>>(P, theta, full ? 1 : 0);
   return cudaGetLastError();
