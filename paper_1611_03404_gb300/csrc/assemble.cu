@@ -1,4 +1,4 @@
-// Float64 assembly of each source's ELBO, gradient and Hessian from the per-tile pixel sums,
+// Assembly of each source's ELBO, gradient and Hessian from the per-tile pixel sums,
 // plus the KL term of q (paper, Sec. "Variational Inference": Eq. (1)-(3); q(a) Bernoulli,
 // q(r|a) lognormal, q(c|a) normal, each conjugate to its prior).
 //
@@ -6,9 +6,9 @@
 // the pixel-space mean mu = A u + o (so the pixel sums need no WCS); the u rows/columns are
 // mapped back with A before summing over the source's images.
 //
-// GB300 float64 latencies are long (a dependent FMA ~64 cycles, exp ~1100), so every
-// transcendental is evaluated once per source and in parallel across threads; the per-patch
-// work is plain multiply-adds spread over the CTA.
+// A float64 warp instruction occupies its SM sub-partition's FP64 pipe for ~64 cycles on this
+// part, whatever the number of active lanes, so every transcendental is evaluated once per source
+// and in parallel across threads, and only the objective and gradient are lifted in float64.
 #include <algorithm>
 
 #include "celeste_internal.cuh"
@@ -97,31 +97,62 @@ struct PatchLift {
   int band;
 };
 
+// Float32 copies of the lift quantities that only the Hessian uses.
+struct PatchLiftF {
+  float L1[2], L2[2], dL1[2][10], dL2[2][10], d2l1[2][10], d2l2[2][10], A[4];
+  float a0, a1, aa;
+};
+
+// ELBO and gradient are summed and lifted in float64 (the cross-pixel sums of the objective and
+// its gradient); the Hessian, whose per-pixel terms are float32 to begin with, in float32 with
+// compensated cross-tile sums.  On this part a float64 warp instruction costs ~64 cycles, a
+// float32 one a single issue slot, so the split cuts the kernel's float64 instructions about
+// fourfold.
 __global__ void __launch_bounds__(128) assemble_kernel(ProblemDev P, const double* __restrict__ theta, int full,
                                                        double* elbo, double* grad, double* hess) {
   const int tid = threadIdx.x, nt = blockDim.x;
-  __shared__ double sums[NACC];
-  __shared__ double Hs[NP * NP], gs[NP], HE[NP * NP], gE[NP];
-  __shared__ double Msym[NRED * NRED], nzK[NP], nzL[NP], ghat[NRED], H2[NP * NP];
+  constexpr int ND = ACC_HP;            // float64 sums: L, S1, S2
+  constexpr int NF = NACC - ACC_HP;     // float32 sums: HP, M
+  __shared__ double sd[ND];
+  __shared__ float sdf[ND], sf[NF];
+  __shared__ float Hs[NP * NP], HE[NP * NP], H2[NP * NP], Msym[NRED * NRED], nzKf[NP], nzLf[NP];
+  __shared__ double gs[NP], gE[NP], nzK[NP], nzL[NP], ghat[NRED];
   __shared__ int nzA[NP], nzB[NP];
   __shared__ PatchLift c;
+  __shared__ PatchLiftF cf;
   __shared__ SourceConst sc;
   __shared__ double Lsum, red[16];
   __shared__ int slot;
   for (int s = wl_next_cta(P, WL_SOURCES, slot); s >= 0; s = wl_next_cta(P, WL_SOURCES, slot)) {
   const double* th = theta + (size_t)s * NP;
-  for (int i = tid; i < NP * NP; i += nt) Hs[i] = 0.0;
+  for (int i = tid; i < NP * NP; i += nt) Hs[i] = 0.f;
   for (int i = tid; i < NP; i += nt) gs[i] = 0.0;
   if (tid == 0) Lsum = 0.0;
   source_const_parallel(th, sc, tid);
   __syncthreads();
+  if (tid == 0) {
+    cf.a0 = (float)sc.a0;
+    cf.a1 = (float)sc.a1;
+    cf.aa = (float)sc.aa;
+  }
   for (int p = P.src_patch[s]; p < P.src_patch[s + 1]; ++p) {
     const PatchDev pt = P.patches[p];
-    // ---- tile sums (float64, fixed order) and the band moments, in parallel
-    if (tid < NACC) {
+    // ---- tile sums (fixed order; float64 for the objective and gradient, compensated float32 for
+    //      the Hessian-only sums) and the band moments, in parallel
+    if (tid < ND) {
       double v = 0.0;
       for (int t = pt.tile_begin; t < pt.tile_end; ++t) v += (double)P.partials[(size_t)t * NACC + tid];
-      sums[tid] = v;
+      sd[tid] = v;
+      sdf[tid] = (float)v;
+    } else if (tid < NACC) {
+      float v = 0.f, comp = 0.f;
+      for (int t = pt.tile_begin; t < pt.tile_end; ++t) {
+        const float y = P.partials[(size_t)t * NACC + tid] - comp;
+        const float u = v + y;
+        comp = (u - v) - y;
+        v = u;
+      }
+      sf[tid - ND] = v;
     } else if (tid < NACC + 4) {
       const int k = tid - NACC, t = k & 1, second = k >> 1;
       const int band = P.images[pt.image].band;
@@ -132,13 +163,17 @@ __global__ void __launch_bounds__(128) assemble_kernel(ProblemDev P, const doubl
         m += arow[j] * th[bvar(t, 2 + j)];
         v += arow[j] * arow[j] * sc.ev[t][6 + j];
       }
-      if (second)
+      if (second) {
         c.L2[t] = exp(2.0 * m + 2.0 * v);
-      else
+        cf.L2[t] = (float)c.L2[t];
+      } else {
         c.L1[t] = exp(m + 0.5 * v);
+        cf.L1[t] = (float)c.L1[t];
+      }
       if (k == 0) c.band = band;
     } else if (tid < NACC + 8) {
       c.A[tid - NACC - 4] = P.images[pt.image].A[tid - NACC - 4];
+      cf.A[tid - NACC - 4] = (float)c.A[tid - NACC - 4];
     }
     __syncthreads();
     // ---- derivatives of the band moments over the type's brightness parameters
@@ -162,17 +197,21 @@ __global__ void __launch_bounds__(128) assemble_kernel(ProblemDev P, const doubl
       }
       if (which) {
         c.dL2[t][v] = c.L2[t] * dl;
-        c.d2l2[t][v] = d2;
+        cf.dL2[t][v] = (float)c.dL2[t][v];
+        cf.d2l2[t][v] = (float)d2;
       } else {
         c.dL1[t][v] = c.L1[t] * dl;
-        c.d2l1[t][v] = d2;
+        cf.dL1[t][v] = (float)c.dL1[t][v];
+        cf.d2l1[t][v] = (float)d2;
       }
     }
-    if (tid == 64) Lsum += sums[ACC_L];
+    if (tid == 64) Lsum += sd[ACC_L];
     __syncthreads();
-    const double* S1 = sums + ACC_S1;
-    const double* S2 = sums + ACC_S2;
-    // ---- reduced gradient
+    const double* S1 = sd + ACC_S1;
+    const double* S2 = sd + ACC_S2;
+    const float* S1h = sdf + ACC_S1;
+    const float* S2h = sdf + ACC_S2;
+    // ---- reduced gradient (float64)
     if (tid < NRED) {
       const double A0 = sc.a0 * c.L1[0], A1 = sc.a1 * c.L1[1], B0 = sc.a0 * c.L2[0], B1 = sc.a1 * c.L2[1];
       const int a = tid;
@@ -206,15 +245,17 @@ __global__ void __launch_bounds__(128) assemble_kernel(ProblemDev P, const doubl
         nzB[j] = 9 + t;
         nzL[j] = at * c.dL2[t][v];
       }
+      nzKf[j] = (float)nzK[j];
+      nzLf[j] = (float)nzL[j];
     }
     for (int i = tid; i < NRED * NRED; i += nt) {
       const int a = i / NRED, b = i % NRED;
-      Msym[i] = sums[ACC_M + (a <= b ? tri11d(a, b) : tri11d(b, a))];
+      Msym[i] = sf[ACC_M - ND + (a <= b ? tri11d(a, b) : tri11d(b, a))];
     }
-    // second-order part  sum_m w1 d2E[G] + w2 d2E[G^2], filled block by block (uniform work per
-    // thread within a block):  G6 x G6 from the kernel's sums; G6 x alpha; alpha x alpha;
+    // second-order part  sum_m w1 d2E[G] + w2 d2E[G^2] (float32), filled block by block (uniform
+    // work per thread within a block):  G6 x G6 from the kernel's sums; G6 x alpha; alpha x alpha;
     // G6 x brightness; alpha x brightness; brightness x brightness (same type only)
-    for (int i = tid; i < NP * NP; i += nt) H2[i] = 0.0;
+    for (int i = tid; i < NP * NP; i += nt) H2[i] = 0.f;
     __syncthreads();
     for (int q = tid; q < 21; q += nt) {
       int a = 0, rem = q;
@@ -223,34 +264,34 @@ __global__ void __launch_bounds__(128) assemble_kernel(ProblemDev P, const doubl
         ++a;
       }
       const int b = a + rem;
-      H2[a * NP + b] = H2[b * NP + a] = sums[ACC_HP + q];
+      H2[a * NP + b] = H2[b * NP + a] = sf[ACC_HP - ND + q];
     }
-    const double S1f[2] = {S1[0], S1[3]}, S2f[2] = {S2[0], S2[3]};
+    const float S1f[2] = {S1h[0], S1h[3]}, S2f[2] = {S2h[0], S2h[3]};
     for (int i = tid; i < 6 + 1 + 120 + 20 + 200; i += nt) {
       if (i < 6) {
         const int a = i;
-        const double s1f0 = a < 2 ? S1[1 + a] : 0.0, s2f0 = a < 2 ? S2[1 + a] : 0.0;
+        const float s1f0 = a < 2 ? S1h[1 + a] : 0.f, s2f0 = a < 2 ? S2h[1 + a] : 0.f;
         H2[a * NP + 6] = H2[6 * NP + a] =
-            sc.aa * (c.L1[1] * S1[4 + a] - c.L1[0] * s1f0 + c.L2[1] * S2[4 + a] - c.L2[0] * s2f0);
+            cf.aa * (cf.L1[1] * S1h[4 + a] - cf.L1[0] * s1f0 + cf.L2[1] * S2h[4 + a] - cf.L2[0] * s2f0);
       } else if (i == 6) {
-        H2[6 * NP + 6] =
-            sc.aa * (1.0 - 2.0 * sc.a1) * (c.L1[1] * S1f[1] - c.L1[0] * S1f[0] + c.L2[1] * S2f[1] - c.L2[0] * S2f[0]);
+        H2[6 * NP + 6] = cf.aa * (1.f - 2.f * cf.a1) *
+                         (cf.L1[1] * S1f[1] - cf.L1[0] * S1f[0] + cf.L2[1] * S2f[1] - cf.L2[0] * S2f[0]);
       } else if (i < 127) {
         const int k = i - 7, t = k / 60, a = (k % 60) / 10, v = k % 10, j = bvar(t, v);
-        const double s1 = t ? S1[4 + a] : (a < 2 ? S1[1 + a] : 0.0);
-        const double s2 = t ? S2[4 + a] : (a < 2 ? S2[1 + a] : 0.0);
-        H2[a * NP + j] = H2[j * NP + a] = (t ? sc.a1 : sc.a0) * (s1 * c.dL1[t][v] + s2 * c.dL2[t][v]);
+        const float s1 = t ? S1h[4 + a] : (a < 2 ? S1h[1 + a] : 0.f);
+        const float s2 = t ? S2h[4 + a] : (a < 2 ? S2h[1 + a] : 0.f);
+        H2[a * NP + j] = H2[j * NP + a] = (t ? cf.a1 : cf.a0) * (s1 * cf.dL1[t][v] + s2 * cf.dL2[t][v]);
       } else if (i < 147) {
         const int k = i - 127, t = k / 10, v = k % 10, j = bvar(t, v);
-        H2[6 * NP + j] = H2[j * NP + 6] = (t ? sc.aa : -sc.aa) * (S1f[t] * c.dL1[t][v] + S2f[t] * c.dL2[t][v]);
+        H2[6 * NP + j] = H2[j * NP + 6] = (t ? cf.aa : -cf.aa) * (S1f[t] * cf.dL1[t][v] + S2f[t] * cf.dL2[t][v]);
       } else {
         // d2 L = L (dlogL dlogL^T + diag(d2 log L)) within a type
         const int k = i - 147, t = k / 100, v = (k % 100) / 10, w = k % 10;
-        const double dl1v = c.dL1[t][v] / c.L1[t], dl1w = c.dL1[t][w] / c.L1[t];
-        const double dl2v = c.dL2[t][v] / c.L2[t], dl2w = c.dL2[t][w] / c.L2[t];
-        const double d2L1 = c.L1[t] * (dl1v * dl1w + (v == w ? c.d2l1[t][v] : 0.0));
-        const double d2L2 = c.L2[t] * (dl2v * dl2w + (v == w ? c.d2l2[t][v] : 0.0));
-        H2[bvar(t, v) * NP + bvar(t, w)] = (t ? sc.a1 : sc.a0) * (S1f[t] * d2L1 + S2f[t] * d2L2);
+        const float dl1v = cf.dL1[t][v] / cf.L1[t], dl1w = cf.dL1[t][w] / cf.L1[t];
+        const float dl2v = cf.dL2[t][v] / cf.L2[t], dl2w = cf.dL2[t][w] / cf.L2[t];
+        const float d2L1 = cf.L1[t] * (dl1v * dl1w + (v == w ? cf.d2l1[t][v] : 0.f));
+        const float d2L2 = cf.L2[t] * (dl2v * dl2w + (v == w ? cf.d2l2[t][v] : 0.f));
+        H2[bvar(t, v) * NP + bvar(t, w)] = (t ? cf.a1 : cf.a0) * (S1f[t] * d2L1 + S2f[t] * d2L2);
       }
     }
     __syncthreads();
@@ -261,11 +302,11 @@ __global__ void __launch_bounds__(128) assemble_kernel(ProblemDev P, const doubl
         ++r;
       }
       const int col = r + rem;
-      double v = nzK[r] * nzK[col] * Msym[nzA[r] * NRED + nzA[col]];
-      if (nzB[col] >= 0) v += nzK[r] * nzL[col] * Msym[nzA[r] * NRED + nzB[col]];
+      float v = nzKf[r] * nzKf[col] * Msym[nzA[r] * NRED + nzA[col]];
+      if (nzB[col] >= 0) v += nzKf[r] * nzLf[col] * Msym[nzA[r] * NRED + nzB[col]];
       if (nzB[r] >= 0) {
-        v += nzL[r] * nzK[col] * Msym[nzB[r] * NRED + nzA[col]];
-        if (nzB[col] >= 0) v += nzL[r] * nzL[col] * Msym[nzB[r] * NRED + nzB[col]];
+        v += nzLf[r] * nzKf[col] * Msym[nzB[r] * NRED + nzA[col]];
+        if (nzB[col] >= 0) v += nzLf[r] * nzLf[col] * Msym[nzB[r] * NRED + nzB[col]];
       }
       v += H2[r * NP + col];
       HE[r * NP + col] = v;
@@ -279,15 +320,15 @@ __global__ void __launch_bounds__(128) assemble_kernel(ProblemDev P, const doubl
     // map mu -> u: d/du_b = sum_a A[a][b] d/dmu_a
     for (int i = tid; i < NP * NP; i += nt) {
       const int r = i / NP, q = i % NP;
-      double v;
+      float v;
       if (r < 2 && q < 2) {
-        v = 0.0;
+        v = 0.f;
         for (int a = 0; a < 2; ++a)
-          for (int b = 0; b < 2; ++b) v += c.A[a * 2 + r] * c.A[b * 2 + q] * HE[a * NP + b];
+          for (int b = 0; b < 2; ++b) v += cf.A[a * 2 + r] * cf.A[b * 2 + q] * HE[a * NP + b];
       } else if (r < 2) {
-        v = c.A[0 * 2 + r] * HE[0 * NP + q] + c.A[1 * 2 + r] * HE[1 * NP + q];
+        v = cf.A[0 * 2 + r] * HE[0 * NP + q] + cf.A[1 * 2 + r] * HE[1 * NP + q];
       } else if (q < 2) {
-        v = c.A[0 * 2 + q] * HE[r * NP + 0] + c.A[1 * 2 + q] * HE[r * NP + 1];
+        v = cf.A[0 * 2 + q] * HE[r * NP + 0] + cf.A[1 * 2 + q] * HE[r * NP + 1];
       } else {
         v = HE[i];
       }
@@ -336,7 +377,7 @@ __global__ void __launch_bounds__(128) assemble_kernel(ProblemDev P, const doubl
           kl_normal_derivs(th, sc, P, r, t, dK, d2K);
           h = (t ? sc.a1 : sc.a0) * d2K;
         }
-        hess[(size_t)s * NP * NP + i] = Hs[i] - h;
+        hess[(size_t)s * NP * NP + i] = (double)Hs[i] - h;
       }
     }
     if (grad && tid < NP) {
