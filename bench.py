@@ -58,6 +58,8 @@ def parse():
                          "mosaic: 10x10 overlapping fields, 100,000 sources, 1-12 exposures each")
     ap.add_argument("--sources", type=int, default=1000)
     ap.add_argument("--tile", type=int, default=128, help="pixels per tile; 0 = autotune")
+    ap.add_argument("--hessian", default="fp32", choices=["fp32", "tf32", "bf16x3"],
+                    help="Jacobian cross-product of the Hessian: FP32 FMAs or tensor cores (TF32, BF16 hi+lo)")
     ap.add_argument("--seed", type=int, default=1611)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--e2e-steps", type=int, default=2)
@@ -71,12 +73,12 @@ def workload_config(args, tile):
                 "field_overlap": 0.2, "bands_per_field": "1-3", "exposures_per_source": "1-12",
                 "sources_per_gpu": 100_000, "patch_radius": "8-64 (brightness, 4 sigma of the widest component)",
                 "galaxy_fraction": 0.6, "elbo_tol": 1e-8, "max_iter": 50, "tile_pixels": tile,
-                "tile_choice": "autotuned" if args.tile == 0 else "fixed",
+                "hessian_syrk": args.hessian, "tile_choice": "autotuned" if args.tile == 0 else "fixed",
                 "l2": "inputs larger than L2 (GBs of patch pixels) and a 256 MiB flush between timed steps",
                 "parallelism": "one independently seeded mosaic per GPU"}
     return {"workload": f"field_2048x1489x5_{args.sources}src", "image_px": [2048, 1489], "bands": 5,
             "sources_per_gpu": args.sources, "patch_radius": "8-32 by brightness", "galaxy_fraction": 0.6,
-            "elbo_tol": 1e-8, "max_iter": 50, "tile_pixels": tile,
+            "elbo_tol": 1e-8, "max_iter": 50, "tile_pixels": tile, "hessian_syrk": args.hessian,
             "l2": "flushed between timed steps (256 MiB device write)",
             "parallelism": "one independently seeded field per GPU"}
 
@@ -209,7 +211,10 @@ def main():
     if tile == 0:
         from paper_1611_03404_gb300.autotune import tune_tile
         tile, tune = tune_tile(scene, device=dev)
-    prob = P.Problem(scene, device=dev, tile_pixels=tile)
+    hmode = {"fp32": P.HESS_FP32, "tf32": P.HESS_TF32, "bf16x3": P.HESS_BF16X3}[args.hessian]
+    if hmode != P.HESS_FP32:
+        tile = 128
+    prob = P.Problem(scene, device=dev, tile_pixels=tile, hessian_mode=hmode)
     counts = prob.counts()
     theta0 = torch.as_tensor(scene.theta0, device=dev).contiguous()
     theta = theta0.clone()

@@ -92,7 +92,13 @@ typedef struct {
  *   priors: {P(galaxy), mean of log r, variance of log r, colour mean, colour variance}.
  *   exp_* / dev_*: unit-flux circular mixtures sum_j nu_j N(0, tau_j I) (nu > 0, tau > 0)
  *           for the exponential and de Vaucouleurs profiles.
- *   tile_pixels: pixels per work tile (128, 256, 512 or 1024; 0 = default 128). */
+ *   tile_pixels: pixels per work tile (128, 256, 512 or 1024; 0 = default 128).
+ *   hessian_mode: how the pixel kernel forms the Hessian's Jacobian cross-product
+ *           sum_m Y_m^T C_m Y_m (the per-tile SYRK; everything else is unchanged):
+ *           CELESTE_HESS_FP32 (0) float32 FMAs; CELESTE_HESS_TF32 (1) tensor cores, TF32
+ *           operands; CELESTE_HESS_BF16X3 (2) tensor cores, BF16 hi + lo split operands
+ *           (hi*hi + hi*lo + lo*hi); float32 accumulation in all three.  Modes 1 and 2 need
+ *           tile_pixels 128. */
 typedef struct {
   int32_t n_images;
   const celeste_image_desc* images;
@@ -103,7 +109,10 @@ typedef struct {
   double exp_nu[CELESTE_NEXP], exp_tau[CELESTE_NEXP];
   double dev_nu[CELESTE_NDEV], dev_tau[CELESTE_NDEV];
   int32_t tile_pixels;
+  int32_t hessian_mode;
 } celeste_problem_desc;
+
+enum { CELESTE_HESS_FP32 = 0, CELESTE_HESS_TF32 = 1, CELESTE_HESS_BF16X3 = 2 };
 
 typedef struct celeste_problem celeste_problem;
 

@@ -15,6 +15,7 @@ from . import build as _build
 NPARAM = 27
 WANT_ELBO, WANT_GRAD, WANT_HESS = 1, 2, 4
 STATUS_CONVERGED, STATUS_MAX_ITER, STATUS_NONFINITE, STATUS_RADIUS_COLLAPSE = 0, 1, 2, 3
+HESS_FP32, HESS_TF32, HESS_BF16X3 = 0, 1, 2
 
 
 class CelesteError(RuntimeError):
@@ -33,7 +34,7 @@ class ProblemDesc(ctypes.Structure):
                 ("radius", ctypes.POINTER(ctypes.c_int32)), ("priors", ctypes.c_double * 5),
                 ("exp_nu", ctypes.c_double * 6), ("exp_tau", ctypes.c_double * 6),
                 ("dev_nu", ctypes.c_double * 8), ("dev_tau", ctypes.c_double * 8),
-                ("tile_pixels", ctypes.c_int32)]
+                ("tile_pixels", ctypes.c_int32), ("hessian_mode", ctypes.c_int32)]
 
 
 class NewtonOpts(ctypes.Structure):
@@ -115,7 +116,7 @@ class Problem:
     .psf[3,6,6]), .u0 [S,2], .radius [S], .priors [5] and the exp/deV mixture tables.
     device_pixels: optional list of CUDA float32 tensors already holding the images."""
 
-    def __init__(self, scene, device="cuda", tile_pixels=128, device_pixels=None, stream=None):
+    def __init__(self, scene, device="cuda", tile_pixels=128, device_pixels=None, stream=None, hessian_mode=0):
         L = lib()
         self.device = torch.device(device)
         if device_pixels is None:
@@ -146,6 +147,7 @@ class Problem:
         desc.dev_nu[:] = [float(v) for v in scene.dev_nu]
         desc.dev_tau[:] = [float(v) for v in scene.dev_tau]
         desc.tile_pixels = int(tile_pixels)
+        desc.hessian_mode = int(hessian_mode)
         h = ctypes.c_void_p()
         _check(L.celeste_problem_create(ctypes.byref(desc), ctypes.byref(h)))
         self.handle = h
@@ -232,7 +234,7 @@ def tr_solve_batch(B, g, delta, stream=None):
 class HostProblem:
     """Layout-only handle (no device memory): validation and counts, usable without a GPU."""
 
-    def __init__(self, scene, tile_pixels=256):
+    def __init__(self, scene, tile_pixels=256, hessian_mode=0):
         L = lib()
         n = len(scene.images)
         self._imgs = (ImageDesc * n)()
@@ -258,6 +260,7 @@ class HostProblem:
         desc.dev_nu[:] = [float(v) for v in scene.dev_nu]
         desc.dev_tau[:] = [float(v) for v in scene.dev_tau]
         desc.tile_pixels = int(tile_pixels)
+        desc.hessian_mode = int(hessian_mode)
         self.desc = desc
         h = ctypes.c_void_p()
         _check(L.celeste_problem_create(ctypes.byref(desc), ctypes.byref(h)))

@@ -101,7 +101,7 @@ struct ProblemDev {
                                  // then the three queue heads
   int* err;                      // [4] device error words
   unsigned long long* counters;  // [4]: full-kernel pixels, value-kernel pixels
-  int S, n_patches, n_tiles, tile_pixels, n_sm;
+  int S, n_patches, n_tiles, tile_pixels, n_sm, hmode;
   double priors[5];
   double log_var_r, log_var_c, log_phi, log1m_phi, logit_phi;   // logs of the priors (host-computed)
   float nu[NMIX], tau[NMIX];     // exp (0..5) then deV (6..13)

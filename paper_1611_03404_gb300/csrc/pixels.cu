@@ -19,6 +19,8 @@
 // brings the patch table and the tile's pixel records into shared memory with two TMA bulk
 // copies on one mbarrier.  Each thread evaluates its pixels; each warp reduce-scatters the 108
 // per-pixel contributions so that lane l keeps sums l, l+32, l+64, l+96 (4 registers, not 108).
+#include <cuda_bf16.h>
+
 #include <algorithm>
 #include <utility>
 
@@ -126,22 +128,111 @@ __device__ __forceinline__ float slot(const PixelCtx& c) {
   }
 }
 
-template <int CH, int... I>
+// NoM: leave out the Jacobian cross-product sums (formed on the tensor cores instead).
+template <int CH, bool NoM = false, int... I>
 __device__ __forceinline__ void fill_chunk(float (&v)[32], const PixelCtx& c, std::integer_sequence<int, I...>) {
-  ((v[I] = slot<32 * CH + I>(c)), ...);
+  ((v[I] = (NoM && 32 * CH + I >= ACC_M) ? 0.f : slot<32 * CH + I>(c)), ...);
+}
+
+// ---------------------------------------------------------------- tensor-core Jacobian SYRK
+// The cross-product block M_ab = sum_m ta_a yE_b + ua_a yV_b (a, b < 11) as one small GEMM per
+// warp and 32 pixels: M = A' B' with A' = [ta | ua] (11 x 64, padded to 16 rows) and
+// B' = [yE ; yV] (64 x 11, padded to 16 columns), K = 2 x 32 pixel terms.  Each lane stages its
+// pixel's 44 numbers in shared memory (A' rows and B'^T rows of 68 floats: conflict-free stores
+// and fragment loads), then the warp issues mma.sync: TF32 (m16n8k8, 8 k-steps x 2 n-tiles) or
+// BF16 with each operand split into hi + lo (m16n8k16, 4 k-steps x 2 n-tiles x 3 products);
+// float32 accumulators stay in registers across the tile's pixels.
+constexpr int SYRK_LD = 68;
+
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ void mma_tf32(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                         uint32_t b0, uint32_t b1) {
+  asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+               "{%0,%1,%2,%3};"
+               : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+               : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                         uint32_t b0, uint32_t b1) {
+  asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+               "{%0,%1,%2,%3};"
+               : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+               : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// Two consecutive floats (k, k+1) split into bf16 hi and lo pairs, the lower k in the low half.
+__device__ __forceinline__ void split_bf16x2(const float* p, uint32_t& hi, uint32_t& lo) {
+  const float2 x = *reinterpret_cast<const float2*>(p);
+  const __nv_bfloat162 h = __floats2bfloat162_rn(x.x, x.y);
+  const float2 hf = __bfloat1622float2(h);
+  const __nv_bfloat162 l = __floats2bfloat162_rn(x.x - hf.x, x.y - hf.y);
+  hi = *reinterpret_cast<const uint32_t*>(&h);
+  lo = *reinterpret_cast<const uint32_t*>(&l);
+}
+
+// D[nt] (16 x 8 tiles nt = 0, 1) += A' B' for this warp's staged 32 pixels.
+template <int HM>
+__device__ __forceinline__ void syrk_mma(const float (*As)[SYRK_LD], const float (*Bt)[SYRK_LD], float (&d)[2][4],
+                                         int lane) {
+  const int g = lane >> 2, t = lane & 3;
+  if constexpr (HM == 1) {
+#pragma unroll
+    for (int k0 = 0; k0 < 64; k0 += 8) {
+      const uint32_t a0 = to_tf32(As[g][k0 + t]), a1 = to_tf32(As[g + 8][k0 + t]);
+      const uint32_t a2 = to_tf32(As[g][k0 + t + 4]), a3 = to_tf32(As[g + 8][k0 + t + 4]);
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt) {
+        const uint32_t b0 = to_tf32(Bt[8 * nt + g][k0 + t]), b1 = to_tf32(Bt[8 * nt + g][k0 + t + 4]);
+        mma_tf32(d[nt], a0, a1, a2, a3, b0, b1);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int k0 = 0; k0 < 64; k0 += 16) {
+      uint32_t ah[4], al[4];
+      split_bf16x2(&As[g][k0 + 2 * t], ah[0], al[0]);
+      split_bf16x2(&As[g + 8][k0 + 2 * t], ah[1], al[1]);
+      split_bf16x2(&As[g][k0 + 2 * t + 8], ah[2], al[2]);
+      split_bf16x2(&As[g + 8][k0 + 2 * t + 8], ah[3], al[3]);
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt) {
+        uint32_t bh0, bl0, bh1, bl1;
+        split_bf16x2(&Bt[8 * nt + g][k0 + 2 * t], bh0, bl0);
+        split_bf16x2(&Bt[8 * nt + g][k0 + 2 * t + 8], bh1, bl1);
+        mma_bf16(d[nt], ah[0], ah[1], ah[2], ah[3], bh0, bh1);
+        mma_bf16(d[nt], ah[0], ah[1], ah[2], ah[3], bl0, bl1);
+        mma_bf16(d[nt], al[0], al[1], al[2], al[3], bh0, bh1);
+      }
+    }
+  }
 }
 
 // ------------------------------------------------------------------------------ full kernel
-template <int PPT>
+// HM: 0 all sums on the FP32 pipes; 1 / 2 the Jacobian cross-product on the tensor cores with
+// TF32 / BF16 hi+lo operands.
+template <int PPT, int HM>
 __global__ void __launch_bounds__(BLOCK) elbo_full_kernel(ProblemDev P) {
   __shared__ __align__(16) float tab[TB_FLOATS];
   __shared__ __align__(16) float4 spix[BLOCK * PPT];
   __shared__ __align__(8) uint64_t bar;
   __shared__ float red[BLOCK / 32][128];
+  __shared__ __align__(16) float syrk[HM ? BLOCK / 32 : 1][2][16][SYRK_LD];
 
   __shared__ int slot;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid == 0) mbar_init(&bar, 1);
+  if constexpr (HM != 0) {   // padding rows 11..15 of A' and B'^T stay zero
+    for (int i = lane; i < 5 * SYRK_LD; i += 32) {
+      syrk[warp][0][11 + i / SYRK_LD][i % SYRK_LD] = 0.f;
+      syrk[warp][1][11 + i / SYRK_LD][i % SYRK_LD] = 0.f;
+    }
+  }
   __syncthreads();
   uint32_t phase = 0;
   for (int tile = wl_next_cta(P, WL_TILES, slot); tile >= 0; tile = wl_next_cta(P, WL_TILES, slot), phase ^= 1u) {
@@ -154,6 +245,7 @@ __global__ void __launch_bounds__(BLOCK) elbo_full_kernel(ProblemDev P) {
   }
   const SNConst c = *reinterpret_cast<const SNConst*>(&tab[TB_SNC]);
   float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  float dm[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};   // tensor-core M block (HM != 0)
 
 #pragma unroll 1
   for (int r = 0; r < PPT; ++r) {
@@ -334,7 +426,7 @@ __global__ void __launch_bounds__(BLOCK) elbo_full_kernel(ProblemDev P) {
     cx.A0w1 = cx.w1 * c.A0;
     cx.B0w2x2 = 2.f * cx.w2 * c.B0;
 
-    {
+    if constexpr (HM == 0) {
       float v[32];
       fill_chunk<0>(v, cx, std::make_integer_sequence<int, 32>{});
       acc[0] += warp_reduce_scatter32(v, lane);
@@ -344,12 +436,44 @@ __global__ void __launch_bounds__(BLOCK) elbo_full_kernel(ProblemDev P) {
       acc[2] += warp_reduce_scatter32(v, lane);
       fill_chunk<3>(v, cx, std::make_integer_sequence<int, 32>{});
       acc[3] += warp_reduce_scatter32(v, lane);
+    } else {
+      // chunks 0 and 1 hold every sum but the cross-product block (slots >= ACC_M = 42)
+      float v[32];
+      fill_chunk<0, true>(v, cx, std::make_integer_sequence<int, 32>{});
+      acc[0] += warp_reduce_scatter32(v, lane);
+      fill_chunk<1, true>(v, cx, std::make_integer_sequence<int, 32>{});
+      acc[1] += warp_reduce_scatter32(v, lane);
+      float (*As)[SYRK_LD] = syrk[warp][0];
+      float (*Bt)[SYRK_LD] = syrk[warp][1];
+#pragma unroll
+      for (int a = 0; a < NRED; ++a) {
+        As[a][lane] = cx.ta[a];
+        As[a][32 + lane] = cx.ua[a];
+        Bt[a][lane] = cx.yE[a];
+        Bt[a][32 + lane] = cx.yV[a];
+      }
+      __syncwarp();
+      syrk_mma<HM>(As, Bt, dm, lane);
+      __syncwarp();   // the staging area is rewritten for the next 32 pixels
     }
   }
 
   // ---- combine the warps: sum q lives in lane q % 32 of chunk q / 32
 #pragma unroll
   for (int ch = 0; ch < 4; ++ch) red[warp][32 * ch + lane] = acc[ch];
+  if constexpr (HM != 0) {
+    // D fragment (tile nt): rows g, g + 8; columns 8 nt + 2 t, 8 nt + 2 t + 1.  Entry (a, b) with
+    // a <= b < 11 is sum ACC_M + tri(a, b) (the block is symmetric; its upper half is kept).
+    __syncwarp();
+    const int g = lane >> 2, tq = lane & 3;
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int a = g + (e >> 1) * 8, b = 8 * nt + 2 * tq + (e & 1);
+        if (a <= b && b < NRED) red[warp][ACC_M + a * NRED - a * (a - 1) / 2 + (b - a)] = dm[nt][e];
+      }
+  }
   __syncthreads();
   if (tid < NACC) {
     float v = 0.f;
@@ -463,11 +587,19 @@ cudaError_t launch_full(const ProblemDev& P, const double* theta, cudaStream_t s
 cudaError_t launch_full_kernel(const ProblemDev& P, cudaStream_t st) {
   if (P.n_tiles == 0) return cudaSuccess;
   const int g = std::max(1, std::min(P.n_tiles, P.n_sm * FULL_CTAS_PER_SM));
+  if (P.hmode == 1) {
+    elbo_full_kernel<1, 1><<<g, BLOCK, 0, st>>>(P);   // the create call admits these only with 128-pixel tiles
+    return cudaGetLastError();
+  }
+  if (P.hmode == 2) {
+    elbo_full_kernel<1, 2><<<g, BLOCK, 0, st>>>(P);
+    return cudaGetLastError();
+  }
   switch (P.tile_pixels) {
-    case 128: elbo_full_kernel<1><<<g, BLOCK, 0, st>>>(P); break;
-    case 256: elbo_full_kernel<2><<<g, BLOCK, 0, st>>>(P); break;
-    case 512: elbo_full_kernel<4><<<g, BLOCK, 0, st>>>(P); break;
-    default: elbo_full_kernel<8><<<g, BLOCK, 0, st>>>(P); break;
+    case 128: elbo_full_kernel<1, 0><<<g, BLOCK, 0, st>>>(P); break;
+    case 256: elbo_full_kernel<2, 0><<<g, BLOCK, 0, st>>>(P); break;
+    case 512: elbo_full_kernel<4, 0><<<g, BLOCK, 0, st>>>(P); break;
+    default: elbo_full_kernel<8, 0><<<g, BLOCK, 0, st>>>(P); break;
   }
   return cudaGetLastError();
 }

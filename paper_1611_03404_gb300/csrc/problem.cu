@@ -116,6 +116,10 @@ extern "C" int celeste_problem_create(const celeste_problem_desc* d, celeste_pro
   int tp = d->tile_pixels ? d->tile_pixels : 128;
   if (tp != 128 && tp != 256 && tp != 512 && tp != 1024)
     return fail(CELESTE_ERR_INVALID_ARG, "tile_pixels must be 128, 256, 512 or 1024");
+  if (d->hessian_mode < CELESTE_HESS_FP32 || d->hessian_mode > CELESTE_HESS_BF16X3)
+    return fail(CELESTE_ERR_INVALID_ARG, "hessian_mode must be 0, 1 or 2");
+  if (d->hessian_mode != CELESTE_HESS_FP32 && tp != 128)
+    return fail(CELESTE_ERR_INVALID_ARG, "tensor-core hessian modes need tile_pixels 128");
   for (int n = 0; n < d->n_images; ++n) {
     const celeste_image_desc& im = d->images[n];
     if (im.height < 2 || im.width < 2 || im.height > (1 << 20) || im.width > (1 << 20))
@@ -162,6 +166,7 @@ extern "C" int celeste_problem_create(const celeste_problem_desc* d, celeste_pro
   celeste_problem* p = new celeste_problem();
   p->S = d->n_sources;
   p->tile_pixels = tp;
+  p->hessian_mode = d->hessian_mode;
   p->images.assign(d->images, d->images + d->n_images);
   p->u0.assign(d->u0, d->u0 + 2 * (size_t)d->n_sources);
   p->radius.assign(d->radius, d->radius + d->n_sources);
@@ -382,6 +387,7 @@ extern "C" int celeste_problem_bind(celeste_problem* p, void* workspace, size_t 
   D.n_patches = (int)p->patches.size();
   D.n_tiles = (int)p->tiles.size();
   D.tile_pixels = p->tile_pixels;
+  D.hmode = p->hessian_mode;
   std::memcpy(D.priors, p->priors, sizeof(D.priors));
   D.log_var_r = std::log(p->priors[2]);
   D.log_var_c = std::log(p->priors[4]);

@@ -23,6 +23,7 @@ int cuda_fail(cudaError_t e, const char* what);
 struct celeste_problem {
   int S = 0;
   int tile_pixels = 256;
+  int hessian_mode = 0;
   std::vector<celeste_image_desc> images;
   std::vector<double> u0;
   std::vector<int> radius;

@@ -111,3 +111,13 @@ def test_validation_rejects_bad_descriptors(pkg):
     sc.priors = np.array([1.5, 2.0, 1.0, 0.0, 0.25])
     _expect_invalid(pkg, sc)
     _expect_invalid(pkg, base(), tile_pixels=100)
+
+
+def test_hessian_mode_validation(pkg):
+    """The tensor-core SYRK modes exist for 128-pixel tiles only; unknown modes are refused."""
+    sc = synth.tiny(seed=1, n_sources=2, n_images=2)
+    for mode in (pkg.HESS_FP32, pkg.HESS_TF32, pkg.HESS_BF16X3):
+        assert pkg.HostProblem(sc, tile_pixels=128, hessian_mode=mode).counts()["sources"] == 2
+    for mode, tile in ((3, 128), (-1, 128), (pkg.HESS_TF32, 256), (pkg.HESS_BF16X3, 512)):
+        with pytest.raises(pkg.CelesteError, match="invalid argument"):
+            pkg.HostProblem(sc, tile_pixels=tile, hessian_mode=mode)
