@@ -58,6 +58,11 @@ def parse():
                          "mosaic: 10x10 overlapping fields, 100,000 sources, 1-12 exposures each")
     ap.add_argument("--sources", type=int, default=1000)
     ap.add_argument("--tile", type=int, default=128, help="pixels per tile; 0 = autotune")
+    ap.add_argument("--warm-start", action="store_true",
+                    help="learned warm start: train the CNN on (patch, converged parameters) pairs of two freshly "
+                         "seeded workloads of the same kind, then start every timed Newton solve from its prediction "
+                         "(inference inside the timed region)")
+    ap.add_argument("--ws-epochs", type=int, default=6)
     ap.add_argument("--hessian", default="fp32", choices=["fp32", "tf32", "bf16x3"],
                     help="Jacobian cross-product of the Hessian: FP32 FMAs or tensor cores (TF32, BF16 hi+lo)")
     ap.add_argument("--seed", type=int, default=1611)
@@ -73,12 +78,13 @@ def workload_config(args, tile):
                 "field_overlap": 0.2, "bands_per_field": "1-3", "exposures_per_source": "1-12",
                 "sources_per_gpu": 100_000, "patch_radius": "8-64 (brightness, 4 sigma of the widest component)",
                 "galaxy_fraction": 0.6, "elbo_tol": 1e-8, "max_iter": 50, "tile_pixels": tile,
-                "hessian_syrk": args.hessian, "tile_choice": "autotuned" if args.tile == 0 else "fixed",
+                "hessian_syrk": args.hessian, "warm_start": "cnn" if args.warm_start else None, "tile_choice": "autotuned" if args.tile == 0 else "fixed",
                 "l2": "inputs larger than L2 (GBs of patch pixels) and a 256 MiB flush between timed steps",
                 "parallelism": "one independently seeded mosaic per GPU"}
     return {"workload": f"field_2048x1489x5_{args.sources}src", "image_px": [2048, 1489], "bands": 5,
             "sources_per_gpu": args.sources, "patch_radius": "8-32 by brightness", "galaxy_fraction": 0.6,
             "elbo_tol": 1e-8, "max_iter": 50, "tile_pixels": tile, "hessian_syrk": args.hessian,
+            "warm_start": "cnn" if args.warm_start else None,
             "l2": "flushed between timed steps (256 MiB device write)",
             "parallelism": "one independently seeded field per GPU"}
 
@@ -221,10 +227,26 @@ def main():
     delta = torch.zeros(scene.n_sources, dtype=torch.float64, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
-    def step():
+    net, ws_info = None, None
+    if args.warm_start:
+        net, ws_info = train_warm_start(args, P, dev, rank)
+        # the plain form on the same workload, for the iterations the warm start saves (untimed)
         theta.copy_(theta0)
+        prob.render_background(theta0)
+        _, it_cat, st_cat, _ = prob.newton_batch(theta, delta.zero_())
+        ws_info["iters_mean_catalog_start"] = float(it_cat.double().mean())
+        ws_info["converged_catalog_start"] = int((st_cat == P.STATUS_CONVERGED).sum())
+        th_cat = theta.clone()
+
+    def step():
         delta.zero_()
         prob.render_background(theta0)
+        if net is not None:
+            from paper_1611_03404_gb300 import cnn
+            pred = net.predict(prob.extract_patches())
+            theta.copy_(cnn.warm_start(theta0, pred))
+        else:
+            theta.copy_(theta0)
         return prob.newton_batch(theta, delta)
 
     for _ in range(max(args.warmup, 0)):
@@ -250,6 +272,15 @@ def main():
         prof = prof_stats = prob.profile_stop()
     conv = int((status == P.STATUS_CONVERGED).sum())
     iters_mean = float(iters.double().mean())
+    if ws_info is not None:
+        from paper_1611_03404_gb300 import cnn
+        ws_info["iters_mean_warm_start"] = iters_mean
+        ws_info["iters_saved_mean"] = ws_info["iters_mean_catalog_start"] - iters_mean
+        pred = net.predict(prob.extract_patches())
+        tgt = cnn.training_targets(th_cat, torch.as_tensor(scene.u0, device=dev))
+        ok = (st_cat == P.STATUS_CONVERGED)
+        rmse = ((pred - tgt)[ok] / net.sd).pow(2).mean(0).sqrt()
+        ws_info["rmse_vs_converged_standardised"] = [round(float(v), 3) for v in rmse]
     iters_max = int(iters.max())
     status_counts = {name: int((status == code).sum()) for name, code in
                      (("converged", P.STATUS_CONVERGED), ("max_iter", P.STATUS_MAX_ITER),
@@ -328,7 +359,7 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": "sources/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(args, tile),
-                "autotune_us_per_1000px": tune,
+                "autotune_us_per_1000px": tune, "warm_start": ws_info,
                 "pixel_evals_per_s": px_rate, "converged": conv, "newton_iters_mean": iters_mean,
                 "newton_iters_max": iters_max, "status_counts": status_counts,
                 "layout": counts, "wall_s_timed": wall,
@@ -344,6 +375,43 @@ def main():
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def train_warm_start(args, P, dev, rank):
+    """Trains the warm-start network on (patch, converged parameters) pairs of two freshly seeded
+    workloads of the bench's kind (Newton from their catalogs, neighbours fixed at the catalog)."""
+    import torch
+    import synth
+    from paper_1611_03404_gb300 import cnn
+    t0 = time.perf_counter()
+    xs, ts = [], []
+    for k in (101, 102):
+        if args.workload == "mosaic":
+            from synth.mosaic import mosaic
+            sc = mosaic(seed=args.seed + rank + k, device=dev)
+        else:
+            sc = synth.field(seed=args.seed + rank + k, n_sources=args.sources)
+        pr = P.Problem(sc, device=dev, tile_pixels=128)
+        th = torch.as_tensor(sc.theta0, device=dev).contiguous()
+        pr.render_background(th.clone())
+        _, _, st, _ = pr.newton_batch(th)
+        ok = st == P.STATUS_CONVERGED
+        xs.append(pr.extract_patches()[ok])
+        ts.append(cnn.training_targets(th[ok], torch.as_tensor(sc.u0, device=dev)[ok]))
+        pr.close()
+        del sc
+    x, t = torch.cat(xs).contiguous(), torch.cat(ts).contiguous()
+    t_data = time.perf_counter() - t0
+    net = cnn.WarmStartCNN(dev, seed=args.seed)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    hist = net.train(x, t, epochs=args.ws_epochs, batch=512, lr=2e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t1
+    return net, {"train_pairs": int(x.shape[0]), "epochs": args.ws_epochs, "batch": 512,
+                 "loss_first_last": [hist[0], hist[-1]], "data_seconds": t_data, "train_seconds": t_train,
+                 "train_pairs_per_s": x.shape[0] * args.ws_epochs / t_train,
+                 "params_from_network": "type logit, log variances of the log fluxes and colours"}
 
 
 def _build_hash(P):

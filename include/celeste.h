@@ -227,6 +227,54 @@ int celeste_profile_stop(celeste_problem* p, celeste_profile_stats* out);
 int celeste_elbo_batch_noalloc(celeste_problem* p, const double* theta, double* elbo, double* grad,
                                double* hess, celeste_stream_t stream);
 
+/* ---------------------------------------------------------------- learned warm start
+ * A small CNN maps a source's 5-band 32 x 32 patch to initial variational parameters; Newton
+ * (celeste_newton_batch) then runs from that start to the same tolerance as from any other, so
+ * the network only changes where the solve begins.  The paper's model has no such network; it is
+ * the warm start of the workload's learned-part configuration.
+ * Network: conv3x3 5->32 (stride 1), 32->64, 64->64, 64->64 (stride 2 each), padding 1, ReLU ->
+ * 4 x 4 x 64 = 1024 -> fully connected 256, ReLU -> 27.  Activations NHWC BF16 (uint16_t bit
+ * patterns), products on the tensor cores with FP32 accumulation, FP32 master parameters.
+ * Parameter vector (FP32, celeste_cnn_param_count() entries, and a BF16 copy of the same length):
+ *   W1 [32][3][3][5], b1 [32], W2 [64][3][3][32], b2 [64], W3 [64][3][3][64], b3 [64],
+ *   W4 [64][3][3][64], b4 [64], W5 [256][1024] (input index (h * 4 + w) * 64 + c), b5 [256],
+ *   W6 [27][256], b6 [27].
+ * All pointers are device memory owned by the caller; all calls are asynchronous on `stream`. */
+int64_t celeste_cnn_param_count(void);
+
+/* Activation workspace for a batch (bytes; the buffer must be 256-byte aligned). */
+size_t celeste_cnn_workspace_bytes(int batch);
+
+/* He-normal weights (std sqrt(2 / fan_in); the last layer times 0.1) from a counter-based
+ * generator seeded by `seed`, zero biases; writes both copies. */
+int celeste_cnn_init(float* params, uint16_t* params_bf16, uint64_t seed, celeste_stream_t stream);
+
+/* y [batch][27] = network(x [batch][32][32][5]); with out_scale / out_shift (both or neither,
+ * [27]) the output is y * scale + shift.  Keeps the activations in ws for celeste_cnn_backward. */
+int celeste_cnn_forward(const float* params, const uint16_t* params_bf16, const uint16_t* x, int batch,
+                        const float* out_scale, const float* out_shift, float* y, void* ws, size_t ws_bytes,
+                        celeste_stream_t stream);
+
+/* grad [param_count] += d loss / d params given dy = d loss / d y [batch][27], after a forward
+ * call on the same x, ws and parameters (without scale / shift). */
+int celeste_cnn_backward(const float* params, const uint16_t* params_bf16, const uint16_t* x, const float* dy,
+                         int batch, float* grad, void* ws, size_t ws_bytes, celeste_stream_t stream);
+
+/* loss (one double, accumulated) += mean over [batch][27] of weight_j (y - target)^2 and
+ * dy = its gradient; weight [27] may be NULL (all ones). */
+int celeste_cnn_mse(const float* y, const float* target, const float* weight, int batch, float* dy, double* loss,
+                    celeste_stream_t stream);
+
+/* One AdamW step (bias-corrected; decoupled weight decay) on the FP32 parameters, refreshing the
+ * BF16 copy; m, v: FP32 moment buffers of param_count entries; step >= 1. */
+int celeste_cnn_adamw(float* params, uint16_t* params_bf16, float* m, float* v, const float* grad, float lr,
+                      float beta1, float beta2, float eps, float weight_decay, int step, celeste_stream_t stream);
+
+/* Network input of every source of a bound problem: x [S][32][32][5] (BF16), band b taken from
+ * the source's first patch in an image of band b, centred on its patch centre, pixel value
+ * asinh((count - sky) / sqrt(sky)), zero where the band is missing or outside the image. */
+int celeste_extract_patches(celeste_problem* p, uint16_t* x, celeste_stream_t stream);
+
 /* Release the problem (not the caller's workspace).  NULL is ignored. */
 void celeste_problem_destroy(celeste_problem* p);
 

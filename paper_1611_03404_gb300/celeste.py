@@ -52,7 +52,9 @@ class ProfileStats(ctypes.Structure):
 EXPORTED = ["celeste_problem_create", "celeste_problem_workspace_bytes", "celeste_problem_counts",
             "celeste_problem_bind", "celeste_render_background", "celeste_elbo_batch", "celeste_newton_batch",
             "celeste_problem_destroy", "celeste_strerror", "celeste_last_error_detail", "celeste_profile_start",
-            "celeste_profile_stop", "celeste_tr_solve_batch", "celeste_elbo_batch_noalloc"]
+            "celeste_profile_stop", "celeste_tr_solve_batch", "celeste_elbo_batch_noalloc", "celeste_cnn_param_count",
+            "celeste_cnn_workspace_bytes", "celeste_cnn_init", "celeste_cnn_forward", "celeste_cnn_backward",
+            "celeste_cnn_mse", "celeste_cnn_adamw", "celeste_extract_patches"]
 
 
 def load_library(path=None):
@@ -76,6 +78,15 @@ def load_library(path=None):
         "celeste_profile_stop": (ctypes.c_int, [vp, ctypes.POINTER(ProfileStats)]),
         "celeste_tr_solve_batch": (ctypes.c_int, [dp, dp, dp, ctypes.c_int, dp, dp, dp, vp]),
         "celeste_elbo_batch_noalloc": (ctypes.c_int, [vp, dp, dp, dp, dp, vp]),
+        "celeste_cnn_param_count": (ctypes.c_int64, []),
+        "celeste_cnn_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int]),
+        "celeste_cnn_init": (ctypes.c_int, [dp, dp, ctypes.c_uint64, vp]),
+        "celeste_cnn_forward": (ctypes.c_int, [dp, dp, dp, ctypes.c_int, dp, dp, dp, dp, ctypes.c_size_t, vp]),
+        "celeste_cnn_backward": (ctypes.c_int, [dp, dp, dp, dp, ctypes.c_int, dp, dp, ctypes.c_size_t, vp]),
+        "celeste_cnn_mse": (ctypes.c_int, [dp, dp, dp, ctypes.c_int, dp, dp, vp]),
+        "celeste_cnn_adamw": (ctypes.c_int, [dp, dp, dp, dp, dp, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                             ctypes.c_float, ctypes.c_float, ctypes.c_int, vp]),
+        "celeste_extract_patches": (ctypes.c_int, [vp, dp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -192,6 +203,12 @@ class Problem:
         _check(lib().celeste_newton_batch(self.handle, _ptr(theta), ctypes.byref(opts), _ptr(delta), _ptr(iters),
                                           _ptr(status), _ptr(elbo), _stream(stream)))
         return delta, iters, status, elbo
+
+    def extract_patches(self, stream=None):
+        """The warm-start network's input for every source: int16 [S, 32, 32, 5] BF16 bit patterns."""
+        x = torch.empty(self.S, 32, 32, 5, dtype=torch.int16, device=self.device)
+        _check(lib().celeste_extract_patches(self.handle, _ptr(x), _stream(stream)))
+        return x
 
     def rebind(self, stream=None):
         """Upload the layout again and re-gather the patch pixels from the device images."""
