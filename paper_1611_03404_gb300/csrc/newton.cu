@@ -17,7 +17,7 @@
 
 namespace celeste {
 
-constexpr int TR_WARPS = 4;     // sources per CTA of the step kernel
+constexpr int TR_WARPS = 1;     // sources per CTA of the step kernel (one warp: 29 KB of shared memory)
 
 // Per-source integer state.
 constexpr int ST_ACTIVE = 0, ST_ITERS = 1, ST_STATUS = 2, ST_BOUNDARY = 3;

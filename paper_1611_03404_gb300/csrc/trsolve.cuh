@@ -13,14 +13,20 @@
 //   * otherwise B is reduced once to tridiagonal form T = Q^T B Q by Householder reflections
 //     (lane-parallel; g is reflected in the same reductions), after which every solve with
 //     T + lambda I is an O(n) LDL^T recurrence:
-//   * positive definiteness of B  <=>  all LDL^T pivots of T positive (Sylvester);
-//   * lambda_min(T): a float32 Sturm-sequence multisection bracket (each lane tests its own shift),
-//     refined in float64 by inverse iteration and the Rayleigh quotient;
-//   * |p(lambda)| = delta by the safeguarded Newton iteration on 1/|p| - 1/delta
-//     (Nocedal & Wright Algorithm 4.3), phi'(lambda) = |w|^2/|p|^3, L D w = p;
-//   * hard case: eigenvector of lambda_min by inverse iteration on T.
+//   * the multiplier lambda >= max(0, -lambda_min) with |p(lambda)| = delta (Nocedal & Wright
+//     Sec. 4.3, Moré-Sorensen) by passes of 32 multipliers at once, one per lane (each lane
+//     factors T + lambda I and solves with it): a geometric-plus-uniform grid over the bracket,
+//     then points around the Newton iterate of phi(lambda) = 1/|p| - 1/delta from the largest
+//     left point (phi concave and increasing: Newton from the left stays left).  A float64
+//     warp instruction costs the same for 1 or 32 lanes here, so a pass costs one evaluation;
+//     positive definiteness of T + lambda I (Sylvester: all LDL^T pivots positive) tells the
+//     points left of the pole -lambda_min; lambda = 0 tests the interior step;
+//   * hard case (the bracket closes on the pole with |p| < delta): eigenvector of lambda_min by
+//     inverse iteration on T after a float32 Sturm bracket, p = y + tau z.
 // The step is mapped back with the reflections, p = Q y.
 #pragma once
+
+#include <cfloat>
 
 #include "celeste_internal.cuh"
 
@@ -41,6 +47,8 @@ struct TrSmem {
   double D[TR_N], L[TR_N];        // LDL^T of T + lambda I (D holds the reciprocal pivots)
   double sc[4];                   // broadcast scalars
   int flag[4];
+  // lane-private factors of T + lambda_lane I for the parallel secular-equation passes
+  double PL[TR_N][32], PR[TR_N][32], PY[TR_N][32];
 };
 
 __device__ inline double tr_warp_sum(double v) {
@@ -87,18 +95,6 @@ __device__ inline double tr_norm(const double* x) {
   return sqrt((s0 + s1) + (s2 + s3));
 }
 
-// Number of eigenvalues of T below x (negative pivots of T - x I).
-__device__ inline int tr_sturm(const TrSmem& S, double x) {
-  double q = S.d[0] - x;
-  int c = q < 0.0;
-  for (int i = 1; i < TR_N; ++i) {
-    if (q == 0.0) q = -1e-300;
-    q = S.d[i] - x - S.off[i] * S.off[i] / q;
-    c += q < 0.0;
-  }
-  return c;
-}
-
 // Float32 Sturm count (only used to bracket lambda_min; the bracket is widened afterwards).
 __device__ inline int tr_sturm_f(const TrSmem& S, float x) {
   float q = (float)S.d[0] - x;
@@ -112,112 +108,143 @@ __device__ inline int tr_sturm_f(const TrSmem& S, float x) {
   return c;
 }
 
-// Lane 0 only: float32 Newton iterations on phi(lambda) = 1/|y| - 1/delta to a starting point for
-// the float64 iteration (|y| within ~1e-5 of delta).  The float32 phi can have the wrong sign close
-// to the pole, so this phase keeps its own bracket and leaves the float64 safeguards untouched.
-__device__ inline double tr_newton_lambda_f32(const TrSmem& S, double lambda, double lo, double hi, double delta) {
-  float D[TR_N], L[TR_N], y[TR_N];
-  for (int it = 0; it < 30; ++it) {
-    const float lam = (float)lambda;
-    float Dp = (float)S.d[0] + lam;
-    bool pd = Dp > 0.f;
-    D[0] = 1.f / Dp;
-    for (int i = 1; i < TR_N; ++i) {
-      const float o = (float)S.off[i];
-      L[i] = o * D[i - 1];
-      Dp = (float)S.d[i] + lam - L[i] * o;
-      pd = pd && Dp > 0.f;
-      D[i] = 1.f / Dp;
-    }
-    if (!pd) {
-      lo = lambda;
-      lambda = 0.5 * (lo + hi);
-      continue;
-    }
-    y[0] = -(float)S.gh[0];
-    for (int i = 1; i < TR_N; ++i) y[i] = -(float)S.gh[i] - L[i] * y[i - 1];
-    for (int i = 0; i < TR_N; ++i) y[i] *= D[i];
-    for (int i = TR_N - 2; i >= 0; --i) y[i] -= L[i + 1] * y[i + 1];
-    float pn2 = 0.f;
-    for (int i = 0; i < TR_N; ++i) pn2 += y[i] * y[i];
-    const float pn = sqrtf(pn2);
-    float wv = y[0], qn2 = wv * wv * D[0];
-    for (int i = 1; i < TR_N; ++i) {
-      wv = y[i] - L[i] * wv;
-      qn2 += wv * wv * D[i];
-    }
-    if (!(pn > 0.f) || !isfinite(pn)) break;
-    if (fabsf(pn - (float)delta) <= 1e-5f * (float)delta) break;
-    const double phi = 1.0 / pn - 1.0 / delta;
-    if (phi > 0)
-      hi = lambda;
-    else
-      lo = lambda;
-    double ln = lambda - phi / ((double)qn2 / ((double)pn * pn * pn));
-    if (!(lo < ln && ln < hi)) ln = 0.5 * (lo + hi);
-    if (ln == lambda) break;
-    lambda = ln;
+// Lane-private evaluation at the lane's own multiplier lam: L D L^T = T + lam I (reciprocal
+// pivots in PR), y = -(T + lam I)^-1 gh in PY; returns false if a pivot is not positive.
+// Otherwise pn = |y| and qn2 = y^T (T + lam I)^-1 y (phi'(lam) = qn2 / pn^3 for
+// phi = 1/|y| - 1/delta).  All lanes run the same instruction stream on their own lam, so a pass
+// costs one evaluation's float64 instructions for 32 multipliers.
+__device__ inline bool tr_eval_lane(TrSmem& S, int lane, double lam, double& pn, double& qn2) {
+  double Dp = S.d[0] + lam;
+  bool pd = Dp > 0.0;
+  double r = 1.0 / Dp;
+  double w = -S.gh[0];
+  S.PR[0][lane] = r;
+  S.PY[0][lane] = w;
+  for (int i = 1; i < TR_N; ++i) {
+    const double l = S.off[i] * r;
+    Dp = fma(-S.o2[i], r, S.d[i] + lam);
+    pd = pd && Dp > 0.0;
+    r = 1.0 / Dp;
+    w = fma(-l, w, -S.gh[i]);
+    S.PL[i][lane] = l;
+    S.PR[i][lane] = r;
+    S.PY[i][lane] = w;
   }
-  return lambda;
+  if (!pd) return false;
+  double y = S.PY[TR_N - 1][lane] * S.PR[TR_N - 1][lane];
+  S.PY[TR_N - 1][lane] = y;
+  double p2 = y * y;
+  for (int i = TR_N - 2; i >= 0; --i) {
+    y = fma(-S.PL[i + 1][lane], y, S.PY[i][lane] * S.PR[i][lane]);
+    S.PY[i][lane] = y;
+    p2 = fma(y, y, p2);
+  }
+  double z = S.PY[0][lane], q2 = z * z * S.PR[0][lane];
+  for (int i = 1; i < TR_N; ++i) {
+    z = fma(-S.PL[i][lane], z, S.PY[i][lane]);
+    q2 = fma(z * z, S.PR[i][lane], q2);
+  }
+  pn = sqrt(p2);
+  qn2 = q2;
+  return true;
 }
 
-// Lane 0 only: safeguarded Newton on phi(lambda) = 1/|y| - 1/delta over (lo, hi); result in S.y.
-__device__ inline void tr_newton_lambda(TrSmem& S, double lambda, double lo, double hi, double delta) {
-  double mg[TR_N];
-  for (int i = 0; i < TR_N; ++i) mg[i] = -S.gh[i];
-  bool have = false;
-  // float32 estimate, checked in float64: on the near (phi < 0) side it is the starting point of the
-  // monotone float64 Newton iteration; beyond the root or below the pole it only tightens the
-  // bracket and the iteration starts from the given point, where phi < 0.
-  const double lam_f = tr_newton_lambda_f32(S, lambda, lo, hi, delta);
-  if (lam_f != lambda && lam_f > lo && lam_f < hi) {
-    if (tr_ldl(S, lam_f)) {
-      tr_ldl_solve(S, mg, S.y);
-      if (tr_norm(S.y) > delta)
-        lambda = lam_f;
-      else
-        hi = lam_f;
-    } else {
-      lo = lam_f;
-      if (lambda <= lo) lambda = 0.5 * (lo + hi);
-    }
-  }
-  for (int it = 0; it < 60; ++it) {
-    if (!tr_ldl(S, lambda)) {   // below lambda_min: move up by bisection
-      lo = lambda;
-      lambda = 0.5 * (lo + hi);
-      continue;
-    }
-    tr_ldl_solve(S, mg, S.y);
-    have = true;
-    const double pn = tr_norm(S.y);
-    double wv = S.y[0], qn2 = wv * wv * S.D[0];
-    for (int i = 1; i < TR_N; ++i) {
-      wv = S.y[i] - S.L[i] * wv;
-      qn2 += wv * wv * S.D[i];
-    }
-    if (fabs(pn - delta) <= 1e-10 * delta) break;
-    const double phi = 1.0 / pn - 1.0 / delta;
-    if (phi > 0)
-      hi = lambda;
+__device__ inline double tr_warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ inline double tr_warp_min(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Copies lane src's y into S.y (lanes < 27 in parallel).
+__device__ inline void tr_take_y(TrSmem& S, int lane, int src) {
+  __syncwarp();
+  if (lane < TR_N) S.y[lane] = S.PY[lane][src];
+  __syncwarp();
+}
+
+// Root of phi(lambda) = 1/|y(lambda)| - 1/delta over [lo, hi] (lo <= lambda*, phi(hi) >= 0), or
+// lambda* = 0 when T is positive definite and |T^-1 gh| <= delta.  Each pass evaluates 32
+// multipliers: a geometric grid over the bracket, refined around the Newton point of the
+// largest evaluated multiplier on the left (phi < 0; phi is concave and increasing, so Newton
+// from the left stays left).  Non-positive-definite points lie left of -lambda_min <= lambda*.
+// On return S.y holds the step in the T basis; returns 1 for the hard case (the bracket closes
+// on the pole with phi > 0 to its right), in which S.y is not set.
+__device__ inline int tr_lambda_parallel(TrSmem& S, int lane, double lo, double hi, double delta, bool try_zero) {
+  constexpr double TOL = 1e-10;
+  double L = lo, H = hi;            // L <= lambda* <= H
+  bool have_h = false;              // S.y holds the point H (phi(H) >= 0)
+  double lamN = -1.0;               // Newton point from the best left evaluation (< 0: none)
+  // Lane offsets.  Without a Newton point: lanes 1-15 geometric from L (2^-45 .. 2^-3 of the
+  // bracket, for a root or pole just above L), lanes 16-31 uniform (1/17 .. 16/17, so the bracket
+  // shrinks at least 17-fold).  With one: lane 0 at it, lanes 1-15 above and 16-31 below at
+  // 2^-3 .. 2^-48 of the distance to the bracket's ends.
+  const double gfac = lane < 16 ? ldexp(1.0, -3 * (16 - lane)) : (double)(lane - 15) / 17.0;
+  const double nfac = ldexp(1.0, -3 * ((lane & 15) + 1));
+  for (int pass = 0; pass < 16; ++pass) {
+    // ---- this lane's multiplier
+    double lam;
+    const double span = H - L;
+    if (pass > 0 && lamN > L && lamN < H)
+      lam = lane == 0 ? lamN : (lane < 16 ? lamN + (H - lamN) * nfac : lamN - (lamN - L) * nfac);
+    else if (lane == 0)
+      lam = (pass == 0 && try_zero) ? 0.0 : L + 0.5 * span;
     else
-      lo = lambda;
-    double ln = lambda - phi / (qn2 / (pn * pn * pn));
-    if (!(lo < ln && ln < hi)) ln = 0.5 * (lo + hi);
-    if (ln == lambda) break;
-    lambda = ln;
+      lam = L + span * gfac;
+    double pn = 0.0, qn2 = 0.0;
+    const bool pd = tr_eval_lane(S, lane, lam, pn, qn2);
+    // ---- interior solution
+    if (pass == 0 && try_zero) {
+      const bool interior = __shfl_sync(0xffffffffu, (int)(pd && pn <= delta), 0) != 0;
+      if (interior) {
+        tr_take_y(S, lane, 0);
+        return 0;
+      }
+    }
+    // ---- converged lane?
+    const double err = pd ? fabs(pn - delta) : INFINITY;
+    const double best = tr_warp_min(err);
+    if (best <= TOL * delta) {
+      const unsigned m = __ballot_sync(0xffffffffu, err == best);
+      tr_take_y(S, lane, __ffs(m) - 1);
+      return 0;
+    }
+    // ---- new bracket
+    const bool right = pd && pn <= delta;
+    const double newL = tr_warp_max(right ? -INFINITY : lam);
+    const double newH = tr_warp_min(right ? lam : INFINITY);
+    if (newH < H) {
+      const unsigned m = __ballot_sync(0xffffffffu, right && lam == newH);
+      tr_take_y(S, lane, __ffs(m) - 1);
+      H = newH;
+      have_h = true;
+    }
+    L = fmax(L, newL);
+    // ---- Newton point from the largest left evaluation with phi < 0
+    const bool lft = pd && pn > delta;
+    const double lbest = tr_warp_max(lft ? lam : -INFINITY);
+    lamN = -1.0;
+    if (lbest > -INFINITY) {
+      const unsigned m = __ballot_sync(0xffffffffu, lft && lam == lbest);
+      const int src = __ffs(m) - 1;
+      const double pnb = __shfl_sync(0xffffffffu, pn, src), qb = __shfl_sync(0xffffffffu, qn2, src);
+      const double phi = 1.0 / pnb - 1.0 / delta;
+      lamN = lbest - phi / (qb / (pnb * pnb * pnb));
+    }
+    // ---- bracket closed: no float64 multiplier left between L and H
+    if (H - L <= 4.0 * DBL_EPSILON * fmax(fabs(H), 1e-300)) {
+      if (!have_h) return 1;
+      // phi(H) >= 0 with H next to L: the root, unless |y| jumps across delta within the last
+      // ulps of lambda -- the pole, where g's component along the eigenvector of lambda_min is
+      // too small to resolve (the hard case, numerically)
+      return tr_norm(S.y) < delta * (1.0 - 1e-6) ? 1 : 0;
+    }
   }
-  if (!have || !tr_ldl(S, lambda)) {   // fall back to the upper bracket end, always admissible
-    tr_ldl(S, hi);
-    tr_ldl_solve(S, mg, S.y);
-  }
-  // Near the pole lambda = -lambda_min the last ulp of lambda can move |y| by ~1e-8 relative;
-  // keep the step feasible.
-  const double yn = tr_norm(S.y);
-  if (yn > delta) {
-    const double r = delta / yn;
-    for (int i = 0; i < TR_N; ++i) S.y[i] *= r;
-  }
+  return have_h ? 0 : 1;
 }
 
 // Loads B (scaled by bsign) into S.A, lane-parallel and coalesced.
@@ -352,96 +379,77 @@ __device__ inline void tr_solve_warp(TrSmem& S, const double* __restrict__ Bsrc,
   if (row) S.o2[lane] = S.off[lane] * S.off[lane];
   __syncwarp();
 
-  // ---- positive definite and interior?
-  if (lane == 0) {
-    S.flag[0] = tr_ldl(S, 0.0);
-    S.flag[1] = 0;   // done
-    S.flag[2] = 0;   // hard case
-    if (S.flag[0]) {
+  // ---- multiplier: lambda* >= max(0, -lambda_min) >= max(0, -min_i d_i); at
+  //      hi = |g| / delta - a (a <= lambda_min, Gershgorin) |p(hi)| <= |g| / (hi + lambda_min) <= delta
+  double a = INFINITY, dmin = INFINITY, dmax = 0.0, omax = 0.0;
+  for (int i = 0; i < n; ++i) {
+    const double r = fabs(S.off[i]) + (i + 1 < n ? fabs(S.off[i + 1]) : 0.0);
+    a = fmin(a, S.d[i] - r);
+    dmin = fmin(dmin, S.d[i]);
+    dmax = fmax(dmax, fabs(S.d[i]));
+    omax = fmax(omax, fabs(S.off[i]));
+  }
+  const double scale = fmax(1.0, dmax + 2.0 * omax);
+  const double lo = fmax(0.0, -dmin);
+  const double hi = fmax(lo, gnorm / delta - a) * (1.0 + 1e-12) + 1e-300;
+  if (lane == 0) S.flag[2] = 0;
+  __syncwarp();
+  if (tr_lambda_parallel(S, lane, lo, hi, delta, lo == 0.0)) {
+    // hard case: g has (almost) no component along the eigenvector z of lambda_min.  lambda_min
+    // from a float32 Sturm bracket refined by inverse iteration (lane 0), then
+    // p = y(-lambda_min) + tau z with |p| = delta.
+    float fa = (float)a, fb = (float)(dmin);
+    for (int it = 0; it < 6; ++it) {
+      const float x = fa + (fb - fa) * (float)(lane + 1) / 33.f;
+      const unsigned m = __ballot_sync(0xffffffffu, tr_sturm_f(S, x) >= 1);
+      const int f = m ? __ffs(m) - 1 : 32;
+      const float na = f > 0 ? fa + (fb - fa) * (float)f / 33.f : fa;
+      const float nb = f < 32 ? fa + (fb - fa) * (float)(f + 1) / 33.f : fb;
+      fa = na;
+      fb = nb;
+    }
+    const double ab = fmax(a, (double)fa - 1e-5 * scale), bb = fmin((double)dmin, (double)fb + 1e-5 * scale);
+    if (lane == 0) {
+      tr_ldl(S, -(ab - 1e-8 * scale));
+      for (int i = 0; i < n; ++i) S.z[i] = 1.0;
+      for (int r = 0; r < 4; ++r) {
+        tr_ldl_solve(S, S.z, S.z);
+        const double rz = 1.0 / tr_norm(S.z);
+        for (int i = 0; i < n; ++i) S.z[i] *= rz;
+      }
+      double lmin = 0.0, zg = 0.0;
+      for (int i = 0; i < n; ++i) {
+        double Tz = S.d[i] * S.z[i];
+        if (i > 0) Tz += S.off[i] * S.z[i - 1];
+        if (i + 1 < n) Tz += S.off[i + 1] * S.z[i + 1];
+        lmin += S.z[i] * Tz;
+        zg += S.z[i] * S.gh[i];
+      }
+      lmin = fmin(lmin, bb);
+      tr_ldl(S, fmax(0.0, -lmin) + 1e-9 * scale);
       for (int i = 0; i < n; ++i) S.y[i] = -S.gh[i];
       tr_ldl_solve(S, S.y, S.y);
-      if (tr_norm(S.y) <= delta) S.flag[1] = 1;
+      double zy = 0.0;
+      for (int i = 0; i < n; ++i) zy += S.z[i] * S.y[i];
+      for (int i = 0; i < n; ++i) S.y[i] -= zy * S.z[i];
+      const double yn = tr_norm(S.y);
+      if (yn > delta) {
+        for (int i = 0; i < n; ++i) S.y[i] *= delta / yn;
+      } else {
+        // the sign that lowers the model: tau z.g < 0 (either sign when z.g = 0 exactly)
+        const double tau = copysign(sqrt(fmax(delta * delta - yn * yn, 0.0)), -zg);
+        for (int i = 0; i < n; ++i) S.y[i] += tau * S.z[i];
+      }
+      S.flag[2] = 1;
     }
+    __syncwarp();
+  } else if (lane == 0) {
+    // next to the pole the last ulp of lambda can move |y| by ~1e-8 relative; keep the step feasible
+    const double yn = tr_norm(S.y);
+    if (yn > delta)
+      for (int i = 0; i < n; ++i) S.y[i] *= delta / yn;
   }
   __syncwarp();
-  if (!S.flag[1]) {
-    double lo = 0.0, lam0 = 0.0, scale = 1.0;
-    if (!S.flag[0]) {
-      // lambda_min of T by multisection of its Gershgorin interval (one shift per lane)
-      double a = INFINITY, b = -INFINITY, dmax = 0.0, omax = 0.0;
-      for (int i = 0; i < n; ++i) {
-        const double r = fabs(S.off[i]) + (i + 1 < n ? fabs(S.off[i + 1]) : 0.0);
-        a = fmin(a, S.d[i] - r);
-        b = fmax(b, S.d[i] + r);
-        dmax = fmax(dmax, fabs(S.d[i]));
-        omax = fmax(omax, fabs(S.off[i]));
-      }
-      scale = fmax(1.0, dmax + 2.0 * omax);
-      // Bracket [a, b] of lambda_min by Sturm multisection in float32 (one shift per lane), widened by
-      // 1e-5 of the spectrum scale to cover the rounding; it supplies the shift of the float64
-      // inverse iteration below.
-      {
-        float fa = (float)a, fb = (float)b;
-        for (int it = 0; it < 6; ++it) {
-          const float x = fa + (fb - fa) * (float)(lane + 1) / 33.f;
-          const unsigned m = __ballot_sync(0xffffffffu, tr_sturm_f(S, x) >= 1);
-          const int f = m ? __ffs(m) - 1 : 32;
-          const float na = f > 0 ? fa + (fb - fa) * (float)f / 33.f : fa;
-          const float nb = f < 32 ? fa + (fb - fa) * (float)(f + 1) / 33.f : fb;
-          fa = na;
-          fb = nb;
-          if (fb - fa <= 1e-6f * (float)scale) break;
-        }
-        a = fmax(a, (double)fa - 1e-5 * scale);
-        b = fmin(b, (double)fb + 1e-5 * scale);
-      }
-      if (lane == 0) {
-        // float64 refinement: eigenvector z of lambda_min by inverse iteration with a shift below the
-        // bracket, lambda_min from its Rayleigh quotient (>= lambda_min, so -lambda_R is a lower bound
-        // of the admissible lambdas).  The hard case needs g to have (almost) no component on z.
-        tr_ldl(S, -(a - 1e-8 * scale));
-        for (int i = 0; i < n; ++i) S.z[i] = 1.0;
-        for (int r = 0; r < 4; ++r) {
-          tr_ldl_solve(S, S.z, S.z);
-          const double rz = 1.0 / tr_norm(S.z);
-          for (int i = 0; i < n; ++i) S.z[i] *= rz;
-        }
-        double lmin = 0.0, zg = 0.0;
-        for (int i = 0; i < n; ++i) {
-          double Tz = S.d[i] * S.z[i];
-          if (i > 0) Tz += S.off[i] * S.z[i - 1];
-          if (i + 1 < n) Tz += S.off[i + 1] * S.z[i + 1];
-          lmin += S.z[i] * Tz;
-          zg += S.z[i] * S.gh[i];
-        }
-        lmin = fmin(lmin, b);
-        S.sc[0] = fmax(0.0, -lmin);
-        S.sc[1] = fmax(0.0, -lmin) + 1e-12 * scale;
-        if (fabs(zg) <= 1e-12 * fmax(gnorm, 1e-300)) {
-          tr_ldl(S, fmax(0.0, -lmin) + 1e-9 * scale);
-          for (int i = 0; i < n; ++i) S.y[i] = -S.gh[i];
-          tr_ldl_solve(S, S.y, S.y);
-          double zy = 0.0;
-          for (int i = 0; i < n; ++i) zy += S.z[i] * S.y[i];
-          for (int i = 0; i < n; ++i) S.y[i] -= zy * S.z[i];
-          const double yn = tr_norm(S.y);
-          if (yn <= delta) {
-            const double tau = sqrt(fmax(delta * delta - yn * yn, 0.0));
-            for (int i = 0; i < n; ++i) S.y[i] += tau * S.z[i];
-            S.flag[1] = 1;
-            S.flag[2] = 1;
-          }
-        }
-      }
-      __syncwarp();
-      lo = S.sc[0];
-      lam0 = S.sc[1];
-    }
-    // upper end: |p(lambda)| <= |g| / (lambda + lambda_min) <= delta there (lam0 >= -lambda_min up
-    // to the Rayleigh-quotient error, covered by the + 1)
-    if (!S.flag[1] && lane == 0) tr_newton_lambda(S, lam0, lo, lam0 + gnorm / delta + 1.0, delta);
-    __syncwarp();
-  }
   hard = S.flag[2];
   // ---- p = Q y, and the model value through T: g.p = gh.y, p.B.p = y.T.y
   double yi = row ? S.y[lane] : 0.0;
