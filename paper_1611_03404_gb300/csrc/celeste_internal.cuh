@@ -78,6 +78,9 @@ struct TileDev {
 // Worklists (offsets into ProblemDev::wl and indices of ProblemDev::wl_count).
 constexpr int WL_TILES = 0, WL_PATCHES = 1, WL_SOURCES = 2;
 constexpr int WL_INTS = 8;
+// Doubles per source kept by the trust-region step for a repeated subproblem (Householder
+// vectors, tridiagonal form, reflected gradient, reflection coefficients, squared off-diagonal).
+constexpr int TR_CACHE = NP * NP + 5 * NP;
 
 // Device view of a bound problem (passed by value to kernels).
 struct ProblemDev {

@@ -19,8 +19,10 @@ namespace celeste {
 
 constexpr int TR_WARPS = 1;     // sources per CTA of the step kernel (one warp: 29 KB of shared memory)
 
-// Per-source integer state.
-constexpr int ST_ACTIVE = 0, ST_ITERS = 1, ST_STATUS = 2, ST_BOUNDARY = 3;
+// Per-source integer state (ST_STRIDE ints).  ST_SAME: the last step was rejected, so the next
+// subproblem has the same B and g; ST_CACHED: the tridiagonal form of that B is in the cache.
+constexpr int ST_ACTIVE = 0, ST_ITERS = 1, ST_STATUS = 2, ST_BOUNDARY = 3, ST_SAME = 4, ST_CACHED = 5;
+constexpr int ST_STRIDE = 8;
 
 struct NewtonDev {
   double* theta;        // [S][27] current iterate (caller memory)
@@ -31,7 +33,8 @@ struct NewtonDev {
   double* trial;        // [S][27]
   double* pred;         // [S] predicted reduction of f = -ELBO
   double* Ltrial;       // [S] ELBO change from theta to the trial point
-  int* state;           // [S][4]
+  double* tcache;       // [S][TR_CACHE] tridiagonal form of the last Householder-reduced B
+  int* state;           // [S][ST_STRIDE]
   int* count;           // [0]: active sources after the update
   int S;
   double ftol, gtol, delta0, delta_max, eta, delta_min;
@@ -51,10 +54,12 @@ __device__ inline double warp_max(double v) {
 __global__ void newton_init_kernel(NewtonDev N, int* flags) {
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= N.S) return;
-  N.state[4 * s + ST_ACTIVE] = 1;
-  N.state[4 * s + ST_ITERS] = 0;
-  N.state[4 * s + ST_STATUS] = CELESTE_STATUS_MAX_ITER;
-  N.state[4 * s + ST_BOUNDARY] = 0;
+  N.state[ST_STRIDE * s + ST_ACTIVE] = 1;
+  N.state[ST_STRIDE * s + ST_ITERS] = 0;
+  N.state[ST_STRIDE * s + ST_STATUS] = CELESTE_STATUS_MAX_ITER;
+  N.state[ST_STRIDE * s + ST_BOUNDARY] = 0;
+  N.state[ST_STRIDE * s + ST_SAME] = 0;
+  N.state[ST_STRIDE * s + ST_CACHED] = 0;
   if (!(N.delta[s] > 0.0)) N.delta[s] = N.delta0;
   flags[s] = FLAG_FULL;
 }
@@ -65,7 +70,7 @@ __global__ void __launch_bounds__(32 * TR_WARPS) tr_step_kernel(NewtonDev N, int
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int s = blockIdx.x * TR_WARPS + warp;
   if (s >= N.S) return;
-  int* st = N.state + 4 * s;
+  int* st = N.state + ST_STRIDE * s;
   if (!st[ST_ACTIVE]) {
     if (lane == 0) flags[s] = 0;
     return;
@@ -98,9 +103,16 @@ __global__ void __launch_bounds__(32 * TR_WARPS) tr_step_kernel(NewtonDev N, int
   const double delta = N.delta[s];
   double pk, pred;
   int hard;
-  // the Newton step is tried first where the previous step was interior
-  const bool try_newton = st[ST_ITERS] > 0 && !st[ST_BOUNDARY];
-  tr_solve_warp(S, HL, -1.0, gk, delta, try_newton, pk, pred, hard);
+  // A rejected step leaves B and g as they were: reuse their tridiagonal form if it was cached
+  // (the Newton step, tried first where the previous step was interior, cannot fit the smaller
+  // radius then).
+  const bool same = st[ST_SAME] != 0;
+  const bool use_cache = same && st[ST_CACHED];
+  const bool try_newton = !same && st[ST_ITERS] > 0 && !st[ST_BOUNDARY];
+  double* cache = N.tcache + (size_t)s * TR_CACHE;
+  const bool reduced = tr_solve_warp(S, HL, -1.0, gk, delta, try_newton, use_cache ? cache : nullptr, cache, pk,
+                                     pred, hard);
+  if (lane == 0) st[ST_CACHED] = use_cache || reduced;
   const double pnorm = sqrt(warp_sum(lane < NP ? pk * pk : 0.0));
   if (lane < NP) N.trial[(size_t)s * NP + lane] = N.theta[(size_t)s * NP + lane] + pk;
   if (lane == 0) {
@@ -131,7 +143,7 @@ __global__ void __launch_bounds__(32 * TR_WARPS) tr_solve_batch_kernel(const dou
   const double gk = lane < NP ? g[(size_t)q * NP + lane] : 0.0;
   double pk, pr;
   int hc;
-  tr_solve_warp(S, B + (size_t)q * NP * NP, 1.0, gk, delta[q], true, pk, pr, hc);
+  tr_solve_warp(S, B + (size_t)q * NP * NP, 1.0, gk, delta[q], true, nullptr, nullptr, pk, pr, hc);
   if (lane < NP) p[(size_t)q * NP + lane] = pk;
   if (lane == 0) {
     if (pred) pred[q] = pr;
@@ -144,7 +156,7 @@ __global__ void tr_update_kernel(NewtonDev N, int* flags) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   int active = 0;
   if (s < N.S) {
-    int* st = N.state + 4 * s;
+    int* st = N.state + ST_STRIDE * s;
     if (flags[s] & FLAG_VALUE) {
       const double dL = N.Ltrial[s], pred = N.pred[s];   // f - f_new = L_new - L = dL
       double rho = pred > 0 ? dL / pred : -1.0;
@@ -156,7 +168,10 @@ __global__ void tr_update_kernel(NewtonDev N, int* flags) {
         delta = fmin(2.0 * delta, N.delta_max);
       N.delta[s] = delta;
       int fl = 0;
+      st[ST_SAME] = 1;   // until accepted below
       if (rho > N.eta) {
+        st[ST_SAME] = 0;
+        st[ST_CACHED] = 0;
         const double Lnew = N.L[s] + dL;
         const bool done = fabs(dL) <= N.ftol * fabs(Lnew);
         for (int k = 0; k < NP; ++k) N.theta[(size_t)s * NP + k] = N.trial[(size_t)s * NP + k];
@@ -187,8 +202,8 @@ __global__ void tr_update_kernel(NewtonDev N, int* flags) {
 __global__ void newton_finish_kernel(NewtonDev N, int32_t* iters, int32_t* status, double* elbo) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= N.S) return;
-  if (iters) iters[s] = N.state[4 * s + ST_ITERS];
-  if (status) status[s] = N.state[4 * s + ST_STATUS];
+  if (iters) iters[s] = N.state[ST_STRIDE * s + ST_ITERS];
+  if (status) status[s] = N.state[ST_STRIDE * s + ST_STATUS];
   if (elbo) elbo[s] = N.L[s];
 }
 
@@ -250,6 +265,7 @@ extern "C" int celeste_newton_batch(celeste_problem* p, double* theta, const cel
   N.pred = reinterpret_cast<double*>(p->base + L.nt_pred);
   N.Ltrial = reinterpret_cast<double*>(p->base + L.nt_ftrial);
   N.state = reinterpret_cast<int*>(p->base + L.nt_state);
+  N.tcache = reinterpret_cast<double*>(p->base + L.nt_tcache);
   N.count = reinterpret_cast<int*>(p->base + L.nt_count);
   N.S = p->S;
   N.ftol = o.ftol > 0 ? o.ftol : 1e-8;

@@ -309,7 +309,8 @@ void build_layout(celeste_problem* p) {
   L.nt_trial = take(sizeof(double) * NP * S);
   L.nt_pred = take(sizeof(double) * S);
   L.nt_ftrial = take(sizeof(double) * S);
-  L.nt_state = take(sizeof(int) * 4 * S);
+  L.nt_state = take(sizeof(int) * 8 * S);
+  L.nt_tcache = take(sizeof(double) * TR_CACHE * S);
   L.nt_count = take(sizeof(int) * 4);
   L.total = o;
 }

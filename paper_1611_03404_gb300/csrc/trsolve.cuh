@@ -291,13 +291,30 @@ __device__ inline bool tr_newton_step(TrSmem& S, double gi, double& p_i) {
 
 // Solves the subproblem for B (device, row-major 27 x 27, times bsign) and the gradient g_i held by
 // lane i (0 for lanes >= 27).  On return lane i < 27 holds p_i; pred = -(g.p + p.B.p/2); hard =
-// hard case taken.  try_newton: attempt the Newton step first.
-__device__ inline void tr_solve_warp(TrSmem& S, const double* __restrict__ Bsrc, double bsign, double gi, double delta,
-                                     bool try_newton, double& p_i, double& pred, int& hard) {
+// hard case taken.  try_newton: attempt the Newton step first.  cache_in (or null): the
+// tridiagonal form of this same B and g, stored by an earlier call, replaces the reduction;
+// cache_out (or null): where to store the reduction when one is made.  Returns true when the
+// reduction was made and stored.
+__device__ inline bool tr_solve_warp(TrSmem& S, const double* __restrict__ Bsrc, double bsign, double gi,
+                                     double delta, bool try_newton, const double* __restrict__ cache_in,
+                                     double* __restrict__ cache_out, double& p_i, double& pred, int& hard) {
   const int lane = threadIdx.x & 31;
   const int n = TR_N;
   const bool row = lane < n;
   const double gnorm = sqrt(tr_warp_sum(gi * gi));
+  bool stored = false;
+  if (cache_in) {
+    // layout: A [27][27], d, off, o2, gh, beta [27] each
+    for (int i = lane; i < TR_N * TR_N; i += 32) S.A[(i / TR_N) * TR_LD + (i % TR_N)] = cache_in[i];
+    if (row) {
+      S.d[lane] = cache_in[TR_N * TR_N + lane];
+      S.off[lane] = cache_in[TR_N * TR_N + TR_N + lane];
+      S.o2[lane] = cache_in[TR_N * TR_N + 2 * TR_N + lane];
+      S.gh[lane] = cache_in[TR_N * TR_N + 3 * TR_N + lane];
+      S.beta[lane] = cache_in[TR_N * TR_N + 4 * TR_N + lane];
+    }
+    __syncwarp();
+  } else {
   if (try_newton) {
     tr_load(S, Bsrc, bsign);
     double pn;
@@ -307,7 +324,7 @@ __device__ inline void tr_solve_warp(TrSmem& S, const double* __restrict__ Bsrc,
         p_i = pn;
         pred = -0.5 * tr_warp_sum(gi * pn);   // -(g.p + p.B.p/2) with B p = -g
         hard = 0;
-        return;
+        return false;
       }
     }
   }
@@ -378,6 +395,18 @@ __device__ inline void tr_solve_warp(TrSmem& S, const double* __restrict__ Bsrc,
   __syncwarp();
   if (row) S.o2[lane] = S.off[lane] * S.off[lane];
   __syncwarp();
+  if (cache_out) {
+    for (int i = lane; i < TR_N * TR_N; i += 32) cache_out[i] = S.A[(i / TR_N) * TR_LD + (i % TR_N)];
+    if (row) {
+      cache_out[TR_N * TR_N + lane] = S.d[lane];
+      cache_out[TR_N * TR_N + TR_N + lane] = S.off[lane];
+      cache_out[TR_N * TR_N + 2 * TR_N + lane] = S.o2[lane];
+      cache_out[TR_N * TR_N + 3 * TR_N + lane] = S.gh[lane];
+      cache_out[TR_N * TR_N + 4 * TR_N + lane] = S.beta[lane];
+    }
+    stored = true;
+  }
+  }   // reduction
 
   // ---- multiplier: lambda* >= max(0, -lambda_min) >= max(0, -min_i d_i); at
   //      hi = |g| / delta - a (a <= lambda_min, Gershgorin) |p(hi)| <= |g| / (hi + lambda_min) <= delta
@@ -468,6 +497,7 @@ __device__ inline void tr_solve_warp(TrSmem& S, const double* __restrict__ Bsrc,
   }
   p_i = yi;
   __syncwarp();
+  return stored;
 }
 
 }  // namespace celeste
