@@ -103,58 +103,64 @@ struct PatchLiftF {
   float a0, a1, aa;
 };
 
+// Per-warp working set of one patch's lift.
+struct WarpLift {
+  double sd[ACC_HP];                                  // float64 sums: L, S1, S2
+  double gs[NP], gE[NP], nzK[NP], nzL[NP], ghat[NRED];
+  double Lsum;
+  PatchLift c;
+  float sdf[ACC_HP], sf[NACC - ACC_HP];               // float32 copies / compensated sums: HP, M
+  float Hs[NP * NP], H2[NP * NP];                     // accumulated Hessian; per-patch second-order part
+  float Msym[NRED * NRED], nzKf[NP], nzLf[NP];
+  PatchLiftF cf;
+  int nzA[NP], nzB[NP];
+};
+
 // ELBO and gradient are summed and lifted in float64 (the cross-pixel sums of the objective and
 // its gradient); the Hessian, whose per-pixel terms are float32 to begin with, in float32 with
-// compensated cross-tile sums.  On this part a float64 warp instruction costs ~64 cycles, a
-// float32 one a single issue slot, so the split cuts the kernel's float64 instructions about
-// fourfold.
+// compensated cross-tile sums.  On this part a float64 warp instruction costs ~64 cycles of its
+// SM sub-partition, a float32 one a single issue slot, so the split cuts the kernel's float64
+// instructions about fourfold.  A CTA takes one source; each of its four warps lifts every fourth
+// patch of the source into warp-private accumulators (the four sub-partitions' float64 pipes run
+// in parallel), then the warps' sums are added.
 __global__ void __launch_bounds__(128) assemble_kernel(ProblemDev P, const double* __restrict__ theta, int full,
                                                        double* elbo, double* grad, double* hess) {
-  const int tid = threadIdx.x, nt = blockDim.x;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int NW = 4;                 // warps per CTA
   constexpr int ND = ACC_HP;            // float64 sums: L, S1, S2
   constexpr int NF = NACC - ACC_HP;     // float32 sums: HP, M
-  __shared__ double sd[ND];
-  __shared__ float sdf[ND], sf[NF];
-  __shared__ float Hs[NP * NP], HE[NP * NP], H2[NP * NP], Msym[NRED * NRED], nzKf[NP], nzLf[NP];
-  __shared__ double gs[NP], gE[NP], nzK[NP], nzL[NP], ghat[NRED];
-  __shared__ int nzA[NP], nzB[NP];
-  __shared__ PatchLift c;
-  __shared__ PatchLiftF cf;
+  __shared__ WarpLift wl[NW];
+  __shared__ float Hs[NP * NP];
+  __shared__ double gs[NP];
   __shared__ SourceConst sc;
   __shared__ double Lsum, red[16];
   __shared__ int slot;
+  WarpLift& W = wl[warp];
+  PatchLift& c = W.c;
+  PatchLiftF& cf = W.cf;
   for (int s = wl_next_cta(P, WL_SOURCES, slot); s >= 0; s = wl_next_cta(P, WL_SOURCES, slot)) {
   const double* th = theta + (size_t)s * NP;
-  for (int i = tid; i < NP * NP; i += nt) Hs[i] = 0.f;
-  for (int i = tid; i < NP; i += nt) gs[i] = 0.0;
-  if (tid == 0) Lsum = 0.0;
+  for (int i = lane; i < NP * NP; i += 32) W.Hs[i] = 0.f;
+  if (lane < NP) W.gs[lane] = 0.0;
+  if (lane == 0) W.Lsum = 0.0;
   source_const_parallel(th, sc, tid);
   __syncthreads();
-  if (tid == 0) {
+  if (lane == 0) {
     cf.a0 = (float)sc.a0;
     cf.a1 = (float)sc.a1;
     cf.aa = (float)sc.aa;
   }
-  for (int p = P.src_patch[s]; p < P.src_patch[s + 1]; ++p) {
+  for (int p = P.src_patch[s] + warp; p < P.src_patch[s + 1]; p += NW) {
     const PatchDev pt = P.patches[p];
     // ---- tile sums (fixed order; float64 for the objective and gradient, compensated float32 for
-    //      the Hessian-only sums) and the band moments, in parallel
-    if (tid < ND) {
+    //      the Hessian-only sums) and the band moments
+    if (lane < ND) {
       double v = 0.0;
-      for (int t = pt.tile_begin; t < pt.tile_end; ++t) v += (double)P.partials[(size_t)t * NACC + tid];
-      sd[tid] = v;
-      sdf[tid] = (float)v;
-    } else if (tid < NACC) {
-      float v = 0.f, comp = 0.f;
-      for (int t = pt.tile_begin; t < pt.tile_end; ++t) {
-        const float y = P.partials[(size_t)t * NACC + tid] - comp;
-        const float u = v + y;
-        comp = (u - v) - y;
-        v = u;
-      }
-      sf[tid - ND] = v;
-    } else if (tid < NACC + 4) {
-      const int k = tid - NACC, t = k & 1, second = k >> 1;
+      for (int t = pt.tile_begin; t < pt.tile_end; ++t) v += (double)P.partials[(size_t)t * NACC + lane];
+      W.sd[lane] = v;
+      W.sdf[lane] = (float)v;
+    } else if (lane < ND + 4) {
+      const int k = lane - ND, t = k & 1, second = k >> 1;
       const int band = P.images[pt.image].band;
       double arow[4];
       color_row(band, arow);
@@ -171,14 +177,24 @@ __global__ void __launch_bounds__(128) assemble_kernel(ProblemDev P, const doubl
         cf.L1[t] = (float)c.L1[t];
       }
       if (k == 0) c.band = band;
-    } else if (tid < NACC + 8) {
-      c.A[tid - NACC - 4] = P.images[pt.image].A[tid - NACC - 4];
-      cf.A[tid - NACC - 4] = (float)c.A[tid - NACC - 4];
+    } else if (lane < ND + 8) {
+      c.A[lane - ND - 4] = P.images[pt.image].A[lane - ND - 4];
+      cf.A[lane - ND - 4] = (float)c.A[lane - ND - 4];
     }
-    __syncthreads();
+    for (int q = lane; q < NF; q += 32) {
+      float v = 0.f, comp = 0.f;
+      for (int t = pt.tile_begin; t < pt.tile_end; ++t) {
+        const float y = P.partials[(size_t)t * NACC + ND + q] - comp;
+        const float u = v + y;
+        comp = (u - v) - y;
+        v = u;
+      }
+      W.sf[q] = v;
+    }
+    __syncwarp();
     // ---- derivatives of the band moments over the type's brightness parameters
-    if (tid < 40) {
-      const int t = tid / 20, which = (tid % 20) / 10, v = tid % 10;
+    for (int q = lane; q < 40; q += 32) {
+      const int t = q / 20, which = (q % 20) / 10, v = q % 10;
       double arow[4];
       color_row(c.band, arow);
       double dl, d2;
@@ -205,16 +221,16 @@ __global__ void __launch_bounds__(128) assemble_kernel(ProblemDev P, const doubl
         cf.d2l1[t][v] = (float)d2;
       }
     }
-    if (tid == 64) Lsum += sd[ACC_L];
-    __syncthreads();
-    const double* S1 = sd + ACC_S1;
-    const double* S2 = sd + ACC_S2;
-    const float* S1h = sdf + ACC_S1;
-    const float* S2h = sdf + ACC_S2;
+    if (lane == 0) W.Lsum += W.sd[ACC_L];
+    __syncwarp();
+    const double* S1 = W.sd + ACC_S1;
+    const double* S2 = W.sd + ACC_S2;
+    const float* S1h = W.sdf + ACC_S1;
+    const float* S2h = W.sdf + ACC_S2;
     // ---- reduced gradient (float64)
-    if (tid < NRED) {
+    if (lane < NRED) {
       const double A0 = sc.a0 * c.L1[0], A1 = sc.a1 * c.L1[1], B0 = sc.a0 * c.L2[0], B1 = sc.a1 * c.L2[1];
-      const int a = tid;
+      const int a = lane;
       double v;
       if (a < 2)
         v = A0 * S1[1 + a] + A1 * S1[4 + a] + B0 * S2[1 + a] + B1 * S2[4 + a];
@@ -224,50 +240,51 @@ __global__ void __launch_bounds__(128) assemble_kernel(ProblemDev P, const doubl
         v = sc.aa * (c.L1[1] * S1[3] - c.L1[0] * S1[0] + c.L2[1] * S2[3] - c.L2[0] * S2[0]);
       else
         v = a == 7 ? S1[0] : a == 8 ? S1[3] : a == 9 ? S2[0] : S2[3];
-      ghat[a] = v;
+      W.ghat[a] = v;
     }
     // Lift from the 11-column reduced basis to the 27 parameters: column j of K has at most two
     // nonzeros (a, k): j < 7 -> (j, 1); brightness parameter v of type t -> (7 + t, a_t dL1_t[v])
     // from the E-row and (9 + t, a_t dL2_t[v]) from the V-row.  H_E = K^T M K + H2, g_E = K^T ghat.
-    if (tid >= 32 && tid < 32 + NP) {
-      const int j = tid - 32;
+    if (lane < NP) {
+      const int j = lane;
       if (j < 7) {
-        nzA[j] = j;
-        nzK[j] = 1.0;
-        nzB[j] = -1;
-        nzL[j] = 0.0;
+        W.nzA[j] = j;
+        W.nzK[j] = 1.0;
+        W.nzB[j] = -1;
+        W.nzL[j] = 0.0;
       } else {
         int t, v;
         bvar_inv(j, t, v);
         const double at = t ? sc.a1 : sc.a0;
-        nzA[j] = 7 + t;
-        nzK[j] = at * c.dL1[t][v];
-        nzB[j] = 9 + t;
-        nzL[j] = at * c.dL2[t][v];
+        W.nzA[j] = 7 + t;
+        W.nzK[j] = at * c.dL1[t][v];
+        W.nzB[j] = 9 + t;
+        W.nzL[j] = at * c.dL2[t][v];
       }
-      nzKf[j] = (float)nzK[j];
-      nzLf[j] = (float)nzL[j];
+      W.nzKf[j] = (float)W.nzK[j];
+      W.nzLf[j] = (float)W.nzL[j];
     }
-    for (int i = tid; i < NRED * NRED; i += nt) {
+    for (int i = lane; i < NRED * NRED; i += 32) {
       const int a = i / NRED, b = i % NRED;
-      Msym[i] = sf[ACC_M - ND + (a <= b ? tri11d(a, b) : tri11d(b, a))];
+      W.Msym[i] = W.sf[ACC_M - ND + (a <= b ? tri11d(a, b) : tri11d(b, a))];
     }
-    // second-order part  sum_m w1 d2E[G] + w2 d2E[G^2] (float32), filled block by block (uniform
-    // work per thread within a block):  G6 x G6 from the kernel's sums; G6 x alpha; alpha x alpha;
-    // G6 x brightness; alpha x brightness; brightness x brightness (same type only)
-    for (int i = tid; i < NP * NP; i += nt) H2[i] = 0.f;
-    __syncthreads();
-    for (int q = tid; q < 21; q += nt) {
+    // second-order part  sum_m w1 d2E[G] + w2 d2E[G^2] (float32), filled block by block:
+    // G6 x G6 from the kernel's sums; G6 x alpha; alpha x alpha; G6 x brightness;
+    // alpha x brightness; brightness x brightness (same type only)
+    float* H2 = W.H2;
+    for (int i = lane; i < NP * NP; i += 32) H2[i] = 0.f;
+    __syncwarp();
+    for (int q = lane; q < 21; q += 32) {
       int a = 0, rem = q;
       while (rem >= 6 - a) {
         rem -= 6 - a;
         ++a;
       }
       const int b = a + rem;
-      H2[a * NP + b] = H2[b * NP + a] = sf[ACC_HP - ND + q];
+      H2[a * NP + b] = H2[b * NP + a] = W.sf[ACC_HP - ND + q];
     }
     const float S1f[2] = {S1h[0], S1h[3]}, S2f[2] = {S2h[0], S2h[3]};
-    for (int i = tid; i < 6 + 1 + 120 + 20 + 200; i += nt) {
+    for (int i = lane; i < 6 + 1 + 120 + 20 + 200; i += 32) {
       if (i < 6) {
         const int a = i;
         const float s1f0 = a < 2 ? S1h[1 + a] : 0.f, s2f0 = a < 2 ? S2h[1 + a] : 0.f;
@@ -294,31 +311,33 @@ __global__ void __launch_bounds__(128) assemble_kernel(ProblemDev P, const doubl
         H2[bvar(t, v) * NP + bvar(t, w)] = (t ? cf.a1 : cf.a0) * (S1f[t] * d2L1 + S2f[t] * d2L2);
       }
     }
-    __syncthreads();
-    for (int q = tid; q < NP * (NP + 1) / 2; q += nt) {
+    __syncwarp();
+    // H_E = K^T M K + H2, in place over H2 (each pair (r <= col) reads only its own upper entry)
+    for (int q = lane; q < NP * (NP + 1) / 2; q += 32) {
       int r = 0, rem = q;   // q -> (r, col) with r <= col
       while (rem >= NP - r) {
         rem -= NP - r;
         ++r;
       }
       const int col = r + rem;
-      float v = nzKf[r] * nzKf[col] * Msym[nzA[r] * NRED + nzA[col]];
-      if (nzB[col] >= 0) v += nzKf[r] * nzLf[col] * Msym[nzA[r] * NRED + nzB[col]];
-      if (nzB[r] >= 0) {
-        v += nzLf[r] * nzKf[col] * Msym[nzB[r] * NRED + nzA[col]];
-        if (nzB[col] >= 0) v += nzLf[r] * nzLf[col] * Msym[nzB[r] * NRED + nzB[col]];
+      float v = W.nzKf[r] * W.nzKf[col] * W.Msym[W.nzA[r] * NRED + W.nzA[col]];
+      if (W.nzB[col] >= 0) v += W.nzKf[r] * W.nzLf[col] * W.Msym[W.nzA[r] * NRED + W.nzB[col]];
+      if (W.nzB[r] >= 0) {
+        v += W.nzLf[r] * W.nzKf[col] * W.Msym[W.nzB[r] * NRED + W.nzA[col]];
+        if (W.nzB[col] >= 0) v += W.nzLf[r] * W.nzLf[col] * W.Msym[W.nzB[r] * NRED + W.nzB[col]];
       }
       v += H2[r * NP + col];
-      HE[r * NP + col] = v;
-      HE[col * NP + r] = v;
+      H2[r * NP + col] = v;
+      H2[col * NP + r] = v;
     }
-    if (tid < NP) {
-      const int j = tid;
-      gE[j] = nzK[j] * ghat[nzA[j]] + (nzB[j] >= 0 ? nzL[j] * ghat[nzB[j]] : 0.0);
+    if (lane < NP) {
+      const int j = lane;
+      W.gE[j] = W.nzK[j] * W.ghat[W.nzA[j]] + (W.nzB[j] >= 0 ? W.nzL[j] * W.ghat[W.nzB[j]] : 0.0);
     }
-    __syncthreads();
+    __syncwarp();
     // map mu -> u: d/du_b = sum_a A[a][b] d/dmu_a
-    for (int i = tid; i < NP * NP; i += nt) {
+    const float* HE = H2;
+    for (int i = lane; i < NP * NP; i += 32) {
       const int r = i / NP, q = i % NP;
       float v;
       if (r < 2 && q < 2) {
@@ -332,14 +351,20 @@ __global__ void __launch_bounds__(128) assemble_kernel(ProblemDev P, const doubl
       } else {
         v = HE[i];
       }
-      Hs[i] += v;
+      W.Hs[i] += v;
     }
-    for (int j = tid; j < NP; j += nt) {
-      double v = j < 2 ? c.A[0 * 2 + j] * gE[0] + c.A[1 * 2 + j] * gE[1] : gE[j];
-      gs[j] += v;
+    if (lane < NP) {
+      const int j = lane;
+      W.gs[j] += j < 2 ? c.A[0 * 2 + j] * W.gE[0] + c.A[1 * 2 + j] * W.gE[1] : W.gE[j];
     }
-    __syncthreads();
+    __syncwarp();
   }
+  __syncthreads();
+  // ---- the warps' sums (fixed order)
+  for (int i = tid; i < NP * NP; i += nt) Hs[i] = (wl[0].Hs[i] + wl[1].Hs[i]) + (wl[2].Hs[i] + wl[3].Hs[i]);
+  if (tid < NP) gs[tid] = (wl[0].gs[tid] + wl[1].gs[tid]) + (wl[2].gs[tid] + wl[3].gs[tid]);
+  if (tid == 0) Lsum = (wl[0].Lsum + wl[1].Lsum) + (wl[2].Lsum + wl[3].Lsum);
+  __syncthreads();
 
   // ---- KL = a1 (log a1 - log Phi) + a0 (log a0 - log(1 - Phi)) + a0 K_0 + a1 K_1 and its
   //      derivatives (closed forms from the source constants; no further transcendentals)
