@@ -2,9 +2,12 @@
 """Benchmark: light sources per second to convergence, batched trust-region Newton on one GPU.
 
 One step = one block-coordinate pass over a synthetic field (2048x1489 px x 5 bands, 1000 sources,
-patch radius 8-32 px by brightness): render the neighbours' fixed background, then run
-trust-region Newton (ELBO + exact gradient + dense Hessian per iteration) on every source until
-all have stopped.  Under torchrun every rank solves its own independently seeded field (weak
+patch radius 8-32 px by brightness): render the neighbours' fixed background, run the learned
+warm-start network on every source's patch, then run trust-region Newton (ELBO + exact gradient +
+dense Hessian per iteration) on every source from that start until all have stopped.  The network
+is trained before the timed region on pairs from two freshly seeded scenes; the plain form
+(Newton from the catalog, no network) is timed as well and reported as "plain_fp32"
+(--no-warm-start times only the plain form).  Under torchrun every rank solves its own independently seeded field (weak
 scaling, no collective on the data path); the timing is the max over ranks.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -58,10 +61,12 @@ def parse():
                          "mosaic: 10x10 overlapping fields, 100,000 sources, 1-12 exposures each")
     ap.add_argument("--sources", type=int, default=1000)
     ap.add_argument("--tile", type=int, default=128, help="pixels per tile; 0 = autotune")
-    ap.add_argument("--warm-start", action="store_true",
-                    help="learned warm start: train the CNN on (patch, converged parameters) pairs of two freshly "
-                         "seeded workloads of the same kind, then start every timed Newton solve from its prediction "
-                         "(inference inside the timed region)")
+    ap.add_argument("--no-warm-start", dest="warm_start", action="store_false",
+                    help="time only the plain form (Newton from the catalog).  By default the learned warm start is "
+                         "trained first (on (patch, converged parameters) pairs of two freshly seeded scenes of the "
+                         "same kind, outside the timed region) and every timed Newton solve starts from its "
+                         "prediction (inference inside the timed region); the plain form is timed too and reported "
+                         "beside it")
     ap.add_argument("--ws-epochs", type=int, default=6)
     ap.add_argument("--hessian", default="fp32", choices=["fp32", "tf32", "bf16x3"],
                     help="Jacobian cross-product of the Hessian: FP32 FMAs or tensor cores (TF32, BF16 hi+lo)")
@@ -159,6 +164,7 @@ def cpu_baseline(scene, seconds):
 def run_reference(args, rank, world):
     if rank != 0:
         return
+    args.warm_start = False   # the oracle runs the method as written: Newton from the catalog
     import torch
     import synth
     scene = synth.field(seed=args.seed, n_sources=args.sources)
@@ -227,33 +233,68 @@ def main():
     delta = torch.zeros(scene.n_sources, dtype=torch.float64, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
-    net, ws_info = None, None
-    if args.warm_start:
-        net, ws_info = train_warm_start(args, P, dev, rank)
-        # the plain form on the same workload, for the iterations the warm start saves (untimed)
-        theta.copy_(theta0)
-        prob.render_background(theta0)
-        _, it_cat, st_cat, _ = prob.newton_batch(theta, delta.zero_())
-        ws_info["iters_mean_catalog_start"] = float(it_cat.double().mean())
-        ws_info["converged_catalog_start"] = int((st_cat == P.STATUS_CONVERGED).sum())
-        th_cat = theta.clone()
+    net, ws_info, plain = None, None, None
+    stream = torch.cuda.current_stream()
 
-    def step():
+    def plain_step():
         delta.zero_()
         prob.render_background(theta0)
-        if net is not None:
-            from paper_1611_03404_gb300 import cnn
-            pred = net.predict(prob.extract_patches())
-            theta.copy_(cnn.warm_start(theta0, pred))
-        else:
-            theta.copy_(theta0)
+        theta.copy_(theta0)
         return prob.newton_batch(theta, delta)
+
+    def warm_step():
+        from paper_1611_03404_gb300 import cnn
+        delta.zero_()
+        prob.render_background(theta0)
+        pred = net.predict(prob.extract_patches())
+        theta.copy_(cnn.warm_start(theta0, pred))
+        return prob.newton_batch(theta, delta)
+
+    def time_steps(fn):
+        """W untimed steps, then K steps timed by CUDA events (L2 flushed before each); max over ranks."""
+        for _ in range(max(args.warmup, 0)):
+            fn()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        out = None
+        for k in range(args.steps):
+            flush.zero_()
+            evs[k][0].record(stream)
+            out = fn()
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+        t = float(np.sum([a.elapsed_time(b) for a, b in evs])) / 1e3
+        if world > 1:
+            tt = torch.tensor([t], device=dev, dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            t = float(tt)
+        return t, out
+
+    if args.warm_start:
+        net, ws_info = train_warm_start(args, P, dev, rank)
+        # the plain form (Newton from the catalog) on the same workload, timed the same way
+        t_plain, (_, it_cat, st_cat, _) = time_steps(plain_step)
+        th_cat = theta.clone()
+        conv_plain = int((st_cat == P.STATUS_CONVERGED).sum())
+        if world > 1:
+            c = torch.tensor([conv_plain], device=dev, dtype=torch.float64)
+            dist.all_reduce(c, op=dist.ReduceOp.SUM)
+            conv_plain_total = float(c)
+        else:
+            conv_plain_total = conv_plain
+        plain = {"value": conv_plain_total / (t_plain / args.steps), "ms_per_step": 1e3 * t_plain / args.steps,
+                 "newton_iters_mean": float(it_cat.double().mean()), "converged": conv_plain,
+                 "form": "plain FP32 path, Newton from the catalog"}
+        ws_info["iters_mean_catalog_start"] = plain["newton_iters_mean"]
+        ws_info["converged_catalog_start"] = conv_plain
+    step = warm_step if net is not None else plain_step
 
     for _ in range(max(args.warmup, 0)):
         step()
     torch.cuda.synchronize()
 
-    stream = torch.cuda.current_stream()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     if world > 1:
         dist.barrier()
@@ -272,6 +313,8 @@ def main():
         prof = prof_stats = prob.profile_stop()
     conv = int((status == P.STATUS_CONVERGED).sum())
     iters_mean = float(iters.double().mean())
+    # warm-start inference per timed step: patch extraction + six GEMM launches per batch of 4096
+    cnn_launches = args.steps * (1 + 6 * ((scene.n_sources + 4095) // 4096)) if net is not None else 0
     if ws_info is not None:
         from paper_1611_03404_gb300 import cnn
         ws_info["iters_mean_warm_start"] = iters_mean
@@ -359,7 +402,7 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": "sources/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(args, tile),
-                "autotune_us_per_1000px": tune, "warm_start": ws_info,
+                "autotune_us_per_1000px": tune, "warm_start": ws_info, "plain_fp32": plain,
                 "pixel_evals_per_s": px_rate, "converged": conv, "newton_iters_mean": iters_mean,
                 "newton_iters_max": iters_max, "status_counts": status_counts,
                 "layout": counts, "wall_s_timed": wall,
@@ -371,7 +414,8 @@ def main():
                              "flops_per_pixel": FLOPS_FULL_PER_PIXEL,
                              "launches": prof["full_launches"], "kernel_ms": full_ms,
                              "share_of_step": full_ms / (1e3 * t_step) if t_step > 0 else None},
-                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": prof["kernel_launches"], "clocks": clocks}
+                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": prof["kernel_launches"] + cnn_launches,
+                "clocks": clocks}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -379,18 +423,23 @@ def main():
 
 def train_warm_start(args, P, dev, rank):
     """Trains the warm-start network on (patch, converged parameters) pairs of two freshly seeded
-    workloads of the bench's kind (Newton from their catalogs, neighbours fixed at the catalog)."""
+    100k-source scenes of the bench's kind (mosaics; for the field workload with the field's five
+    bands per exposure and radius rule), solved by Newton from their catalogs with neighbours fixed
+    at the catalog."""
     import torch
     import synth
     from paper_1611_03404_gb300 import cnn
     t0 = time.perf_counter()
     xs, ts = [], []
+    from synth.mosaic import mosaic
     for k in (101, 102):
         if args.workload == "mosaic":
-            from synth.mosaic import mosaic
             sc = mosaic(seed=args.seed + rank + k, device=dev)
         else:
-            sc = synth.field(seed=args.seed + rank + k, n_sources=args.sources)
+            # field-like exposures (all five bands per field, the field's radius rule), rendered on the
+            # GPU: 100k sources per training scene instead of the field's 1000
+            sc = mosaic(seed=args.seed + rank + k, bands_per_field=(5, 5), extended=0.0, rmax=32,
+                        radius_rule="brightness", device=dev)
         pr = P.Problem(sc, device=dev, tile_pixels=128)
         th = torch.as_tensor(sc.theta0, device=dev).contiguous()
         pr.render_background(th.clone())

@@ -120,7 +120,8 @@ def _patch_radius_v(img, pos, is_gal, e_scale, counts, rmin, rmax):
 
 
 def mosaic(seed=1611, fields_x=10, fields_y=10, n_sources=100_000, field_W=2048, field_H=1489, overlap=0.2,
-           bands_per_field=(1, 3), p_gal=0.6, extended=0.02, rmin=8, rmax=64, noise=True, priors=None, device=None):
+           bands_per_field=(1, 3), p_gal=0.6, extended=0.02, rmin=8, rmax=64, radius_rule="brightness+4sigma",
+           noise=True, priors=None, device=None):
     """A fields_x x fields_y grid of fields stepping by (1 - overlap) of the field size; each field
     observed in a random subset of 1-3 bands (one exposure each, its pixel grid rotated by up to
     0.02 rad, scaled by 0.98-1.02 and offset by a sub-pixel shift); sources uniform over the
@@ -129,7 +130,9 @@ def mosaic(seed=1611, fields_x=10, fields_y=10, n_sources=100_000, field_W=2048,
 
     Catalog as in the field scenes, plus a fraction `extended` of the galaxies with half-light
     radius U(4, 8) px.  Patch radius: the larger of the field scenes' brightness rule and 4 sigma of
-    the source's widest true component, clamped to [rmin, rmax]."""
+    the source's widest true component, clamped to [rmin, rmax]; radius_rule="brightness" keeps the
+    field scenes' rule alone (with bands_per_field=(5, 5), extended=0 and rmax=32 the exposures
+    look like the field scenes')."""
     rng = np.random.default_rng(seed)
     priors = DEFAULT_PRIORS.copy() if priors is None else np.asarray(priors, np.float64)
     device = torch.device(device or ("cuda" if torch.cuda.is_available() else "cpu"))
@@ -177,8 +180,11 @@ def mosaic(seed=1611, fields_x=10, fields_y=10, n_sources=100_000, field_W=2048,
         sel = np.nonzero((cxy[:, 0] >= 0) & (cxy[:, 0] <= W - 1) & (cxy[:, 1] >= 0) & (cxy[:, 1] <= H - 1))[0]
         n_img[sel] += 1
         r = _patch_radius_v(im, pos[sel], g[sel], shp[sel, 3], im.iota * fl[sel, im.band], rmin, rmax)
-        wts, _, cvs = _components(im, pos[sel], g[sel], shp[sel])
-        radius_f[sel] = np.maximum(radius_f[sel], np.maximum(r, _window(cvs, wts, cap=rmax)))
+        if radius_rule == "brightness":
+            radius_f[sel] = np.maximum(radius_f[sel], r)
+        else:
+            wts, _, cvs = _components(im, pos[sel], g[sel], shp[sel])
+            radius_f[sel] = np.maximum(radius_f[sel], np.maximum(r, _window(cvs, wts, cap=rmax)))
     radius = np.clip(np.ceil(radius_f), rmin, rmax).astype(np.int32)
     truth = dict(u=u, is_gal=g, log_r=lr, colors=col, shape=shp, n_images=n_img)
     return Scene(images, theta0[:, 0:2].copy(), radius, theta0, priors, truth=truth,
