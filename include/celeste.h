@@ -177,6 +177,15 @@ int celeste_newton_batch(celeste_problem* p, double* theta_inout, const celeste_
                          double* delta_inout, int32_t* iters_out, int32_t* status_out,
                          double* elbo_out, celeste_stream_t stream);
 
+/* Linear-response covariance of every source's variational parameters at theta (normally the
+ * optimum from celeste_newton_batch): cov_s = (-H_s)^-1, H_s the exact ELBO Hessian w.r.t. the 27
+ * free parameters (Sec. "Variational Inference", the Newton solver's curvature reused).
+ *   theta: device float64 [S][27]; cov: device float64 [S][27][27] out; ok: device int32 [S] out,
+ *   1 where -H_s is positive definite (else cov_s is NaN).  Uses the problem's Newton workspace;
+ *   the background must be rendered. */
+int celeste_covariance_batch(celeste_problem* p, const double* theta, double* cov, int32_t* ok,
+                             celeste_stream_t stream);
+
 /* The trust-region subproblem of celeste_newton_batch on its own, for n independent problems
  * (Sec. "Variational Inference": Newton's method with a trust region):
  *     p = argmin g.p + p.B.p/2  subject to |p| <= delta.

@@ -54,7 +54,7 @@ EXPORTED = ["celeste_problem_create", "celeste_problem_workspace_bytes", "celest
             "celeste_problem_destroy", "celeste_strerror", "celeste_last_error_detail", "celeste_profile_start",
             "celeste_profile_stop", "celeste_tr_solve_batch", "celeste_elbo_batch_noalloc", "celeste_cnn_param_count",
             "celeste_cnn_workspace_bytes", "celeste_cnn_init", "celeste_cnn_forward", "celeste_cnn_backward",
-            "celeste_cnn_mse", "celeste_cnn_adamw", "celeste_extract_patches"]
+            "celeste_cnn_mse", "celeste_cnn_adamw", "celeste_extract_patches", "celeste_covariance_batch"]
 
 
 def load_library(path=None):
@@ -87,6 +87,7 @@ def load_library(path=None):
         "celeste_cnn_adamw": (ctypes.c_int, [dp, dp, dp, dp, dp, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                              ctypes.c_float, ctypes.c_float, ctypes.c_int, vp]),
         "celeste_extract_patches": (ctypes.c_int, [vp, dp, vp]),
+        "celeste_covariance_batch": (ctypes.c_int, [vp, dp, dp, dp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -203,6 +204,14 @@ class Problem:
         _check(lib().celeste_newton_batch(self.handle, _ptr(theta), ctypes.byref(opts), _ptr(delta), _ptr(iters),
                                           _ptr(status), _ptr(elbo), _stream(stream)))
         return delta, iters, status, elbo
+
+    def covariance(self, theta, stream=None):
+        """Linear-response covariance (-H)^-1 per source at theta: ([S, 27, 27] float64, ok [S])."""
+        assert theta.dtype == torch.float64 and theta.is_contiguous() and theta.shape == (self.S, NPARAM)
+        cov = torch.empty(self.S, NPARAM, NPARAM, dtype=torch.float64, device=theta.device)
+        ok = torch.empty(self.S, dtype=torch.int32, device=theta.device)
+        _check(lib().celeste_covariance_batch(self.handle, _ptr(theta), _ptr(cov), _ptr(ok), _stream(stream)))
+        return cov, ok
 
     def extract_patches(self, stream=None):
         """The warm-start network's input for every source: int16 [S, 32, 32, 5] BF16 bit patterns."""

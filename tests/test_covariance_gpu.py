@@ -1,0 +1,66 @@
+"""Linear-response covariance (-H)^-1 at the optimum, against the float64 oracle's Hessian, plus
+the truth-recovery and calibration report on a seeded field (printed with pytest -s).
+
+The GPU Hessian carries float32 rounding of about 1e-6 of each entry's natural scale
+sqrt(|H_ii H_jj|) (see the parity tests); to first order the inverse then moves by
+Sigma dH Sigma, so each variance is held to ten times that bound computed with a 1e-5 scale."""
+import json
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import celeste_oracle as O
+from synth.metrics import truth_recovery
+
+pytestmark = pytest.mark.gpu
+
+
+def test_covariance_matches_oracle_and_calibration_report():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1611_03404_gb300 as P
+    dev = torch.device("cuda:0")
+    sc = synth.field(seed=1621, W=1024, H=745, n_sources=300)
+    prob = P.Problem(sc, device=dev)
+    th0 = torch.as_tensor(sc.theta0, device=dev).contiguous()
+    prob.render_background(th0)
+    th = th0.clone()
+    _, iters, status, _ = prob.newton_batch(th)
+    cov, ok = prob.covariance(th)
+    torch.cuda.synchronize()
+    conv = (status == P.STATUS_CONVERGED).cpu().numpy()
+    okn = ok.cpu().numpy().astype(bool)
+    assert okn[conv].mean() >= 0.95
+    cov, thn = cov.cpu().numpy(), th.cpu().numpy()
+    orc = O.Oracle(sc)
+    rng = np.random.default_rng(2)
+    cand = [s for s in rng.permutation(sc.n_sources) if conv[s] and okn[s] and orc.rects[s]][:5]
+    for s in cand:
+        _, _, H = orc.elbo_grad_hess(s, thn[s], sc.theta0)
+        Sig = np.linalg.inv(-H)
+        dH = 1e-5 * np.sqrt(np.abs(np.outer(np.diag(H), np.diag(H))))
+        bound = np.einsum("ij,jk,ki->i", np.abs(Sig), dH, np.abs(Sig))
+        err = np.abs(np.diag(cov[s]) - np.diag(Sig))
+        assert np.all(err <= 10 * bound + 1e-12 * np.abs(np.diag(Sig))), (s, float((err / (bound + 1e-300)).max()))
+        assert np.abs(cov[s] - cov[s].T).max() <= 1e-6 * np.abs(np.diag(cov[s])).max()
+    # calibration on the truth: z-scores of the truth under the linear-response posterior
+    use = conv & okn
+    tr = sc.truth
+    z_pos = ((thn[use, 0:2] - tr["u"][use]) / np.sqrt(np.stack([cov[use, 0, 0], cov[use, 1, 1]], 1))).ravel()
+    gal = tr["is_gal"][use]
+    j = np.where(gal, 9, 7)
+    r_sd = np.sqrt(cov[use][np.arange(use.sum()), j, j])
+    z_r = (thn[use][np.arange(use.sum()), j] - tr["log_r"][use]) / r_sd
+    report = {"sources": int(use.sum()),
+              "position_z_within_1": float(np.mean(np.abs(z_pos) < 1)), "position_z_within_2": float(np.mean(np.abs(z_pos) < 2)),
+              "log_flux_z_within_1": float(np.mean(np.abs(z_r) < 1)), "log_flux_z_within_2": float(np.mean(np.abs(z_r) < 2)),
+              "truth_recovery": truth_recovery(sc, thn)}
+    print("CALIBRATION " + json.dumps(report))
+    # calibration and type recovery are reported, not required: faint small galaxies are
+    # indistinguishable from stars at these noise levels
+    assert report["truth_recovery"]["position_px_median"] < 0.5
+    assert 0.5 < report["position_z_within_1"] < 0.9
