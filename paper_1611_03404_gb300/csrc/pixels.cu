@@ -213,6 +213,62 @@ __device__ __forceinline__ void syrk_mma(const float (*As)[SYRK_LD], const float
   }
 }
 
+// One galaxy mixture component's contribution at pixel offset d (squares s): value, 5 first and 15
+// second derivatives over v5 = (mu0, mu1, axis, angle, scale), accumulated into its family's sums.
+__device__ __forceinline__ void gal_component(const float* ep, float d0, float d1, float s0, float s1, float s2,
+                                              float& F, float (&Fv)[5], float (&Fvv)[15]) {
+  float e[GT_STRIDE];
+  {
+    const float4* e4 = reinterpret_cast<const float4*>(ep);
+#pragma unroll
+    for (int w = 0; w < GT_STRIDE / 4; ++w) {
+      const float4 t4 = e4[w];
+      e[4 * w + 0] = t4.x;
+      e[4 * w + 1] = t4.y;
+      e[4 * w + 2] = t4.z;
+      e[4 * w + 3] = t4.w;
+    }
+  }
+  const float q = e[GT_P] * s0 + e[GT_P + 1] * s1 + e[GT_P + 2] * s2;
+  const float N = e[GT_W] * exp2f(q * (-0.5f * LOG2E));
+  const float z0 = e[GT_P] * d0 + e[GT_P + 1] * d1, z1 = e[GT_P + 1] * d0 + e[GT_P + 2] * d1;
+  float b[3], t0[3], t1[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float* Q = e + GT_QA + 3 * a;
+    b[a] = e[GT_LA + a] + Q[0] * s0 + Q[1] * s1 + Q[2] * s2;
+    t0[a] = Q[0] * d0 + Q[1] * d1;   // (Q_a d); (dP/da) d = -2 Q_a d
+    t1[a] = Q[1] * d0 + Q[2] * d1;
+  }
+  const float Nz0 = N * z0, Nz1 = N * z1, Nm2 = -2.f * N;
+  F += N;
+  Fv[0] += Nz0;
+  Fv[1] += Nz1;
+  float Nb[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    Nb[a] = N * b[a];
+    Fv[2 + a] += Nb[a];
+  }
+  Fvv[tri5(0, 0)] += Nz0 * z0 - N * e[GT_P];
+  Fvv[tri5(0, 1)] += Nz0 * z1 - N * e[GT_P + 1];
+  Fvv[tri5(1, 1)] += Nz1 * z1 - N * e[GT_P + 2];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    Fvv[tri5(0, 2 + a)] += Nz0 * b[a] + Nm2 * t0[a];
+    Fvv[tri5(1, 2 + a)] += Nz1 * b[a] + Nm2 * t1[a];
+  }
+  int pq = 0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int bb = a; bb < 3; ++bb, ++pq) {
+      const float* Q = e + GT_QAB + 3 * pq;
+      const float cab = e[GT_LAB + pq] + Q[0] * s0 + Q[1] * s1 + Q[2] * s2;
+      Fvv[tri5(2 + a, 2 + bb)] += Nb[a] * b[bb] + N * cab;
+    }
+}
+
 // ------------------------------------------------------------------------------ full kernel
 // HM: 0 all sums on the FP32 pipes; 1 / 2 the Jacobian cross-product on the tensor cores with
 // TF32 / BF16 hi+lo operands.
@@ -285,60 +341,14 @@ __global__ void __launch_bounds__(BLOCK) elbo_full_kernel(ProblemDev P) {
         f0mm[1] += N * (z0 * z1 - st.z);
         f0mm[2] += N * (z1 * z1 - st.w);
       }
-#pragma unroll
-      for (int j = 0; j < NMIX; ++j) {
-        const int fam = j < CELESTE_NEXP ? 0 : 1;
-        float e[GT_STRIDE];
-        {
-          const float4* e4 = reinterpret_cast<const float4*>(&tab[TB_GAL + (k * NMIX + j) * GT_STRIDE]);
-#pragma unroll
-          for (int w = 0; w < GT_STRIDE / 4; ++w) {
-            const float4 t4 = e4[w];
-            e[4 * w + 0] = t4.x;
-            e[4 * w + 1] = t4.y;
-            e[4 * w + 2] = t4.z;
-            e[4 * w + 3] = t4.w;
-          }
-        }
-        const float q = e[GT_P] * s0 + e[GT_P + 1] * s1 + e[GT_P + 2] * s2;
-        const float N = e[GT_W] * exp2f(q * (-0.5f * LOG2E));
-        const float z0 = e[GT_P] * d0 + e[GT_P + 1] * d1, z1 = e[GT_P + 1] * d0 + e[GT_P + 2] * d1;
-        float b[3], t0[3], t1[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          const float* Q = e + GT_QA + 3 * a;
-          b[a] = e[GT_LA + a] + Q[0] * s0 + Q[1] * s1 + Q[2] * s2;
-          t0[a] = Q[0] * d0 + Q[1] * d1;   // (Q_a d); (dP/da) d = -2 Q_a d
-          t1[a] = Q[1] * d0 + Q[2] * d1;
-        }
-        const float Nz0 = N * z0, Nz1 = N * z1, Nm2 = -2.f * N;
-        F[fam] += N;
-        Fv[fam][0] += Nz0;
-        Fv[fam][1] += Nz1;
-        float Nb[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          Nb[a] = N * b[a];
-          Fv[fam][2 + a] += Nb[a];
-        }
-        Fvv[fam][tri5(0, 0)] += Nz0 * z0 - N * e[GT_P];
-        Fvv[fam][tri5(0, 1)] += Nz0 * z1 - N * e[GT_P + 1];
-        Fvv[fam][tri5(1, 1)] += Nz1 * z1 - N * e[GT_P + 2];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          Fvv[fam][tri5(0, 2 + a)] += Nz0 * b[a] + Nm2 * t0[a];
-          Fvv[fam][tri5(1, 2 + a)] += Nz1 * b[a] + Nm2 * t1[a];
-        }
-        int pq = 0;
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-#pragma unroll
-          for (int bb = a; bb < 3; ++bb, ++pq) {
-            const float* Q = e + GT_QAB + 3 * pq;
-            const float cab = e[GT_LAB + pq] + Q[0] * s0 + Q[1] * s1 + Q[2] * s2;
-            Fvv[fam][tri5(2 + a, 2 + bb)] += Nb[a] * b[bb] + N * cab;
-          }
-      }
+      // one family at a time, rolled loops: the component body stays small enough for the
+      // instruction cache, and each family's accumulators stay statically indexed
+#pragma unroll 1
+      for (int j = 0; j < CELESTE_NEXP; ++j)
+        gal_component(&tab[TB_GAL + (k * NMIX + j) * GT_STRIDE], d0, d1, s0, s1, s2, F[0], Fv[0], Fvv[0]);
+#pragma unroll 1
+      for (int j = CELESTE_NEXP; j < NMIX; ++j)
+        gal_component(&tab[TB_GAL + (k * NMIX + j) * GT_STRIDE], d0, d1, s0, s1, s2, F[1], Fv[1], Fvv[1]);
     }
 
     // ---- galaxy profile over G6 = (mu0, mu1, dev, axis, angle, scale);  v5 index -> G6 index:
