@@ -127,6 +127,12 @@ __device__ inline int wl_next_cta(const ProblemDev& P, int which, int& slot) {
   return item;
 }
 
+// One thread's fetch from the work queue (the caller publishes the result to the CTA).
+__device__ inline int wl_take(const ProblemDev& P, int which) {
+  const int i = atomicAdd(P.wl_count + 3 + which, 1);
+  return i < P.wl_count[which] ? wl_list(P, which)[i] : -1;
+}
+
 // The same for one warp (lane 0 takes the item, a shuffle broadcasts it).
 __device__ inline int wl_next_warp(const ProblemDev& P, int which) {
   int item = -1;

@@ -15,10 +15,11 @@
 // dE[G] are f_i times a per-(source, image) constant vector), C_m the 2x2 curvature of the
 // pixel term, w1 = iota l_E - 2 iota^2 E[G] l_V and w2 = iota^2 l_V.
 //
-// A CTA of 128 threads takes one tile (up to 128 * PPT consecutive pixels of one patch).  Thread 0
-// brings the patch table and the tile's pixel records into shared memory with two TMA bulk
-// copies on one mbarrier.  Each thread evaluates its pixels; each warp reduce-scatters the 108
-// per-pixel contributions so that lane l keeps sums l, l+32, l+64, l+96 (4 registers, not 108).
+// A CTA of 128 threads takes tiles (up to 128 * PPT consecutive pixels of one patch) from the
+// work queue.  Thread 0 brings each tile's patch table and pixel records into shared memory with
+// two TMA bulk copies on one mbarrier, the next tile's while the current one is evaluated.  Each
+// thread evaluates its pixels; each warp reduce-scatters the 108 per-pixel contributions so that
+// lane l keeps sums l, l+32, l+64, l+96 (4 registers, not 108).
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -65,24 +66,31 @@ __device__ __forceinline__ float warp_reduce_scatter32(float (&v)[32], int lane)
   return v[0];
 }
 
-// Stage the patch table and the tile's pixel records (one mbarrier, two bulk copies). The barrier
-// is initialised once per CTA; `phase` is the parity of this use. The caller has synchronised the
-// CTA since the buffers were last read.
-__device__ __forceinline__ bool stage_tile(const ProblemDev& P, const TileDev& t, const PatchDev& pt, float* tab,
-                                           float4* spix, uint64_t* bar, uint32_t phase, int tid) {
-  if (tid == 0) {
-    fence_proxy_async_smem();
-    const uint32_t tb = TB_FLOATS * 4u, pb = (uint32_t)t.count * 16u;
-    mbar_expect_tx(bar, tb + pb);
-    bulk_copy(tab, P.ptab + (size_t)t.patch * TB_FLOATS, tb, bar);
-    bulk_copy(spix, P.pix + pt.pix_off + t.start, pb, bar);
-  }
+// Thread 0: bulk copies of tile `tile`'s patch table and pixel records into (tab, spix),
+// completing on bar (one expect_tx for both).  The caller has synchronised the CTA since the
+// buffer was last read; the proxy fence orders those generic reads before the async writes.
+__device__ __forceinline__ void issue_tile(const ProblemDev& P, int tile, float* tab, float4* spix, uint64_t* bar) {
+  const TileDev t = P.tiles[tile];
+  fence_proxy_async_smem();
+  const uint32_t tb = TB_FLOATS * 4u, pb = (uint32_t)t.count * 16u;
+  mbar_expect_tx(bar, tb + pb);
+  bulk_copy(tab, P.ptab + (size_t)t.patch * TB_FLOATS, tb, bar);
+  bulk_copy(spix, P.pix + P.patches[t.patch].pix_off + t.start, pb, bar);
+}
+
+// All threads: wait (bounded) for a staged buffer.  On a timeout: error word, a last bounded wait
+// for these copies and for the other buffer's when they are in flight (so that no copy lands
+// after the CTA has left), and false on every thread.
+__device__ __forceinline__ bool wait_tile(const ProblemDev& P, uint64_t* bar, uint32_t phase, uint64_t* other,
+                                          uint32_t other_phase, bool other_busy) {
   bool ok = mbar_wait(bar, phase, WAIT_BUDGET);
   if (!ok) {
     atomicExch(P.err + ERR_TIMEOUT, 1);
-    mbar_wait(bar, phase, WAIT_BUDGET);   // give the copies in flight a last chance before leaving
+    mbar_wait(bar, phase, WAIT_BUDGET);
   }
-  return __syncthreads_and(ok);
+  ok = __syncthreads_and(ok);
+  if (!ok && other_busy && threadIdx.x == 0) mbar_wait(other, other_phase, WAIT_BUDGET);
+  return ok;
 }
 
 // Per-pixel quantities that the 108 sums are built from.
@@ -272,33 +280,53 @@ __device__ __forceinline__ void gal_component(const float* ep, float d0, float d
 // ------------------------------------------------------------------------------ full kernel
 // HM: 0 all sums on the FP32 pipes; 1 / 2 the Jacobian cross-product on the tensor cores with
 // TF32 / BF16 hi+lo operands.
+// Tiles are double-buffered (HM = 0): the next tile's copies are issued before the current one
+// is evaluated.  The tensor-core variants keep one buffer (their staging area fills the rest of
+// the 48 KB of static shared memory).
 template <int PPT, int HM>
 __global__ void __launch_bounds__(BLOCK) elbo_full_kernel(ProblemDev P) {
-  __shared__ __align__(16) float tab[TB_FLOATS];
-  __shared__ __align__(16) float4 spix[BLOCK * PPT];
-  __shared__ __align__(8) uint64_t bar;
+  constexpr int NB = HM == 0 ? 2 : 1;
+  __shared__ __align__(16) float tab_buf[NB][TB_FLOATS];
+  __shared__ __align__(16) float4 spix_buf[NB][BLOCK * PPT];
+  __shared__ __align__(8) uint64_t bar[NB];
   __shared__ float red[BLOCK / 32][128];
   __shared__ __align__(16) float syrk[HM ? BLOCK / 32 : 1][2][16][SYRK_LD];
 
   __shared__ int slot;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (tid == 0) mbar_init(&bar, 1);
+  if (tid == 0)
+    for (int b = 0; b < NB; ++b) mbar_init(&bar[b], 1);
   if constexpr (HM != 0) {   // padding rows 11..15 of A' and B'^T stay zero
     for (int i = lane; i < 5 * SYRK_LD; i += 32) {
       syrk[warp][0][11 + i / SYRK_LD][i % SYRK_LD] = 0.f;
       syrk[warp][1][11 + i / SYRK_LD][i % SYRK_LD] = 0.f;
     }
   }
+  // Iteration it uses buffer it % NB for its (it / NB + 1)-th time: the barrier's phase parity is
+  // (it / NB) & 1.  Thread 0 takes the next tile from the queue and issues its copies; the wait's
+  // barrier publishes its index in `slot`, which thread 0 rewrites only after the iteration's
+  // closing barrier.
+  if (tid == 0) {
+    slot = wl_take(P, WL_TILES);
+    if (slot >= 0) issue_tile(P, slot, tab_buf[0], spix_buf[0], &bar[0]);
+  }
   __syncthreads();
-  uint32_t phase = 0;
-  for (int tile = wl_next_cta(P, WL_TILES, slot); tile >= 0; tile = wl_next_cta(P, WL_TILES, slot), phase ^= 1u) {
-  const TileDev t = P.tiles[tile];
-  const PatchDev pt = P.patches[t.patch];
-  if (tid == 0) atomicAdd(P.counters + 0, (unsigned long long)t.count);
-  if (!stage_tile(P, t, pt, tab, spix, &bar, phase, tid)) {
+  int tile = slot;
+  for (uint32_t it = 0; tile >= 0; ++it) {
+  const int b = NB == 2 ? (int)(it & 1u) : 0;
+  if (NB == 2 && tid == 0) {
+    slot = wl_take(P, WL_TILES);
+    if (slot >= 0) issue_tile(P, slot, tab_buf[b ^ 1], spix_buf[b ^ 1], &bar[b ^ 1]);
+  }
+  if (!wait_tile(P, &bar[b], (it / NB) & 1u, &bar[b ^ (NB - 1)], ((it + 1) / NB) & 1u, NB == 2 && slot >= 0)) {
     if (tid < NACC) P.partials[(size_t)tile * NACC + tid] = __int_as_float(0x7fc00000);
     return;
   }
+  const float* tab = tab_buf[b];
+  const float4* spix = spix_buf[b];
+  const TileDev t = P.tiles[tile];
+  const PatchDev pt = P.patches[t.patch];
+  if (tid == 0) atomicAdd(P.counters + 0, (unsigned long long)t.count);
   const SNConst c = *reinterpret_cast<const SNConst*>(&tab[TB_SNC]);
   float acc[4] = {0.f, 0.f, 0.f, 0.f};
   float dm[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};   // tensor-core M block (HM != 0)
@@ -491,7 +519,18 @@ __global__ void __launch_bounds__(BLOCK) elbo_full_kernel(ProblemDev P) {
     for (int w = 0; w < BLOCK / 32; ++w) v += red[w][tid];
     P.partials[(size_t)tile * NACC + tid] = v;
   }
-  __syncthreads();   // tab, spix and red are refilled for the next tile
+  const int next = slot;
+  __syncthreads();   // this buffer, red and slot are rewritten after this point
+  if constexpr (NB == 1) {
+    if (tid == 0) {
+      slot = wl_take(P, WL_TILES);
+      if (slot >= 0) issue_tile(P, slot, tab_buf[0], spix_buf[0], &bar[0]);
+    }
+    __syncthreads();
+    tile = slot;
+  } else {
+    tile = next;
+  }
   }
 }
 
@@ -502,24 +541,38 @@ __global__ void __launch_bounds__(BLOCK) elbo_full_kernel(ProblemDev P) {
 //           part without the rounding of two large sums.
 template <int PPT>
 __global__ void __launch_bounds__(BLOCK) elbo_value_kernel(ProblemDev P, int diff) {
-  __shared__ __align__(16) float tab[TB_FLOATS];
-  __shared__ __align__(16) float4 spix[BLOCK * PPT];
-  __shared__ __align__(8) uint64_t bar;
+  __shared__ __align__(16) float tab_buf[2][TB_FLOATS];
+  __shared__ __align__(16) float4 spix_buf[2][BLOCK * PPT];
+  __shared__ __align__(8) uint64_t bar[2];
   __shared__ float red[BLOCK / 32];
 
   __shared__ int slot;
   const int tid = threadIdx.x;
-  if (tid == 0) mbar_init(&bar, 1);
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+  }
+  if (tid == 0) {
+    slot = wl_take(P, WL_TILES);
+    if (slot >= 0) issue_tile(P, slot, tab_buf[0], spix_buf[0], &bar[0]);
+  }
   __syncthreads();
-  uint32_t phase = 0;
-  for (int tile = wl_next_cta(P, WL_TILES, slot); tile >= 0; tile = wl_next_cta(P, WL_TILES, slot), phase ^= 1u) {
-  const TileDev t = P.tiles[tile];
-  const PatchDev pt = P.patches[t.patch];
-  if (tid == 0) atomicAdd(P.counters + 1, (unsigned long long)t.count);
-  if (!stage_tile(P, t, pt, tab, spix, &bar, phase, tid)) {
+  int tile = slot;
+  for (uint32_t it = 0; tile >= 0; ++it) {
+  const int b = (int)(it & 1u);
+  if (tid == 0) {
+    slot = wl_take(P, WL_TILES);
+    if (slot >= 0) issue_tile(P, slot, tab_buf[b ^ 1], spix_buf[b ^ 1], &bar[b ^ 1]);
+  }
+  if (!wait_tile(P, &bar[b], (it >> 1) & 1u, &bar[b ^ 1], ((it + 1) >> 1) & 1u, slot >= 0)) {
     if (tid == 0) P.vpartials[tile] = __int_as_float(0x7fc00000);
     return;
   }
+  const float* tab = tab_buf[b];
+  const float4* spix = spix_buf[b];
+  const TileDev t = P.tiles[tile];
+  const PatchDev pt = P.patches[t.patch];
+  if (tid == 0) atomicAdd(P.counters + 1, (unsigned long long)t.count);
   const SNConst c = *reinterpret_cast<const SNConst*>(&tab[TB_SNC]);
   float sum = 0.f;
 #pragma unroll 1
@@ -577,7 +630,9 @@ __global__ void __launch_bounds__(BLOCK) elbo_value_kernel(ProblemDev P, int dif
     for (int w = 0; w < BLOCK / 32; ++w) v += red[w];
     P.vpartials[tile] = v;
   }
-  __syncthreads();   // tab, spix and red are refilled for the next tile
+  const int next = slot;
+  __syncthreads();   // this buffer, red and slot are rewritten after this point
+  tile = next;
   }
 }
 
