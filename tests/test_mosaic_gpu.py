@@ -11,7 +11,7 @@ import torch
 
 from oracle import celeste_oracle as O
 from synth.mosaic import mosaic
-from test_parity_gpu import check_elbo, check_grad, check_hess, compare_optimum, stop_slack
+from test_parity_gpu import check_elbo, check_grad, check_hess, compare_optimum, grad_natural_scale, hess_natural_scale, stop_slack
 
 pytestmark = pytest.mark.gpu
 
@@ -82,8 +82,8 @@ def test_mosaic_sampled_sources_match_oracle(run):
         L, gL, HL = orc.elbo_grad_hess(0, sc.theta0[s], sc.theta0[keep])
         what = f"mosaic s={s} images={sc.truth['n_images'][s]} radius={sc.radius[s]}"
         check_elbo(run["e"][s], L, what)
-        check_grad(run["g"][s], gL, what)
-        check_hess(run["h"][s], HL, what)
+        check_grad(run["g"][s], gL, what, natural=lambda: grad_natural_scale(orc, 0, sc.theta0[s], sc.theta0[keep]))
+        check_hess(run["h"][s], HL, what, natural=lambda: hess_natural_scale(orc, 0, sc.theta0[s], sc.theta0[keep]))
 
 
 def test_mosaic_newton(run):
