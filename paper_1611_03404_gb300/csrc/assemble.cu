@@ -37,154 +37,229 @@ __device__ inline void bvar_inv(int j, int& t, int& v) {
   else v = 6 + (j - 23);
 }
 
-// Source-level quantities shared by all patches (exps of the log-variances, type probabilities).
-struct SourceConst {
-  double a0, a1, aa, la0, la1;   // P(star), P(galaxy), product, their logs
-  double ev[2][10];              // exp of the log-variance parameters (v = 1, 6..9), 0 elsewhere
-};
-
-__device__ inline void source_const_parallel(const double* th, SourceConst& sc, int tid) {
-  if (tid < 10) {
-    const int t = tid / 5, k = tid % 5, v = k == 0 ? 1 : 5 + k;
-    sc.ev[t][v] = exp(th[bvar(t, v)]);
-  } else if (tid < 20) {
-    const int t = (tid - 10) / 5, k = (tid - 10) % 5, v = k == 0 ? 0 : k + 1;   // v = 0, 2..5
-    sc.ev[t][v] = 0.0;
-  } else if (tid == 20) {
-    const double al = th[6];
-    const double e = exp(-fabs(al)), l1p = log1p(e);
-    sc.la1 = al >= 0 ? -l1p : al - l1p;   // log sigmoid(alpha)
-    sc.la0 = sc.la1 - al;                  // log sigmoid(-alpha)
-    const double sg = 1.0 / (1.0 + e);
-    sc.a1 = al >= 0 ? sg : e * sg;
-    sc.a0 = al >= 0 ? e * sg : sg;
-    sc.aa = sc.a0 * sc.a1;
-  }
-}
-
-// One normal-KL term of type t: k = 0 the log flux, k = 1..4 the colours j = k - 1.
-// KL_N(m, v || mu, s2) = (log s2 - log v + (v + (m - mu)^2) / s2 - 1) / 2 with v = exp(log v).
-__device__ inline double kl_normal_term(const double* th, const double* ev, const ProblemDev& P, int t, int k) {
+// One normal-KL term of type t: k = 0 the log flux, k = 1..4 the colours j = k - 1, with v the
+// exp of its log-variance parameter.
+// KL_N(m, v || mu, s2) = (log s2 - log v + (v + (m - mu)^2) / s2 - 1) / 2.
+__device__ inline double kl_normal_term(const double* th, double v, const ProblemDev& P, int t, int k) {
   const double m = k == 0 ? th[bvar(t, 0)] : th[bvar(t, 1 + k)];
   const double lv = k == 0 ? th[bvar(t, 1)] : th[bvar(t, 5 + k)];
-  const double v = k == 0 ? ev[1] : ev[5 + k];
-  const double mu = k == 0 ? P.priors[1] : P.priors[3], s2 = k == 0 ? P.priors[2] : P.priors[4];
+  const double mu = k == 0 ? P.priors[1] : P.priors[3], is2 = k == 0 ? P.inv_var_r : P.inv_var_c;
   const double ls2 = k == 0 ? P.log_var_r : P.log_var_c;
-  return 0.5 * (ls2 - lv + (v + (m - mu) * (m - mu)) / s2 - 1.0);
+  return 0.5 * (ls2 - lv + (v + (m - mu) * (m - mu)) * is2 - 1.0);
 }
 
-// First and second derivative of K_t w.r.t. brightness parameter j of type t.
-__device__ inline void kl_normal_derivs(const double* th, const SourceConst& sc, const ProblemDev& P, int j, int& t,
-                                        double& dK, double& d2K) {
-  int v;
-  bvar_inv(j, t, v);
-  if (v == 0 || (v >= 2 && v < 6)) {
-    const double mu = v == 0 ? P.priors[1] : P.priors[3], s2 = v == 0 ? P.priors[2] : P.priors[4];
-    dK = (th[j] - mu) / s2;
-    d2K = 1.0 / s2;
-  } else {
-    const double s2 = v == 1 ? P.priors[2] : P.priors[4];
-    dK = 0.5 * (sc.ev[t][v] / s2 - 1.0);
-    d2K = 0.5 * sc.ev[t][v] / s2;
+// Per-source quantities shared by the source's patches, for all five bands: the type
+// probabilities, the band moments of the lognormal flux and their derivatives over the type's
+// brightness parameters, and the KL term with its derivatives.  Built once per source by the
+// whole CTA, so a patch's lift needs no transcendental and almost no float64 arithmetic.
+struct SrcTab {
+  double ev[2][10];                       // exp of the log-variance parameters (v = 1, 6..9), 0 elsewhere
+  double a0, a1, aa, la0, la1;            // P(star), P(galaxy), their product, their logs
+  double L1[2][5], L2[2][5];              // E[l_b | t], E[l_b^2 | t]
+  double gc[5][8];                        // per band: a0 L1_0, a1 L1_1, a0 L2_0, a1 L2_1, aa x (L1_0, L1_1, L2_0, L2_1)
+  double kd1[2][5][10], kd2[2][5][10];    // a_t dL1_t / d(brightness v), a_t dL2_t / d(v): the lift's coefficients
+  double klg[NP], klhd[NP], klh6[NP];     // KL gradient; KL Hessian diagonal and row (= column) 6
+  double kterm[10], kl;                   // the ten normal-KL terms; the KL
+  float fL1[2][5], fL2[2][5];
+  float kf1[2][5][10], kf2[2][5][10];     // kd1, kd2
+  float fdL1[2][5][10], fdL2[2][5][10];   // dL1, dL2
+  float fdl1[2][5][10], fdl2[2][5][10];   // d log L1, d log L2
+  float fd2l1[2][5][10], fd2l2[2][5][10]; // diagonal second derivatives of log L1, log L2
+  float fa0, fa1, faa;
+};
+
+// Builds the source table (every thread of the CTA calls it; ends with a barrier).
+__device__ inline void build_src_tab(const ProblemDev& P, const double* __restrict__ th, SrcTab& T, int tid) {
+  // ---- exps of the log-variances (warp 0), type probabilities (warp 1), zeros (warp 2)
+  if (tid < 10) {
+    const int t = tid / 5, k = tid % 5, v = k == 0 ? 1 : 5 + k;
+    T.ev[t][v] = exp(th[bvar(t, v)]);
+  } else if (tid == 32) {
+    const double al = th[6];
+    const double e = exp(-fabs(al)), l1p = log1p(e);
+    T.la1 = al >= 0 ? -l1p : al - l1p;   // log sigmoid(alpha)
+    T.la0 = T.la1 - al;                  // log sigmoid(-alpha)
+    const double sg = 1.0 / (1.0 + e);
+    T.a1 = al >= 0 ? sg : e * sg;
+    T.a0 = al >= 0 ? e * sg : sg;
+    T.aa = T.a0 * T.a1;
+    T.fa0 = (float)T.a0;
+    T.fa1 = (float)T.a1;
+    T.faa = (float)T.aa;
+  } else if (tid >= 64 && tid < 74) {
+    const int k = tid - 64, t = k / 5, kk = k % 5, v = kk == 0 ? 0 : kk + 1;   // v = 0, 2..5
+    T.ev[t][v] = 0.0;
   }
+  __syncthreads();
+  // ---- band moments (warp 0), KL derivative tables (warp 1), normal-KL terms (warp 2)
+  if (tid < 20) {
+    const int t = tid / 10, b = (tid >> 1) % 5, which = tid & 1;
+    double m = th[bvar(t, 0)], v = T.ev[t][1];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const double c = color_coef(b, j);
+      m = fma(c, th[bvar(t, 2 + j)], m);
+      v = fma(c * c, T.ev[t][6 + j], v);
+    }
+    const double L = which ? exp(2.0 * m + 2.0 * v) : exp(m + 0.5 * v);
+    if (which) {
+      T.L2[t][b] = L;
+      T.fL2[t][b] = (float)L;
+    } else {
+      T.L1[t][b] = L;
+      T.fL1[t][b] = (float)L;
+    }
+  } else if (tid >= 32 && tid < 32 + NP) {
+    // dK_t/dth_j and d2K_t/dth_j^2 of the normal-KL sum K_t of j's type (closed forms); row 6
+    // (alpha) is set once K_0 and K_1 are known
+    const int j = tid - 32;
+    double g = 0.0, hd = 0.0, h6 = 0.0;
+    if (j >= 7) {
+      int t, v;
+      bvar_inv(j, t, v);
+      const double is2 = v <= 1 ? P.inv_var_r : P.inv_var_c;
+      double dK, d2K;
+      if (v == 0 || (v >= 2 && v < 6)) {
+        dK = (th[j] - (v == 0 ? P.priors[1] : P.priors[3])) * is2;
+        d2K = is2;
+      } else {
+        d2K = 0.5 * T.ev[t][v] * is2;
+        dK = d2K - 0.5;
+      }
+      const double at = t ? T.a1 : T.a0;
+      g = at * dK;
+      hd = at * d2K;
+      h6 = (t ? T.aa : -T.aa) * dK;
+    }
+    if (j != 6) {
+      T.klg[j] = g;
+      T.klhd[j] = hd;
+      T.klh6[j] = h6;
+    }
+  } else if (tid >= 64 && tid < 74) {
+    const int k = tid - 64, t = k / 5, kk = k % 5;
+    T.kterm[k] = kl_normal_term(th, T.ev[t][kk == 0 ? 1 : 5 + kk], P, t, kk);
+  }
+  __syncthreads();
+  // ---- derivatives of the band moments (items 0..199), the gradient coefficients per band
+  //      (200..239); the last thread adds up the KL and its alpha row
+  for (int i = tid; i < 240; i += blockDim.x) {
+    if (i < 200) {
+      const int t = i / 100, b = (i / 20) % 5, which = (i / 10) & 1, v = i % 10;
+      const bool var = v == 1 || v >= 6;
+      double c = v < 2 ? 1.0 : color_coef(b, (v - 2) & 3);
+      if (v >= 6) c *= c;
+      const double dl = (which ? 2.0 : (var ? 0.5 : 1.0)) * c * (var ? T.ev[t][v] : 1.0);   // d log L
+      const double L = which ? T.L2[t][b] : T.L1[t][b];
+      const double dL = L * dl, kd = (t ? T.a1 : T.a0) * dL;
+      if (which) {
+        T.kd2[t][b][v] = kd;
+        T.kf2[t][b][v] = (float)kd;
+        T.fdL2[t][b][v] = (float)dL;
+        T.fdl2[t][b][v] = (float)dl;
+        T.fd2l2[t][b][v] = var ? (float)dl : 0.f;
+      } else {
+        T.kd1[t][b][v] = kd;
+        T.kf1[t][b][v] = (float)kd;
+        T.fdL1[t][b][v] = (float)dL;
+        T.fdl1[t][b][v] = (float)dl;
+        T.fd2l1[t][b][v] = var ? (float)dl : 0.f;
+      }
+    } else {
+      const int b = (i - 200) >> 3, k = (i - 200) & 7, t = k & 1;
+      const double L = (k & 2) ? T.L2[t][b] : T.L1[t][b];
+      T.gc[b][k] = (k < 4 ? (t ? T.a1 : T.a0) : T.aa) * L;
+    }
+  }
+  if (tid == blockDim.x - 1) {
+    // KL = a1 (log a1 - log Phi) + a0 (log a0 - log(1 - Phi)) + a0 K_0 + a1 K_1
+    double K0 = 0.0, K1 = 0.0;
+    for (int i = 0; i < 5; ++i) {
+      K0 += T.kterm[i];
+      K1 += T.kterm[5 + i];
+    }
+    const double dlg = th[6] - P.logit_phi, dK = K1 - K0, s = 1.0 - 2.0 * T.a1;
+    T.kl = T.a1 * (T.la1 - P.log_phi) + T.a0 * (T.la0 - P.log1m_phi) + T.a0 * K0 + T.a1 * K1;
+    T.klg[6] = T.aa * dlg + T.aa * dK;
+    T.klhd[6] = T.aa * (s * dlg + 1.0) + T.aa * s * dK;
+    T.klh6[6] = 0.0;
+  }
+  __syncthreads();
 }
-
-struct PatchLift {
-  double L1[2], L2[2];                     // E[l_b|i], E[l_b^2|i]
-  double dL1[2][10], dL2[2][10];           // gradients over the type's brightness parameters
-  double d2l1[2][10], d2l2[2][10];         // diagonal second derivatives of log L1, log L2
-  double A[4];                             // WCS linear part
-  int band;
-};
-
-// Float32 copies of the lift quantities that only the Hessian uses.
-struct PatchLiftF {
-  float L1[2], L2[2], dL1[2][10], dL2[2][10], d2l1[2][10], d2l2[2][10], A[4];
-  float a0, a1, aa;
-};
 
 // Per-warp working set of one patch's lift.
 struct WarpLift {
   double sd[ACC_HP];                                  // float64 sums: L, S1, S2
   double gs[NP], gE[NP], nzK[NP], nzL[NP], ghat[NRED];
+  double A[4];                                        // the image's WCS linear part
   double Lsum;
-  PatchLift c;
   float sdf[ACC_HP], sf[NACC - ACC_HP];               // float32 copies / compensated sums: HP, M
   float Hs[NP * NP], H2[NP * NP];                     // accumulated Hessian; per-patch second-order part
-  float Msym[NRED * NRED], nzKf[NP], nzLf[NP];
-  PatchLiftF cf;
+  float Msym[NRED * NRED], nzKf[NP], nzLf[NP], Af[4];
   int nzA[NP], nzB[NP];
 };
 
 // ELBO and gradient are summed and lifted in float64 (the cross-pixel sums of the objective and
 // its gradient); the Hessian, whose per-pixel terms are float32 to begin with, in float32 with
 // compensated cross-tile sums.  On this part a float64 warp instruction costs ~64 cycles of its
-// SM sub-partition, a float32 one a single issue slot, so the split cuts the kernel's float64
-// instructions about fourfold.  A CTA takes one source; each of its four warps lifts every fourth
-// patch of the source into warp-private accumulators (the four sub-partitions' float64 pipes run
-// in parallel), then the warps' sums are added.
+// SM sub-partition and a float32 one a single issue slot, so every transcendental and every
+// derivative of the band moments is formed once per source (SrcTab) and a patch's lift keeps
+// only the sums' float64 work.  A CTA takes one source; each of its four warps lifts every
+// fourth patch of the source into warp-private accumulators (the four sub-partitions' float64
+// pipes run in parallel), then the warps' sums are added.
 __global__ void __launch_bounds__(128) assemble_kernel(ProblemDev P, const double* __restrict__ theta, int full,
                                                        double* elbo, double* grad, double* hess) {
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
   constexpr int NW = 4;                 // warps per CTA
   constexpr int ND = ACC_HP;            // float64 sums: L, S1, S2
   constexpr int NF = NACC - ACC_HP;     // float32 sums: HP, M
+  constexpr int NTRI = NP * (NP + 1) / 2;
   __shared__ WarpLift wl[NW];
+  __shared__ SrcTab T;
   __shared__ float Hs[NP * NP];
   __shared__ double gs[NP];
-  __shared__ SourceConst sc;
-  __shared__ double Lsum, red[16];
+  __shared__ double Lsum;
+  __shared__ unsigned short tri[NTRI];   // packed upper triangle index -> (row << 8) | column
   __shared__ int slot;
   WarpLift& W = wl[warp];
-  PatchLift& c = W.c;
-  PatchLiftF& cf = W.cf;
+  for (int q = tid; q < NTRI; q += nt) {
+    int r = 0, rem = q;
+    while (rem >= NP - r) {
+      rem -= NP - r;
+      ++r;
+    }
+    tri[q] = (unsigned short)((r << 8) | (r + rem));
+  }
   for (int s = wl_next_cta(P, WL_SOURCES, slot); s >= 0; s = wl_next_cta(P, WL_SOURCES, slot)) {
   const double* th = theta + (size_t)s * NP;
   for (int i = lane; i < NP * NP; i += 32) W.Hs[i] = 0.f;
   if (lane < NP) W.gs[lane] = 0.0;
   if (lane == 0) W.Lsum = 0.0;
-  source_const_parallel(th, sc, tid);
-  __syncthreads();
-  if (lane == 0) {
-    cf.a0 = (float)sc.a0;
-    cf.a1 = (float)sc.a1;
-    cf.aa = (float)sc.aa;
-  }
+  build_src_tab(P, th, T, tid);
   for (int p = P.src_patch[s] + warp; p < P.src_patch[s + 1]; p += NW) {
     const PatchDev pt = P.patches[p];
+    const ImageDev& im = P.images[pt.image];
+    const int b = im.band;
     // ---- tile sums (fixed order; float64 for the objective and gradient, compensated float32 for
-    //      the Hessian-only sums) and the band moments
+    //      the Hessian-only sums)
     if (lane < ND) {
       double v = 0.0;
-      for (int t = pt.tile_begin; t < pt.tile_end; ++t) v += (double)P.partials[(size_t)t * NACC + lane];
+      const float* src = P.partials + lane;
+#pragma unroll 4
+      for (int t = pt.tile_begin; t < pt.tile_end; ++t) v += (double)src[(size_t)t * NACC];
       W.sd[lane] = v;
       W.sdf[lane] = (float)v;
     } else if (lane < ND + 4) {
-      const int k = lane - ND, t = k & 1, second = k >> 1;
-      const int band = P.images[pt.image].band;
-      double arow[4];
-      color_row(band, arow);
-      double m = th[bvar(t, 0)], v = sc.ev[t][1];
-      for (int j = 0; j < 4; ++j) {
-        m += arow[j] * th[bvar(t, 2 + j)];
-        v += arow[j] * arow[j] * sc.ev[t][6 + j];
-      }
-      if (second) {
-        c.L2[t] = exp(2.0 * m + 2.0 * v);
-        cf.L2[t] = (float)c.L2[t];
-      } else {
-        c.L1[t] = exp(m + 0.5 * v);
-        cf.L1[t] = (float)c.L1[t];
-      }
-      if (k == 0) c.band = band;
-    } else if (lane < ND + 8) {
-      c.A[lane - ND - 4] = P.images[pt.image].A[lane - ND - 4];
-      cf.A[lane - ND - 4] = (float)c.A[lane - ND - 4];
+      const double a = im.A[lane - ND];
+      W.A[lane - ND] = a;
+      W.Af[lane - ND] = (float)a;
     }
     for (int q = lane; q < NF; q += 32) {
       float v = 0.f, comp = 0.f;
+      const float* src = P.partials + ND + q;
+#pragma unroll 4
       for (int t = pt.tile_begin; t < pt.tile_end; ++t) {
-        const float y = P.partials[(size_t)t * NACC + ND + q] - comp;
+        const float y = src[(size_t)t * NACC] - comp;
         const float u = v + y;
         comp = (u - v) - y;
         v = u;
@@ -192,55 +267,42 @@ __global__ void __launch_bounds__(128) assemble_kernel(ProblemDev P, const doubl
       W.sf[q] = v;
     }
     __syncwarp();
-    // ---- derivatives of the band moments over the type's brightness parameters
-    for (int q = lane; q < 40; q += 32) {
-      const int t = q / 20, which = (q % 20) / 10, v = q % 10;
-      double arow[4];
-      color_row(c.band, arow);
-      double dl, d2;
-      if (v == 0) {
-        dl = which ? 2.0 : 1.0;
-        d2 = 0.0;
-      } else if (v == 1) {
-        dl = (which ? 2.0 : 0.5) * sc.ev[t][1];
-        d2 = dl;
-      } else if (v < 6) {
-        dl = (which ? 2.0 : 1.0) * arow[v - 2];
-        d2 = 0.0;
-      } else {
-        dl = (which ? 2.0 : 0.5) * arow[v - 6] * arow[v - 6] * sc.ev[t][v];
-        d2 = dl;
-      }
-      if (which) {
-        c.dL2[t][v] = c.L2[t] * dl;
-        cf.dL2[t][v] = (float)c.dL2[t][v];
-        cf.d2l2[t][v] = (float)d2;
-      } else {
-        c.dL1[t][v] = c.L1[t] * dl;
-        cf.dL1[t][v] = (float)c.dL1[t][v];
-        cf.d2l1[t][v] = (float)d2;
-      }
-    }
     if (lane == 0) W.Lsum += W.sd[ACC_L];
-    __syncwarp();
     const double* S1 = W.sd + ACC_S1;
     const double* S2 = W.sd + ACC_S2;
     const float* S1h = W.sdf + ACC_S1;
     const float* S2h = W.sdf + ACC_S2;
-    // ---- reduced gradient (float64)
+    // ---- reduced gradient (float64): ghat_a = c0 S1[i0] + c1 S1[i1] + c2 S2[i0] + c3 S2[i1]
     if (lane < NRED) {
-      const double A0 = sc.a0 * c.L1[0], A1 = sc.a1 * c.L1[1], B0 = sc.a0 * c.L2[0], B1 = sc.a1 * c.L2[1];
       const int a = lane;
-      double v;
-      if (a < 2)
-        v = A0 * S1[1 + a] + A1 * S1[4 + a] + B0 * S2[1 + a] + B1 * S2[4 + a];
-      else if (a < 6)
-        v = A1 * S1[4 + a] + B1 * S2[4 + a];
-      else if (a == 6)
-        v = sc.aa * (c.L1[1] * S1[3] - c.L1[0] * S1[0] + c.L2[1] * S2[3] - c.L2[0] * S2[0]);
-      else
-        v = a == 7 ? S1[0] : a == 8 ? S1[3] : a == 9 ? S2[0] : S2[3];
-      W.ghat[a] = v;
+      const double* g = T.gc[b];
+      int i0 = 0, i1 = 3;
+      double c0, c1, c2, c3;
+      if (a < 2) {
+        i0 = 1 + a;
+        i1 = 4 + a;
+        c0 = g[0];
+        c1 = g[1];
+        c2 = g[2];
+        c3 = g[3];
+      } else if (a < 6) {
+        i1 = 4 + a;
+        c0 = 0.0;
+        c1 = g[1];
+        c2 = 0.0;
+        c3 = g[3];
+      } else if (a == 6) {
+        c0 = -g[4];
+        c1 = g[5];
+        c2 = -g[6];
+        c3 = g[7];
+      } else {
+        c0 = a == 7 ? 1.0 : 0.0;
+        c1 = a == 8 ? 1.0 : 0.0;
+        c2 = a == 9 ? 1.0 : 0.0;
+        c3 = a == 10 ? 1.0 : 0.0;
+      }
+      W.ghat[a] = fma(c0, S1[i0], fma(c1, S1[i1], fma(c2, S2[i0], c3 * S2[i1])));
     }
     // Lift from the 11-column reduced basis to the 27 parameters: column j of K has at most two
     // nonzeros (a, k): j < 7 -> (j, 1); brightness parameter v of type t -> (7 + t, a_t dL1_t[v])
@@ -249,24 +311,25 @@ __global__ void __launch_bounds__(128) assemble_kernel(ProblemDev P, const doubl
       const int j = lane;
       if (j < 7) {
         W.nzA[j] = j;
-        W.nzK[j] = 1.0;
         W.nzB[j] = -1;
+        W.nzK[j] = 1.0;
         W.nzL[j] = 0.0;
+        W.nzKf[j] = 1.f;
+        W.nzLf[j] = 0.f;
       } else {
         int t, v;
         bvar_inv(j, t, v);
-        const double at = t ? sc.a1 : sc.a0;
         W.nzA[j] = 7 + t;
-        W.nzK[j] = at * c.dL1[t][v];
         W.nzB[j] = 9 + t;
-        W.nzL[j] = at * c.dL2[t][v];
+        W.nzK[j] = T.kd1[t][b][v];
+        W.nzL[j] = T.kd2[t][b][v];
+        W.nzKf[j] = T.kf1[t][b][v];
+        W.nzLf[j] = T.kf2[t][b][v];
       }
-      W.nzKf[j] = (float)W.nzK[j];
-      W.nzLf[j] = (float)W.nzL[j];
     }
     for (int i = lane; i < NRED * NRED; i += 32) {
-      const int a = i / NRED, b = i % NRED;
-      W.Msym[i] = W.sf[ACC_M - ND + (a <= b ? tri11d(a, b) : tri11d(b, a))];
+      const int a = i / NRED, c = i % NRED;
+      W.Msym[i] = W.sf[ACC_M - ND + (a <= c ? tri11d(a, c) : tri11d(c, a))];
     }
     // second-order part  sum_m w1 d2E[G] + w2 d2E[G^2] (float32), filled block by block:
     // G6 x G6 from the kernel's sums; G6 x alpha; alpha x alpha; G6 x brightness;
@@ -280,46 +343,40 @@ __global__ void __launch_bounds__(128) assemble_kernel(ProblemDev P, const doubl
         rem -= 6 - a;
         ++a;
       }
-      const int b = a + rem;
-      H2[a * NP + b] = H2[b * NP + a] = W.sf[ACC_HP - ND + q];
+      const int c = a + rem;
+      H2[a * NP + c] = H2[c * NP + a] = W.sf[ACC_HP - ND + q];
     }
-    const float S1f[2] = {S1h[0], S1h[3]}, S2f[2] = {S2h[0], S2h[3]};
+    const float S1f0 = S1h[0], S1f1 = S1h[3], S2f0 = S2h[0], S2f1 = S2h[3];
+    const float fa0 = T.fa0, fa1 = T.fa1, faa = T.faa;
+    const float L10 = T.fL1[0][b], L11 = T.fL1[1][b], L20 = T.fL2[0][b], L21 = T.fL2[1][b];
     for (int i = lane; i < 6 + 1 + 120 + 20 + 200; i += 32) {
       if (i < 6) {
         const int a = i;
         const float s1f0 = a < 2 ? S1h[1 + a] : 0.f, s2f0 = a < 2 ? S2h[1 + a] : 0.f;
-        H2[a * NP + 6] = H2[6 * NP + a] =
-            cf.aa * (cf.L1[1] * S1h[4 + a] - cf.L1[0] * s1f0 + cf.L2[1] * S2h[4 + a] - cf.L2[0] * s2f0);
+        H2[a * NP + 6] = H2[6 * NP + a] = faa * (L11 * S1h[4 + a] - L10 * s1f0 + L21 * S2h[4 + a] - L20 * s2f0);
       } else if (i == 6) {
-        H2[6 * NP + 6] = cf.aa * (1.f - 2.f * cf.a1) *
-                         (cf.L1[1] * S1f[1] - cf.L1[0] * S1f[0] + cf.L2[1] * S2f[1] - cf.L2[0] * S2f[0]);
+        H2[6 * NP + 6] = faa * (1.f - 2.f * fa1) * (L11 * S1f1 - L10 * S1f0 + L21 * S2f1 - L20 * S2f0);
       } else if (i < 127) {
         const int k = i - 7, t = k / 60, a = (k % 60) / 10, v = k % 10, j = bvar(t, v);
         const float s1 = t ? S1h[4 + a] : (a < 2 ? S1h[1 + a] : 0.f);
         const float s2 = t ? S2h[4 + a] : (a < 2 ? S2h[1 + a] : 0.f);
-        H2[a * NP + j] = H2[j * NP + a] = (t ? cf.a1 : cf.a0) * (s1 * cf.dL1[t][v] + s2 * cf.dL2[t][v]);
+        H2[a * NP + j] = H2[j * NP + a] = (t ? fa1 : fa0) * (s1 * T.fdL1[t][b][v] + s2 * T.fdL2[t][b][v]);
       } else if (i < 147) {
         const int k = i - 127, t = k / 10, v = k % 10, j = bvar(t, v);
-        H2[6 * NP + j] = H2[j * NP + 6] = (t ? cf.aa : -cf.aa) * (S1f[t] * cf.dL1[t][v] + S2f[t] * cf.dL2[t][v]);
+        H2[6 * NP + j] = H2[j * NP + 6] =
+            (t ? faa : -faa) * ((t ? S1f1 : S1f0) * T.fdL1[t][b][v] + (t ? S2f1 : S2f0) * T.fdL2[t][b][v]);
       } else {
         // d2 L = L (dlogL dlogL^T + diag(d2 log L)) within a type
         const int k = i - 147, t = k / 100, v = (k % 100) / 10, w = k % 10;
-        const float dl1v = cf.dL1[t][v] / cf.L1[t], dl1w = cf.dL1[t][w] / cf.L1[t];
-        const float dl2v = cf.dL2[t][v] / cf.L2[t], dl2w = cf.dL2[t][w] / cf.L2[t];
-        const float d2L1 = cf.L1[t] * (dl1v * dl1w + (v == w ? cf.d2l1[t][v] : 0.f));
-        const float d2L2 = cf.L2[t] * (dl2v * dl2w + (v == w ? cf.d2l2[t][v] : 0.f));
-        H2[bvar(t, v) * NP + bvar(t, w)] = (t ? cf.a1 : cf.a0) * (S1f[t] * d2L1 + S2f[t] * d2L2);
+        const float d2L1 = T.fL1[t][b] * (T.fdl1[t][b][v] * T.fdl1[t][b][w] + (v == w ? T.fd2l1[t][b][v] : 0.f));
+        const float d2L2 = T.fL2[t][b] * (T.fdl2[t][b][v] * T.fdl2[t][b][w] + (v == w ? T.fd2l2[t][b][v] : 0.f));
+        H2[bvar(t, v) * NP + bvar(t, w)] = (t ? fa1 : fa0) * ((t ? S1f1 : S1f0) * d2L1 + (t ? S2f1 : S2f0) * d2L2);
       }
     }
     __syncwarp();
     // H_E = K^T M K + H2, in place over H2 (each pair (r <= col) reads only its own upper entry)
-    for (int q = lane; q < NP * (NP + 1) / 2; q += 32) {
-      int r = 0, rem = q;   // q -> (r, col) with r <= col
-      while (rem >= NP - r) {
-        rem -= NP - r;
-        ++r;
-      }
-      const int col = r + rem;
+    for (int q = lane; q < NTRI; q += 32) {
+      const int rc = tri[q], r = rc >> 8, col = rc & 0xff;
       float v = W.nzKf[r] * W.nzKf[col] * W.Msym[W.nzA[r] * NRED + W.nzA[col]];
       if (W.nzB[col] >= 0) v += W.nzKf[r] * W.nzLf[col] * W.Msym[W.nzA[r] * NRED + W.nzB[col]];
       if (W.nzB[r] >= 0) {
@@ -337,17 +394,18 @@ __global__ void __launch_bounds__(128) assemble_kernel(ProblemDev P, const doubl
     __syncwarp();
     // map mu -> u: d/du_b = sum_a A[a][b] d/dmu_a
     const float* HE = H2;
+    const float* Af = W.Af;
     for (int i = lane; i < NP * NP; i += 32) {
       const int r = i / NP, q = i % NP;
       float v;
       if (r < 2 && q < 2) {
         v = 0.f;
         for (int a = 0; a < 2; ++a)
-          for (int b = 0; b < 2; ++b) v += cf.A[a * 2 + r] * cf.A[b * 2 + q] * HE[a * NP + b];
+          for (int c = 0; c < 2; ++c) v += Af[a * 2 + r] * Af[c * 2 + q] * HE[a * NP + c];
       } else if (r < 2) {
-        v = cf.A[0 * 2 + r] * HE[0 * NP + q] + cf.A[1 * 2 + r] * HE[1 * NP + q];
+        v = Af[0 * 2 + r] * HE[0 * NP + q] + Af[1 * 2 + r] * HE[1 * NP + q];
       } else if (q < 2) {
-        v = cf.A[0 * 2 + q] * HE[r * NP + 0] + cf.A[1 * 2 + q] * HE[r * NP + 1];
+        v = Af[0 * 2 + q] * HE[r * NP + 0] + Af[1 * 2 + q] * HE[r * NP + 1];
       } else {
         v = HE[i];
       }
@@ -355,7 +413,7 @@ __global__ void __launch_bounds__(128) assemble_kernel(ProblemDev P, const doubl
     }
     if (lane < NP) {
       const int j = lane;
-      W.gs[j] += j < 2 ? c.A[0 * 2 + j] * W.gE[0] + c.A[1 * 2 + j] * W.gE[1] : W.gE[j];
+      W.gs[j] += j < 2 ? W.A[0 * 2 + j] * W.gE[0] + W.A[1 * 2 + j] * W.gE[1] : W.gE[j];
     }
     __syncwarp();
   }
@@ -365,59 +423,17 @@ __global__ void __launch_bounds__(128) assemble_kernel(ProblemDev P, const doubl
   if (tid < NP) gs[tid] = (wl[0].gs[tid] + wl[1].gs[tid]) + (wl[2].gs[tid] + wl[3].gs[tid]);
   if (tid == 0) Lsum = (wl[0].Lsum + wl[1].Lsum) + (wl[2].Lsum + wl[3].Lsum);
   __syncthreads();
-
-  // ---- KL = a1 (log a1 - log Phi) + a0 (log a0 - log(1 - Phi)) + a0 K_0 + a1 K_1 and its
-  //      derivatives (closed forms from the source constants; no further transcendentals)
-  if (tid < 10) red[tid] = kl_normal_term(th, sc.ev[tid / 5], P, tid / 5, tid % 5);
-  __syncthreads();
-  if (tid == 0) {
-    double K0 = 0.0, K1 = 0.0;
-    for (int i = 0; i < 5; ++i) {
-      K0 += red[i];
-      K1 += red[5 + i];
-    }
-    red[10] = K0;
-    red[11] = K1;
-    const double kl = sc.a1 * (sc.la1 - P.log_phi) + sc.a0 * (sc.la0 - P.log1m_phi) + sc.a0 * K0 + sc.a1 * K1;
-    if (elbo) elbo[s] = Lsum - kl;
-  }
-  __syncthreads();
+  // ---- ELBO = pixel sum - KL, and the KL's derivatives (closed forms from the source table)
+  if (elbo && tid == 0) elbo[s] = Lsum - T.kl;
   if (full) {
-    const double K0 = red[10], K1 = red[11];
-    const double ga = sc.aa * (th[6] - P.logit_phi) + sc.aa * (K1 - K0);
     if (hess) {
       for (int i = tid; i < NP * NP; i += nt) {
         const int r = i / NP, q = i % NP;
-        double h = 0.0;
-        if (r == 6 && q == 6) {
-          h = sc.aa * ((1.0 - 2.0 * sc.a1) * (th[6] - P.logit_phi) + 1.0) + sc.aa * (1.0 - 2.0 * sc.a1) * (K1 - K0);
-        } else if ((r == 6 && q >= 7) || (q == 6 && r >= 7)) {
-          int t;
-          double dK, d2K;
-          kl_normal_derivs(th, sc, P, r == 6 ? q : r, t, dK, d2K);
-          h = (t ? sc.aa : -sc.aa) * dK;
-        } else if (r == q && r >= 7) {
-          int t;
-          double dK, d2K;
-          kl_normal_derivs(th, sc, P, r, t, dK, d2K);
-          h = (t ? sc.a1 : sc.a0) * d2K;
-        }
+        const double h = (r == q ? T.klhd[r] : 0.0) + (r == 6 ? T.klh6[q] : (q == 6 ? T.klh6[r] : 0.0));
         hess[(size_t)s * NP * NP + i] = (double)Hs[i] - h;
       }
     }
-    if (grad && tid < NP) {
-      const int j = tid;
-      double gk = 0.0;
-      if (j == 6) {
-        gk = ga;
-      } else if (j >= 7) {
-        int t;
-        double dK, d2K;
-        kl_normal_derivs(th, sc, P, j, t, dK, d2K);
-        gk = (t ? sc.a1 : sc.a0) * dK;
-      }
-      grad[(size_t)s * NP + j] = gs[j] - gk;
-    }
+    if (grad && tid < NP) grad[(size_t)s * NP + tid] = gs[tid] - T.klg[tid];
   }
   __syncthreads();   // shared state is reused by the next source
   }
@@ -444,9 +460,7 @@ __global__ void assemble_value_kernel(ProblemDev P, const double* __restrict__ t
     double klp;
     if (k < 10) {
       const int t = k / 5, kk = k % 5;
-      double ev[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-      const int vi = kk == 0 ? 1 : 5 + kk;
-      ev[vi] = exp(th[bvar(t, vi)]);
+      const double ev = exp(th[bvar(t, kk == 0 ? 1 : 5 + kk)]);
       klp = (t ? a1 : a0) * kl_normal_term(th, ev, P, t, kk);
     } else {
       const double l1p = log1p(e);

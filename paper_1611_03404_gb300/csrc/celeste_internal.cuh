@@ -107,6 +107,7 @@ struct ProblemDev {
   int S, n_patches, n_tiles, tile_pixels, n_sm, hmode;
   double priors[5];
   double log_var_r, log_var_c, log_phi, log1m_phi, logit_phi;   // logs of the priors (host-computed)
+  double inv_var_r, inv_var_c;   // reciprocals of the prior variances (host-computed)
   float nu[NMIX], tau[NMIX];     // exp (0..5) then deV (6..13)
 };
 
@@ -197,9 +198,13 @@ __device__ inline PsfComp load_psf(const float* psf_patch, int k) {
 
 // Brightness moments of a lognormal flux in band b for type i: log l_b ~ N(m, v),
 // m = r1 + a_b.c1, v = exp(rho) + (a_b^2).exp(gam); E[l] = exp(m + v/2), E[l^2] = exp(2m + 2v).
+// a_bj in {-1, 0, 1}: u = r - c1 - c2, g = r - c2, r, i = r + c3, z = r + c3 + c4 (log fluxes; no
+// table, so a run-time band indexes no local memory).
+__host__ __device__ inline double color_coef(int band, int j) {
+  return (band < 2 && j >= band && j < 2) ? -1.0 : ((band > 2 && j >= 2 && j < band) ? 1.0 : 0.0);
+}
 __host__ __device__ inline void color_row(int band, double a[4]) {
-  const double M[5][4] = {{-1, -1, 0, 0}, {0, -1, 0, 0}, {0, 0, 0, 0}, {0, 0, 1, 0}, {0, 0, 1, 1}};
-  for (int j = 0; j < 4; ++j) a[j] = M[band][j];
+  for (int j = 0; j < 4; ++j) a[j] = color_coef(band, j);
 }
 __host__ __device__ inline void lognormal_moments(const double* th, int type, int band, double& L1, double& L2,
                                                   double* var_log = nullptr) {

@@ -395,6 +395,8 @@ extern "C" int celeste_problem_bind(celeste_problem* p, void* workspace, size_t 
   D.log_phi = std::log(p->priors[0]);
   D.log1m_phi = std::log1p(-p->priors[0]);
   D.logit_phi = D.log_phi - D.log1m_phi;
+  D.inv_var_r = 1.0 / p->priors[2];
+  D.inv_var_c = 1.0 / p->priors[4];
   std::memcpy(D.nu, p->nu, sizeof(D.nu));
   std::memcpy(D.tau, p->tau, sizeof(D.tau));
   p->base = base;
