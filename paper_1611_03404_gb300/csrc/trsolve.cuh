@@ -130,7 +130,7 @@ __device__ inline bool tr_eval_lane(TrSmem& S, int lane, double lam, double& pn,
     S.PR[i][lane] = r;
     S.PY[i][lane] = w;
   }
-  if (!pd) return false;
+  // (finished whatever the pivots' signs, so the warp stays converged; the caller masks by pd)
   double y = S.PY[TR_N - 1][lane] * S.PR[TR_N - 1][lane];
   S.PY[TR_N - 1][lane] = y;
   double p2 = y * y;
@@ -146,7 +146,7 @@ __device__ inline bool tr_eval_lane(TrSmem& S, int lane, double lam, double& pn,
   }
   pn = sqrt(p2);
   qn2 = q2;
-  return true;
+  return pd;
 }
 
 __device__ inline double tr_warp_max(double v) {
@@ -174,7 +174,8 @@ __device__ inline void tr_take_y(TrSmem& S, int lane, int src) {
 // from the left stays left).  Non-positive-definite points lie left of -lambda_min <= lambda*.
 // On return S.y holds the step in the T basis; returns 1 for the hard case (the bracket closes
 // on the pole with phi > 0 to its right), in which S.y is not set.
-__device__ inline int tr_lambda_parallel(TrSmem& S, int lane, double lo, double hi, double delta, bool try_zero) {
+__device__ inline int tr_lambda_parallel(TrSmem& S, int lane, double lo, double hi, double delta, bool try_zero,
+                                         double spec) {
   constexpr double TOL = 1e-10;
   double L = lo, H = hi;            // L <= lambda* <= H
   bool have_h = false;              // S.y holds the point H (phi(H) >= 0)
@@ -191,10 +192,9 @@ __device__ inline int tr_lambda_parallel(TrSmem& S, int lane, double lo, double 
     const double span = H - L;
     if (pass > 0 && lamN > L && lamN < H)
       lam = lane == 0 ? lamN : (lane < 16 ? lamN + (H - lamN) * nfac : lamN - (lamN - L) * nfac);
-    else if (lane == 0)
-      lam = (pass == 0 && try_zero) ? 0.0 : L + 0.5 * span;
     else
-      lam = L + span * gfac;
+      lam = lane == 0 ? ((pass == 0 && try_zero) ? 0.0 : L + 0.5 * span) : L + span * gfac;
+    __syncwarp();   // (lane choices are selects; the evaluation below must issue once, converged)
     double pn = 0.0, qn2 = 0.0;
     const bool pd = tr_eval_lane(S, lane, lam, pn, qn2);
     // ---- interior solution
@@ -235,8 +235,10 @@ __device__ inline int tr_lambda_parallel(TrSmem& S, int lane, double lo, double 
       const double phi = 1.0 / pnb - 1.0 / delta;
       lamN = lbest - phi / (qb / (pnb * pnb * pnb));
     }
-    // ---- bracket closed: no float64 multiplier left between L and H
-    if (H - L <= 4.0 * DBL_EPSILON * fmax(fabs(H), 1e-300)) {
+    // ---- bracket closed: no multiplier left between L and H that T + lambda I could tell apart
+    //      (its entries carry rounding of a few ulps of the spectrum's scale `spec`, so a bracket
+    //      that narrow around a root next to the pole is resolved as far as float64 allows)
+    if (H - L <= 4.0 * DBL_EPSILON * fmax(fabs(H), spec)) {
       if (!have_h) return 1;
       // phi(H) >= 0 with H next to L: the root, unless |y| jumps across delta within the last
       // ulps of lambda -- the pole, where g's component along the eigenvector of lambda_min is
@@ -410,20 +412,21 @@ __device__ inline bool tr_solve_warp(TrSmem& S, const double* __restrict__ Bsrc,
 
   // ---- multiplier: lambda* >= max(0, -lambda_min) >= max(0, -min_i d_i); at
   //      hi = |g| / delta - a (a <= lambda_min, Gershgorin) |p(hi)| <= |g| / (hi + lambda_min) <= delta
-  double a = INFINITY, dmin = INFINITY, dmax = 0.0, omax = 0.0;
-  for (int i = 0; i < n; ++i) {
-    const double r = fabs(S.off[i]) + (i + 1 < n ? fabs(S.off[i + 1]) : 0.0);
-    a = fmin(a, S.d[i] - r);
-    dmin = fmin(dmin, S.d[i]);
-    dmax = fmax(dmax, fabs(S.d[i]));
-    omax = fmax(omax, fabs(S.off[i]));
-  }
-  const double scale = fmax(1.0, dmax + 2.0 * omax);
+  // (lane-parallel, with selects: a lane-divergent branch here can leave the warp split through
+  // the multiplier search)
+  const int li = row ? lane : 0, ln = lane + 1 < n ? lane + 1 : 0;
+  const double di = S.d[li], oi = fabs(S.off[li]), on = lane + 1 < n ? fabs(S.off[ln]) : 0.0;
+  double a = tr_warp_min(row ? di - (oi + on) : INFINITY);
+  const double dmin = tr_warp_min(row ? di : INFINITY);
+  const double dmax = tr_warp_max(row ? fabs(di) : 0.0);
+  const double omax = tr_warp_max(row ? oi : 0.0);
+  const double spec = dmax + 2.0 * omax;   // >= |eigenvalues of T| (Gershgorin)
+  const double scale = fmax(1.0, spec);
   const double lo = fmax(0.0, -dmin);
   const double hi = fmax(lo, gnorm / delta - a) * (1.0 + 1e-12) + 1e-300;
   if (lane == 0) S.flag[2] = 0;
   __syncwarp();
-  if (tr_lambda_parallel(S, lane, lo, hi, delta, lo == 0.0)) {
+  if (tr_lambda_parallel(S, lane, lo, hi, delta, lo == 0.0, spec)) {
     // hard case: g has (almost) no component along the eigenvector z of lambda_min.  lambda_min
     // from a float32 Sturm bracket refined by inverse iteration (lane 0), then
     // p = y(-lambda_min) + tau z with |p| = delta.
