@@ -1,0 +1,182 @@
+"""FP64 CPU oracle for the joint objective over overlapping sources.  TEST INFRASTRUCTURE ONLY.
+
+Only the test suite, the smoke check and the benchmark's CPU-baseline leg may import this
+module.  It shares no code with the CUDA path.
+
+The paper's concluding section names, as the next step after optimising each light source with
+its neighbours held fixed, finding a stationary point of the objective over all light sources
+jointly.  That objective is the ELBO of all the pixels the sources' windows cover, every pixel
+counted once:
+
+    J(theta) = sum_n sum_{m in U_n} l(x_m, E_m, V_m) - sum_s KL_s(theta_s),
+    U_n = union over s of W_{s,n},
+    E_m = sky_n + iota_n sum_{s: m in W_{s,n}} E[G_s](m),
+    V_m = iota_n^2 sum_{s: m in W_{s,n}} Var[G_s](m),
+
+with W_{s,n} source s's window in image n (the per-source objective's pixel set) and each
+source's light counted on the pixels of its own window.  Then dJ/dtheta_s is the gradient of the
+per-source objective whose neighbours are counted on their own windows only ("clipped"), the
+diagonal Hessian blocks are that objective's Hessian, and the cross block of two sources is
+
+    d2J / dtheta_s dtheta_t = sum_{m in W_s cap W_t} l_EE dE/ds dE/dt^T
+                              + l_EV (dE/ds dV/dt^T + dV/ds dE/dt^T)
+
+(E and V are sums over sources, so their mixed second derivatives vanish, and l_VV = 0).
+Everything here is plain float64 PyTorch; derivatives by automatic differentiation.
+"""
+import numpy as np
+import torch
+
+from .celeste_oracle import kl_source, pixel_term, source_moments
+
+torch.set_default_dtype(torch.float64)
+
+
+def _image_windows(orc):
+    """Per image n: list of (source, x0, x1, y0, y1) inclusive windows."""
+    by_image = {}
+    for s, lst in enumerate(orc.rects):
+        for (n, x0, x1, y0, y1) in lst:
+            by_image.setdefault(n, []).append((s, x0, x1, y0, y1))
+    return by_image
+
+
+def _union_pixels(orc, n, wins):
+    """Union of the windows of image n: pixel coordinates, counts, log-factorials, and per window
+    the boolean mask of its pixels within the union list."""
+    im = orc.scene.images[n]
+    cover = np.zeros((im.H, im.W), bool)
+    for (_, x0, x1, y0, y1) in wins:
+        cover[y0:y1 + 1, x0:x1 + 1] = True
+    ys, xs = np.nonzero(cover)
+    px = torch.as_tensor(xs.astype(np.float64))
+    py = torch.as_tensor(ys.astype(np.float64))
+    x = torch.as_tensor(im.pixels[ys, xs].astype(np.float64))
+    masks = [torch.as_tensor((xs >= x0) & (xs <= x1) & (ys >= y0) & (ys <= y1)) for (_, x0, x1, y0, y1) in wins]
+    return im, px, py, x, torch.lgamma(x + 1.0), masks
+
+
+def joint_fn(orc):
+    """theta [S, 27] -> J(theta) (a pure function, for value and autodiff)."""
+    data = []
+    for n, wins in sorted(_image_windows(orc).items()):
+        im, px, py, x, lgx, masks = _union_pixels(orc, n, wins)
+        data.append((im, px, py, x, lgx, [(w[0], mk, orc.psf_for(w[0], n)) for w, mk in zip(wins, masks)]))
+    priors, mix, S = orc.priors, orc.mix, orc.scene.n_sources
+
+    def J(theta):
+        total = torch.zeros(())
+        for s in range(S):
+            total = total - kl_source(theta[s], priors)
+        for (im, px, py, x, lgx, srcs) in data:
+            EGs = torch.zeros_like(px)
+            VGs = torch.zeros_like(px)
+            for (s, mk, psf) in srcs:
+                EG, EG2 = source_moments(theta[s], im, px, py, psf, mix)
+                EGs = EGs + torch.where(mk, EG, torch.zeros_like(EG))
+                VGs = VGs + torch.where(mk, EG2 - EG * EG, torch.zeros_like(EG))
+            E = im.sky + im.iota * EGs
+            V = im.iota ** 2 * VGs
+            total = total + pixel_term(x, E, V, lgx).sum()
+        return total
+    return J
+
+
+def joint_value_grad_hess(orc, theta):
+    """(J, dJ/dtheta [S, 27], d2J/dtheta2 [S, 27, S, 27]) at theta [S, 27]."""
+    J = joint_fn(orc)
+    th = torch.as_tensor(theta, dtype=torch.float64).clone()
+    with torch.no_grad():
+        val = float(J(th))
+    g = torch.func.grad(J)(th)
+    H = torch.func.hessian(J)(th)
+    return val, g.numpy(), H.numpy()
+
+
+def clipped_elbo_fn(orc, s, nbr_theta):
+    """theta_s -> the per-source objective of s with each neighbour's light counted on the pixels
+    of its own window only (the neighbours at nbr_theta)."""
+    data = []
+    for (n, x0, x1, y0, y1) in orc.rects[s]:
+        im = orc.scene.images[n]
+        ys, xs = torch.meshgrid(torch.arange(y0, y1 + 1, dtype=torch.float64),
+                                torch.arange(x0, x1 + 1, dtype=torch.float64), indexing="ij")
+        px, py = xs.reshape(-1), ys.reshape(-1)
+        x = torch.as_tensor(im.pixels[y0:y1 + 1, x0:x1 + 1].astype(np.float64)).reshape(-1)
+        bE = torch.zeros_like(px)
+        bV = torch.zeros_like(px)
+        with torch.no_grad():
+            for t in orc.nbr[s][n]:
+                tx0, tx1, ty0, ty1 = [r for r in orc.rects[t] if r[0] == n][0][1:]
+                inside = (px >= tx0) & (px <= tx1) & (py >= ty0) & (py <= ty1)
+                EG, EG2 = source_moments(torch.as_tensor(nbr_theta[t]), im, px, py, orc.psf_for(t, n), orc.mix)
+                bE += torch.where(inside, EG, torch.zeros_like(EG))
+                bV += torch.where(inside, EG2 - EG * EG, torch.zeros_like(EG))
+        data.append((im, px, py, x, torch.lgamma(x + 1.0), bE, bV, orc.psf_for(s, n)))
+    priors, mix = orc.priors, orc.mix
+
+    def f(theta):
+        total = -kl_source(theta, priors)
+        for (im, px, py, x, lgx, bE, bV, psf) in data:
+            EG, EG2 = source_moments(theta, im, px, py, psf, mix)
+            E = im.sky + im.iota * (bE + EG)
+            V = im.iota ** 2 * (bV + EG2 - EG * EG)
+            total = total + pixel_term(x, E, V, lgx).sum()
+        return total
+    return f
+
+
+def cross_block_formula(orc, theta, s, t):
+    """d2J/dtheta_s dtheta_t from per-pixel Jacobians (the closed form in the module docstring):
+    sum over the pixels of W_s cap W_t of l_EE dE_s dE_t^T + l_EV (dE_s dV_t^T + dV_s dE_t^T)."""
+    theta = np.asarray(theta, np.float64)
+    out = np.zeros((27, 27))
+    wins = _image_windows(orc)
+    for n, ws in wins.items():
+        ws_s = [w for w in ws if w[0] == s]
+        ws_t = [w for w in ws if w[0] == t]
+        if not ws_s or not ws_t:
+            continue
+        (_, a0, a1, b0, b1), (_, c0, c1, d0, d1) = ws_s[0], ws_t[0]
+        x0, x1, y0, y1 = max(a0, c0), min(a1, c1), max(b0, d0), min(b1, d1)
+        if x0 > x1 or y0 > y1:
+            continue
+        im = orc.scene.images[n]
+        ys, xs = np.mgrid[y0:y1 + 1, x0:x1 + 1]
+        xs, ys = xs.ravel(), ys.ravel()
+        px = torch.as_tensor(xs.astype(np.float64))
+        py = torch.as_tensor(ys.astype(np.float64))
+        x = torch.as_tensor(im.pixels[ys, xs].astype(np.float64))
+        # rate mean and variance from every source whose window holds the pixel
+        E = torch.full_like(px, float(im.sky))
+        V = torch.zeros_like(px)
+        for (u, e0, e1, f0, f1) in ws:
+            inside = torch.as_tensor((xs >= e0) & (xs <= e1) & (ys >= f0) & (ys <= f1))
+            EG, EG2 = source_moments(torch.as_tensor(theta[u]), im, px, py, orc.psf_for(u, n), orc.mix)
+            E = E + im.iota * torch.where(inside, EG, torch.zeros_like(EG))
+            V = V + im.iota ** 2 * torch.where(inside, EG2 - EG * EG, torch.zeros_like(EG))
+        l_EE = -x / E ** 2 - 3.0 * x * V / E ** 4
+        l_EV = x / E ** 3
+
+        def EV(th, u):
+            EG, EG2 = source_moments(th, im, px, py, orc.psf_for(u, n), orc.mix)
+            return torch.stack([im.iota * EG, im.iota ** 2 * (EG2 - EG * EG)])
+
+        Js = torch.func.jacrev(lambda th: EV(th, s))(torch.as_tensor(theta[s]))   # [2, npix, 27]
+        Jt = torch.func.jacrev(lambda th: EV(th, t))(torch.as_tensor(theta[t]))
+        dEs, dVs, dEt, dVt = Js[0], Js[1], Jt[0], Jt[1]
+        out += (torch.einsum("m,mi,mj->ij", l_EE, dEs, dEt)
+                + torch.einsum("m,mi,mj->ij", l_EV, dEs, dVt)
+                + torch.einsum("m,mi,mj->ij", l_EV, dVs, dEt)).numpy()
+    return out
+
+
+def overlapping_pairs(orc):
+    """Sorted list of source pairs (s, t), s < t, whose windows overlap in some image."""
+    pairs = set()
+    for s, d in enumerate(orc.nbr):
+        for n, ts in d.items():
+            for t in ts:
+                if s < t:
+                    pairs.add((s, t))
+    return sorted(pairs)

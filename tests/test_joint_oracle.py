@@ -1,0 +1,110 @@
+"""Pins of the joint-objective oracle (CPU).
+
+The joint objective (every covered pixel counted once, each source's light on its own window)
+is checked against: central finite differences of its value; its reduction to the per-source
+objectives when no windows overlap; the per-source objective with clipped neighbours for its
+gradient and diagonal Hessian blocks; the closed form of the cross blocks from per-pixel
+Jacobians; and, for a neighbour whose window covers the target's, the per-source objective of
+the main oracle (clipping then changes nothing)."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import celeste_oracle as O
+from oracle import joint_oracle as JO
+
+
+@pytest.fixture(scope="module")
+def scene():
+    return synth.tiny(seed=11, n_sources=3, n_images=3)
+
+
+@pytest.fixture(scope="module")
+def joint(scene):
+    orc = O.Oracle(scene)
+    rng = np.random.default_rng(5)
+    theta = scene.theta0 + 0.05 * rng.standard_normal(scene.theta0.shape)
+    val, g, H = JO.joint_value_grad_hess(orc, theta)
+    return orc, theta, val, g, H
+
+
+def test_scene_has_overlaps(joint):
+    orc = joint[0]
+    assert JO.overlapping_pairs(orc) == [(0, 1), (0, 2), (1, 2)]
+
+
+def test_gradient_matches_finite_differences(joint):
+    orc, theta, val, g, _ = joint
+    J = JO.joint_fn(orc)
+    rng = np.random.default_rng(1)
+    for _ in range(8):
+        s, j = int(rng.integers(0, theta.shape[0])), int(rng.integers(0, 27))
+        h = 1e-5
+        tp, tm = theta.copy(), theta.copy()
+        tp[s, j] += h
+        tm[s, j] -= h
+        with torch.no_grad():
+            fd = (float(J(torch.as_tensor(tp))) - float(J(torch.as_tensor(tm)))) / (2 * h)
+        assert abs(fd - g[s, j]) <= 1e-6 * max(1.0, abs(g[s, j])) + 1e-9 * abs(val), (s, j, fd, g[s, j])
+
+
+def test_hessian_symmetric(joint):
+    H = joint[4]
+    S = H.shape[0]
+    M = H.reshape(S * 27, S * 27)
+    assert np.abs(M - M.T).max() <= 1e-9 * np.abs(M).max()
+
+
+def test_diagonal_blocks_are_the_clipped_per_source_objective(joint):
+    orc, theta, _, g, H = joint
+    for s in range(theta.shape[0]):
+        f = JO.clipped_elbo_fn(orc, s, theta)
+        th = torch.as_tensor(theta[s]).clone()
+        gs = torch.func.grad(f)(th).numpy()
+        Hs = torch.func.hessian(f)(th).numpy()
+        assert np.allclose(gs, g[s], rtol=1e-10, atol=1e-9 * np.abs(g[s]).max())
+        assert np.allclose(Hs, H[s, :, s, :], rtol=1e-10, atol=1e-9 * np.abs(Hs).max())
+
+
+def test_cross_blocks_match_the_closed_form(joint):
+    orc, theta, _, _, H = joint
+    for (s, t) in JO.overlapping_pairs(orc):
+        C = JO.cross_block_formula(orc, theta, s, t)
+        ref = H[s, :, t, :]
+        scale = np.abs(ref).max()
+        assert scale > 0
+        assert np.abs(C - ref).max() <= 1e-9 * scale, (s, t, np.abs(C - ref).max(), scale)
+        assert np.abs(H[t, :, s, :] - ref.T).max() <= 1e-9 * scale
+
+
+def test_disjoint_windows_reduce_to_per_source_objectives(scene):
+    # shrink the windows until none overlaps: J is then the sum of the per-source objectives
+    # (no neighbours anywhere) and every cross block vanishes
+    sc = synth.tiny(seed=11, n_sources=3, n_images=3)
+    sc.radius = np.full_like(sc.radius, 1)
+    orc = O.Oracle(sc)
+    assert JO.overlapping_pairs(orc) == []
+    val, g, H = JO.joint_value_grad_hess(orc, sc.theta0)
+    per = sum(orc.elbo(s, sc.theta0[s], sc.theta0) for s in range(sc.n_sources))
+    assert abs(val - per) <= 1e-10 * abs(per)
+    for s in range(sc.n_sources):
+        for t in range(sc.n_sources):
+            if s != t:
+                assert np.abs(H[s, :, t, :]).max() == 0.0
+
+
+def test_covering_neighbour_clips_nothing():
+    # two sources; the second's window covers the first's in every image, so the first's
+    # clipped objective is the main oracle's per-source objective
+    sc = synth.tiny(seed=11, n_sources=2, n_images=2)
+    sc.radius = np.array([3, 40], dtype=sc.radius.dtype)
+    orc = O.Oracle(sc)
+    for (n, x0, x1, y0, y1) in orc.rects[0]:
+        big = [r for r in orc.rects[1] if r[0] == n][0]
+        assert big[1] <= x0 and x1 <= big[2] and big[3] <= y0 and y1 <= big[4]
+    f = JO.clipped_elbo_fn(orc, 0, sc.theta0)
+    with torch.no_grad():
+        v = float(f(torch.as_tensor(sc.theta0[0])))
+    ref = orc.elbo(0, sc.theta0[0], sc.theta0)
+    assert abs(v - ref) <= 1e-12 * abs(ref)
