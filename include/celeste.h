@@ -156,6 +156,46 @@ int celeste_problem_bind(celeste_problem* p, void* workspace, size_t bytes, cele
  * Must run after bind and again whenever the neighbours' parameters change. */
 int celeste_render_background(celeste_problem* p, const double* nbr_theta, celeste_stream_t stream);
 
+/* As celeste_render_background, with the neighbours' extent chosen by `mode`:
+ *   CELESTE_NBR_FULL (0): each neighbour's full light on every pixel of the target's patch (the
+ *     per-source objective, neighbours held fixed);
+ *   CELESTE_NBR_WINDOW (1): each neighbour's light only on the pixels of its own window, as in
+ *     the objective over all sources jointly (paper, concluding section: a stationary point of
+ *     the objective over all light sources at once).  Rendered at nbr_theta = theta, the
+ *     per-source gradient and Hessian of celeste_elbo_batch are then the joint objective's
+ *     gradient and diagonal Hessian blocks.
+ * Errors: CELESTE_ERR_INVALID_ARG for another mode or a NULL nbr_theta. */
+int celeste_render_background_mode(celeste_problem* p, const double* nbr_theta, int mode, celeste_stream_t stream);
+
+enum { CELESTE_NBR_FULL = 0, CELESTE_NBR_WINDOW = 1 };
+
+/* Joint objective over all sources (every pixel of the union of the windows counted once, each
+ * source's light on its own window):
+ *   J(theta) = sum_n sum_{m in U_n} l(x_m, E_m, V_m) - sum_s KL_s,
+ *   E_m = sky + iota sum_{s: m in W_s} E[G_s](m),  V_m = iota^2 sum_{s: m in W_s} Var[G_s](m).
+ * Its cross-source Hessian block of two sources whose windows overlap is
+ *   d2J / dtheta_s dtheta_t = sum_{m in W_s cap W_t} l_EE dE/ds dE/dt^T + l_EV (dE/ds dV/dt^T + dV/ds dE/dt^T).
+ *
+ * celeste_joint_pairs: the pairs (s, t), s < t, of sources whose windows overlap in some image,
+ * in the order celeste_joint_cross_hessian writes their blocks.
+ *   pairs:    host int32 [capacity][2], or NULL to query the count only;
+ *   capacity: number of pairs `pairs` can hold; n_pairs: host, receives the number of pairs.
+ * The pair list and its overlap tiles are built on the host and uploaded on the first call
+ * (device memory owned by the problem).  Errors: CELESTE_ERR_STATE before bind;
+ * CELESTE_ERR_INVALID_ARG when capacity is too small or n_pairs is NULL. */
+int celeste_joint_pairs(celeste_problem* p, int32_t* pairs, int64_t capacity, int64_t* n_pairs);
+
+/* Cross-source Hessian blocks of J at theta, one per pair of celeste_joint_pairs:
+ *   theta:  device float64 [S][27], the parameters of every source;
+ *   blocks: device float64 [n_pairs][27][27]; block k row i, column j = d2J/dtheta_{s,i} dtheta_{t,j}
+ *           for pair k = (s, t).
+ * The background must have been rendered with CELESTE_NBR_WINDOW at nbr_theta = theta (the pixel
+ * rates E_m, V_m include every source's light); the call checks the mode, not the parameters.
+ * Per-pixel Jacobian rows of both sources in float32, per-tile sums in float32, the cross-tile
+ * sum and the lift to the 27 parameters in float64.  Asynchronous on `stream`.
+ * Errors: CELESTE_ERR_STATE when the background was not rendered in window mode. */
+int celeste_joint_cross_hessian(celeste_problem* p, const double* theta, double* blocks, celeste_stream_t stream);
+
 /* ELBO of every source's subproblem and, on request, its exact gradient and dense Hessian
  * w.r.t. the 27 free parameters (Eq. (1)-(2) restricted to the source's patches, minus its KL).
  *   theta: device float64 [S][27].

@@ -126,9 +126,10 @@ def clipped_elbo_fn(orc, s, nbr_theta):
     return f
 
 
-def cross_block_formula(orc, theta, s, t):
+def cross_block_formula(orc, theta, s, t, absolute=False):
     """d2J/dtheta_s dtheta_t from per-pixel Jacobians (the closed form in the module docstring):
-    sum over the pixels of W_s cap W_t of l_EE dE_s dE_t^T + l_EV (dE_s dV_t^T + dV_s dE_t^T)."""
+    sum over the pixels of W_s cap W_t of l_EE dE_s dE_t^T + l_EV (dE_s dV_t^T + dV_s dE_t^T).
+    absolute: the sum of the three terms' magnitudes instead (each entry's natural scale)."""
     theta = np.asarray(theta, np.float64)
     out = np.zeros((27, 27))
     wins = _image_windows(orc)
@@ -165,9 +166,10 @@ def cross_block_formula(orc, theta, s, t):
         Js = torch.func.jacrev(lambda th: EV(th, s))(torch.as_tensor(theta[s]))   # [2, npix, 27]
         Jt = torch.func.jacrev(lambda th: EV(th, t))(torch.as_tensor(theta[t]))
         dEs, dVs, dEt, dVt = Js[0], Js[1], Jt[0], Jt[1]
-        out += (torch.einsum("m,mi,mj->ij", l_EE, dEs, dEt)
-                + torch.einsum("m,mi,mj->ij", l_EV, dEs, dVt)
-                + torch.einsum("m,mi,mj->ij", l_EV, dVs, dEt)).numpy()
+        f = torch.abs if absolute else (lambda z: z)
+        out += (f(torch.einsum("m,mi,mj->mij", l_EE, dEs, dEt)).sum(0)
+                + f(torch.einsum("m,mi,mj->mij", l_EV, dEs, dVt)).sum(0)
+                + f(torch.einsum("m,mi,mj->mij", l_EV, dVs, dEt)).sum(0)).numpy()
     return out
 
 

@@ -16,6 +16,7 @@ NPARAM = 27
 WANT_ELBO, WANT_GRAD, WANT_HESS = 1, 2, 4
 STATUS_CONVERGED, STATUS_MAX_ITER, STATUS_NONFINITE, STATUS_RADIUS_COLLAPSE = 0, 1, 2, 3
 HESS_FP32, HESS_TF32, HESS_BF16X3 = 0, 1, 2
+NBR_FULL, NBR_WINDOW = 0, 1
 
 
 class CelesteError(RuntimeError):
@@ -54,7 +55,8 @@ EXPORTED = ["celeste_problem_create", "celeste_problem_workspace_bytes", "celest
             "celeste_problem_destroy", "celeste_strerror", "celeste_last_error_detail", "celeste_profile_start",
             "celeste_profile_stop", "celeste_tr_solve_batch", "celeste_elbo_batch_noalloc", "celeste_cnn_param_count",
             "celeste_cnn_workspace_bytes", "celeste_cnn_init", "celeste_cnn_forward", "celeste_cnn_backward",
-            "celeste_cnn_mse", "celeste_cnn_adamw", "celeste_extract_patches", "celeste_covariance_batch"]
+            "celeste_cnn_mse", "celeste_cnn_adamw", "celeste_extract_patches", "celeste_covariance_batch",
+            "celeste_render_background_mode", "celeste_joint_pairs", "celeste_joint_cross_hessian"]
 
 
 def load_library(path=None):
@@ -88,6 +90,9 @@ def load_library(path=None):
                                              ctypes.c_float, ctypes.c_float, ctypes.c_int, vp]),
         "celeste_extract_patches": (ctypes.c_int, [vp, dp, vp]),
         "celeste_covariance_batch": (ctypes.c_int, [vp, dp, dp, dp, vp]),
+        "celeste_render_background_mode": (ctypes.c_int, [vp, dp, ctypes.c_int, vp]),
+        "celeste_joint_pairs": (ctypes.c_int, [vp, dp, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
+        "celeste_joint_cross_hessian": (ctypes.c_int, [vp, dp, dp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -176,9 +181,29 @@ class Problem:
         _check(lib().celeste_problem_counts(self.handle, c))
         return dict(sources=c[0], patches=c[1], tiles=c[2], pixels=c[3], neighbours=c[4])
 
-    def render_background(self, nbr_theta, stream=None):
+    def render_background(self, nbr_theta, mode=NBR_FULL, stream=None):
+        """Neighbour background at nbr_theta; mode NBR_WINDOW counts each neighbour on its own window
+        only (the joint objective's per-source blocks)."""
         assert nbr_theta.dtype == torch.float64 and nbr_theta.is_contiguous() and nbr_theta.shape == (self.S, NPARAM)
-        _check(lib().celeste_render_background(self.handle, _ptr(nbr_theta), _stream(stream)))
+        _check(lib().celeste_render_background_mode(self.handle, _ptr(nbr_theta), ctypes.c_int(mode), _stream(stream)))
+
+    def joint_pairs(self):
+        """[n_pairs, 2] int32 (host numpy): source pairs s < t whose windows overlap."""
+        n = ctypes.c_int64(0)
+        _check(lib().celeste_joint_pairs(self.handle, None, ctypes.c_int64(0), ctypes.byref(n)))
+        out = np.zeros((max(n.value, 1), 2), dtype=np.int32)
+        _check(lib().celeste_joint_pairs(self.handle, out.ctypes.data_as(ctypes.c_void_p), ctypes.c_int64(n.value),
+                                         ctypes.byref(n)))
+        return out[:n.value]
+
+    def cross_hessian(self, theta, stream=None):
+        """Cross-source Hessian blocks of the joint objective, [n_pairs, 27, 27] float64 on theta's
+        device, in the order of joint_pairs(); the background must be rendered with NBR_WINDOW at theta."""
+        assert theta.dtype == torch.float64 and theta.is_contiguous() and theta.shape == (self.S, NPARAM)
+        n = len(self.joint_pairs())
+        out = torch.empty(max(n, 1), NPARAM, NPARAM, dtype=torch.float64, device=theta.device)
+        _check(lib().celeste_joint_cross_hessian(self.handle, _ptr(theta), _ptr(out), _stream(stream)))
+        return out[:n]
 
     def elbo_batch(self, theta, want=WANT_ELBO | WANT_GRAD | WANT_HESS, stream=None):
         assert theta.dtype == torch.float64 and theta.is_contiguous() and theta.shape == (self.S, NPARAM)

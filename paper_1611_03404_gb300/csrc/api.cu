@@ -5,15 +5,23 @@
 
 using namespace celeste;
 
-extern "C" int celeste_render_background(celeste_problem* p, const double* nbr_theta, celeste_stream_t stream) {
+extern "C" int celeste_render_background_mode(celeste_problem* p, const double* nbr_theta, int mode,
+                                              celeste_stream_t stream) {
   if (!p) return fail(CELESTE_ERR_INVALID_ARG, "null problem");
   if (!p->bound) return fail(CELESTE_ERR_STATE, "problem is not bound to a workspace");
   if (!nbr_theta) return fail(CELESTE_ERR_INVALID_ARG, "null nbr_theta");
-  cudaError_t e = launch_background(p->dev, nbr_theta, (cudaStream_t)stream);
+  if (mode != CELESTE_NBR_FULL && mode != CELESTE_NBR_WINDOW)
+    return fail(CELESTE_ERR_INVALID_ARG, "mode must be CELESTE_NBR_FULL or CELESTE_NBR_WINDOW");
+  cudaError_t e = launch_background(p->dev, nbr_theta, mode == CELESTE_NBR_WINDOW ? 1 : 0, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "background kernel");
   prof_count(p, 1);
   p->background_ready = true;
+  p->background_mode = mode;
   return CELESTE_OK;
+}
+
+extern "C" int celeste_render_background(celeste_problem* p, const double* nbr_theta, celeste_stream_t stream) {
+  return celeste_render_background_mode(p, nbr_theta, CELESTE_NBR_FULL, stream);
 }
 
 extern "C" int celeste_elbo_batch(celeste_problem* p, const double* theta, unsigned want, double* elbo, double* grad,

@@ -18,25 +18,6 @@ namespace celeste {
 
 __device__ constexpr int tri11d(int i, int j) { return i * 11 - i * (i - 1) / 2 + (j - i); }
 
-// Brightness parameter indices of type t (r1, rho, c1 x4, gamma x4).
-__device__ inline int bvar(int type, int v) {
-  if (v == 0) return type ? 9 : 7;
-  if (v == 1) return type ? 10 : 8;
-  if (v < 6) return (type ? 19 : 11) + (v - 2);
-  return (type ? 23 : 15) + (v - 6);
-}
-
-// Inverse of bvar for a brightness parameter index j >= 7: type and variable number.
-__device__ inline void bvar_inv(int j, int& t, int& v) {
-  t = (j == 9 || j == 10 || j >= 19) ? 1 : 0;
-  if (j == 7 || j == 9) v = 0;
-  else if (j == 8 || j == 10) v = 1;
-  else if (j < 15) v = 2 + (j - 11);
-  else if (j < 19) v = 6 + (j - 15);
-  else if (j < 23) v = 2 + (j - 19);
-  else v = 6 + (j - 23);
-}
-
 // One normal-KL term of type t: k = 0 the log flux, k = 1..4 the colours j = k - 1, with v the
 // exp of its log-variance parameter.
 // KL_N(m, v || mu, s2) = (log s2 - log v + (v + (m - mu)^2) / s2 - 1) / 2.

@@ -2,6 +2,8 @@
 // optimised with its neighbours held fixed).  For pixel m of source s's patch in image n:
 //   bE(m) = sky_n + iota_n sum_{s' in nbr(s, n)} E[G_s'](m),  bV(m) = iota_n^2 sum Var[G_s'](m),
 // with the neighbours' full variational moments (value-only profiles, no derivatives).
+// clip = 1 (the joint objective's per-source blocks): a neighbour counts only on the pixels of its
+// own window, as every source does in the objective over all sources jointly.
 #include "celeste_internal.cuh"
 #include "kernels.h"
 
@@ -10,9 +12,11 @@ namespace celeste {
 // ------------------------------------------------------------------------------ background
 constexpr int NB_CHUNK = 8;   // neighbours staged per pass
 
-__global__ void __launch_bounds__(BLOCK) background_kernel(ProblemDev P, const double* __restrict__ nbr_theta) {
+__global__ void __launch_bounds__(BLOCK) background_kernel(ProblemDev P, const double* __restrict__ nbr_theta,
+                                                           int clip) {
   __shared__ __align__(16) float tab[NB_CHUNK][NCOMP * 6];
   __shared__ float cst[NB_CHUNK][10];   // A0 A1 C0 C1 Cx L10 L11 e
+  __shared__ int win[NB_CHUNK][4];      // neighbour's window relative to this patch: x0, y0, x1, y1 (exclusive)
   const TileDev t = P.tiles[blockIdx.x];
   const PatchDev pt = P.patches[t.patch];
   const ImageDev im = P.images[pt.image];
@@ -46,6 +50,10 @@ __global__ void __launch_bounds__(BLOCK) background_kernel(ProblemDev P, const d
         const float A[4] = {(float)im.A[0], (float)im.A[1], (float)im.A[2], (float)im.A[3]};
         gal_value_entry(pc, congruence(A, gs.S), P.nu[j], P.tau[j], px, py, &tab[q][6 * c]);
       } else {
+        win[q][0] = nb.x0 - pt.x0;
+        win[q][1] = nb.y0 - pt.y0;
+        win[q][2] = nb.x0 - pt.x0 + nb.w;
+        win[q][3] = nb.y0 - pt.y0 + nb.h;
         SNConst sc;
         sn_constants(th, im.band, im.iota, sc);
         cst[q][0] = sc.A0;
@@ -66,6 +74,7 @@ __global__ void __launch_bounds__(BLOCK) background_kernel(ProblemDev P, const d
       const int row = idx / pt.w, col = idx - row * pt.w;
       const float fx = (float)col, fy = (float)row;
       for (int q = 0; q < nc; ++q) {
+        if (clip && (col < win[q][0] || col >= win[q][2] || row < win[q][1] || row >= win[q][3])) continue;
         float f0 = 0.f, fE = 0.f, fD = 0.f;
 #pragma unroll
         for (int c = 0; c < NSTAR; ++c) f0 += gauss_value(&tab[q][6 * c], fx, fy);
@@ -93,9 +102,9 @@ __global__ void __launch_bounds__(BLOCK) background_kernel(ProblemDev P, const d
   }
 }
 
-cudaError_t launch_background(const ProblemDev& P, const double* nbr_theta, cudaStream_t st) {
+cudaError_t launch_background(const ProblemDev& P, const double* nbr_theta, int clip, cudaStream_t st) {
   if (P.n_tiles == 0) return cudaSuccess;
-  background_kernel<<<P.n_tiles, BLOCK, 0, st>>>(P, nbr_theta);
+  background_kernel<<<P.n_tiles, BLOCK, 0, st>>>(P, nbr_theta, clip);
   return cudaGetLastError();
 }
 

@@ -198,6 +198,25 @@ __device__ inline PsfComp load_psf(const float* psf_patch, int k) {
 
 // Brightness moments of a lognormal flux in band b for type i: log l_b ~ N(m, v),
 // m = r1 + a_b.c1, v = exp(rho) + (a_b^2).exp(gam); E[l] = exp(m + v/2), E[l^2] = exp(2m + 2v).
+// Brightness parameter indices of type t (r1, rho, c1 x4, gamma x4).
+__device__ inline int bvar(int type, int v) {
+  if (v == 0) return type ? 9 : 7;
+  if (v == 1) return type ? 10 : 8;
+  if (v < 6) return (type ? 19 : 11) + (v - 2);
+  return (type ? 23 : 15) + (v - 6);
+}
+
+// Inverse of bvar for a brightness parameter index j >= 7: type and variable number.
+__device__ inline void bvar_inv(int j, int& t, int& v) {
+  t = (j == 9 || j == 10 || j >= 19) ? 1 : 0;
+  if (j == 7 || j == 9) v = 0;
+  else if (j == 8 || j == 10) v = 1;
+  else if (j < 15) v = 2 + (j - 11);
+  else if (j < 19) v = 6 + (j - 15);
+  else if (j < 23) v = 2 + (j - 19);
+  else v = 6 + (j - 23);
+}
+
 // a_bj in {-1, 0, 1}: u = r - c1 - c2, g = r - c2, r, i = r + c3, z = r + c3 + c4 (log fluxes; no
 // table, so a run-time band indexes no local memory).
 __host__ __device__ inline double color_coef(int band, int j) {

@@ -5,7 +5,8 @@
 
 namespace celeste {
 
-cudaError_t launch_background(const ProblemDev& P, const double* nbr_theta, cudaStream_t st);
+// clip: neighbours counted on their own windows only (the joint objective's per-source blocks).
+cudaError_t launch_background(const ProblemDev& P, const double* nbr_theta, int clip, cudaStream_t st);
 // Rebuilds the tile/patch/source worklists from the sources whose flags match `mask`. Every
 // launcher below works on the current worklists, whose counts live on the device, so a sequence
 // of launches needs no host round trip and can be captured in a CUDA graph.

@@ -80,8 +80,10 @@ __global__ void __launch_bounds__(32 * TR_WARPS) tr_step_kernel(NewtonDev N, int
   const double* gL = N.gL + (size_t)s * NP;
   // f = -L, g = -gL, B = -HL
   const double gk = lane < NP ? -gL[lane] : 0.0;
-  bool finite = isfinite(N.L[s]) && isfinite(gk);
-  for (int i = lane; i < NP * NP; i += 32) finite = finite && isfinite(HL[i]);
+  // (no short-circuit: the loads are independent and issue together)
+  bool finite = isfinite(N.L[s]) & isfinite(gk);
+#pragma unroll
+  for (int i = lane; i < NP * NP; i += 32) finite &= isfinite(HL[i]);
   finite = __all_sync(0xffffffffu, finite);
   if (!finite) {
     if (lane == 0) {

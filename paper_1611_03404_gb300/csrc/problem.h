@@ -42,6 +42,12 @@ struct celeste_problem {
   celeste::ProblemDev dev{};
   bool bound = false;
   bool background_ready = false;
+  int background_mode = 0;                            // CELESTE_NBR_* of the last rendering
+  // joint objective (built on first use): overlapping pairs, their overlap items and tiles
+  bool joint_built = false;
+  std::vector<int> joint_pairs;                       // [n_pairs][2] sources s < t
+  int joint_n_items = 0, joint_n_tiles = 0;
+  void* joint_dev = nullptr;                          // items, tiles, pair CSR, tile partials
   // profiling (celeste_profile_start/stop)
   bool prof_on = false;
   std::vector<cudaEvent_t> prof_events;

@@ -30,3 +30,23 @@ def test_passes_settle():
     assert hist[3]["mean_change"] < hist[1]["mean_change"] < 0.25 * hist[0]["mean_change"]
     assert hist[3]["newton_iters_mean"] < hist[0]["newton_iters_mean"]
     assert all(h["converged"] >= 0.99 * sc.n_sources for h in hist)
+
+
+def test_window_passes_approach_joint_stationarity():
+    """Window mode: the passes are block-coordinate ascent on the joint objective; its gradient
+    at the end of each pass (every neighbour at its new value) shrinks from pass to pass."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1611_03404_gb300 as P
+    from paper_1611_03404_gb300.blockcoord import block_coordinate
+    dev = torch.device("cuda:0")
+    sc = synth.field(seed=1622, W=768, H=560, n_sources=200)
+    prob = P.Problem(sc, device=dev)
+    theta, hist = block_coordinate(prob, torch.as_tensor(sc.theta0, device=dev), passes=4, mode=P.NBR_WINDOW,
+                                   residual=True)
+    print("JOINT " + json.dumps(hist))
+    med = [h["grad_median"] for h in hist]
+    assert med[3] < med[1] < med[0]
+    assert all(h["converged"] >= 0.98 * sc.n_sources for h in hist)
