@@ -27,7 +27,7 @@ Everything here is plain float64 PyTorch; derivatives by automatic differentiati
 import numpy as np
 import torch
 
-from .celeste_oracle import kl_source, pixel_term, source_moments
+from .celeste_oracle import kl_source, pixel_term, source_moments, trust_region_newton
 
 torch.set_default_dtype(torch.float64)
 
@@ -182,3 +182,26 @@ def overlapping_pairs(orc):
                 if s < t:
                     pairs.add((s, t))
     return sorted(pairs)
+
+
+def joint_newton(orc, theta0, **opts):
+    """Trust-region Newton on f = -J over all sources at once (the same rules as the per-source
+    solve, Nocedal & Wright Alg. 4.1 with the exact subproblem), in float64.
+    Returns dict(theta [S, 27], elbo = J, iters, status)."""
+    J = joint_fn(orc)
+    shape = np.asarray(theta0).shape
+
+    def value(th):
+        with torch.no_grad():
+            return float(J(torch.as_tensor(th.reshape(shape))))
+
+    def vgh(th):
+        t = torch.as_tensor(th.reshape(shape)).clone()
+        n = t.numel()
+        g = torch.func.grad(J)(t).reshape(n)
+        H = torch.func.hessian(J)(t).reshape(n, n)
+        return value(th), g.numpy(), H.numpy()
+
+    res = trust_region_newton(value, vgh, np.asarray(theta0, np.float64).ravel(), **opts)
+    res["theta"] = res["theta"].reshape(shape)
+    return res
