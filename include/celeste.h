@@ -196,6 +196,36 @@ int celeste_joint_pairs(celeste_problem* p, int32_t* pairs, int64_t capacity, in
  * Errors: CELESTE_ERR_STATE when the background was not rendered in window mode. */
 int celeste_joint_cross_hessian(celeste_problem* p, const double* theta, double* blocks, celeste_stream_t stream);
 
+/* Trust-region Newton on the joint objective J over all sources at once (paper, concluding
+ * section), with the per-source solve's rules (Nocedal & Wright Alg. 4.1: eta, the radius update
+ * by 1/4 and 2, ftol on accepted changes and on the Newton decrement, gtol on max |grad|).  The
+ * subproblem is solved by preconditioned conjugate gradients with Steihaug's stopping rules
+ * (Nocedal & Wright Alg. 7.2) over the block-sparse Hessian (celeste_elbo_batch's per-source
+ * blocks in window mode and celeste_joint_cross_hessian's cross blocks); the preconditioner is
+ * blockdiag(-H_ss + mu_s I), mu_s the first shift of {0, 1e-8, 1e-6, 1e-4, 1e-2, 1} x max|H_ii|
+ * that makes the block positive definite, and the radius is measured in its norm, starting at the
+ * norm of the block-diagonal Newton step and capped at opts->delta_max times that.  J's change at
+ * a trial point is summed per pixel against the stored rates at the current point (float32 per
+ * pixel, float64 across tiles and sources), each pixel weighted by 1 / (windows holding it).
+ *   theta:  device float64 [S][27], start on entry, result on return;
+ *   opts:   NULL or the per-source solve's options (graph_iters unused; delta0 unused: see above);
+ *   max_cg: conjugate-gradient iterations per subproblem (<= 0: 100); a subproblem stops early
+ *           once the residual is below 1e-2 |g|;
+ *   iters_out, status_out, J_out, cg_iters_out (may be NULL): host; outer iterations, one
+ *           CELESTE_STATUS_* for the whole solve, J at the result, total CG iterations.
+ * Synchronous (reads a few scalars back every iteration); leaves the background rendered in
+ * window mode at the result.  Allocates its state (about 12 KB per source plus 12 bytes per patch
+ * pixel) with cudaMalloc on first use, owned by the problem. */
+int celeste_joint_newton(celeste_problem* p, double* theta, const celeste_newton_opts* opts, int32_t max_cg,
+                         int32_t* iters_out, int32_t* status_out, double* J_out, int32_t* cg_iters_out,
+                         celeste_stream_t stream);
+
+/* The joint objective J at theta (device float64 [S][27]) into *J_out (host): the window-mode
+ * background at theta, each patch pixel's term weighted by 1 / (windows holding it), float32 per
+ * pixel and float64 across tiles and sources, minus every source's KL.  Synchronous; leaves the
+ * background rendered in window mode at theta. */
+int celeste_joint_value(celeste_problem* p, const double* theta, double* J_out, celeste_stream_t stream);
+
 /* ELBO of every source's subproblem and, on request, its exact gradient and dense Hessian
  * w.r.t. the 27 free parameters (Eq. (1)-(2) restricted to the source's patches, minus its KL).
  *   theta: device float64 [S][27].

@@ -24,10 +24,13 @@ diagonal Hessian blocks are that objective's Hessian, and the cross block of two
 (E and V are sums over sources, so their mixed second derivatives vanish, and l_VV = 0).
 Everything here is plain float64 PyTorch; derivatives by automatic differentiation.
 """
+import math
+
 import numpy as np
 import torch
 
-from .celeste_oracle import kl_source, pixel_term, source_moments, trust_region_newton
+from .celeste_oracle import (STATUS_CONVERGED, STATUS_MAX_ITER, STATUS_NONFINITE, STATUS_RADIUS_COLLAPSE,
+                             kl_source, pixel_term, source_moments, trust_region_newton)
 
 torch.set_default_dtype(torch.float64)
 
@@ -205,3 +208,145 @@ def joint_newton(orc, theta0, **opts):
     res = trust_region_newton(value, vgh, np.asarray(theta0, np.float64).ravel(), **opts)
     res["theta"] = res["theta"].reshape(shape)
     return res
+
+
+# ----------------------------------------------------------------------------- joint Newton, CG subproblems
+PRECOND_LADDER = (1e-4, 1e-3, 1e-2, 1e-1, 1.0, 10.0)
+
+
+def preconditioner(H):
+    """Per source s the matrix M_s = -H_ss + mu I for the first mu in PRECOND_LADDER x max_i |H_ii|
+    that makes it positive definite (else diag(|H_ii|) + max_i |H_ii|); returns the list of M_s."""
+    S = H.shape[0]
+    out = []
+    for s in range(S):
+        B = -H[s, :, s, :]
+        scale = max(np.abs(np.diag(B)).max(), 1e-300)
+        M = None
+        for mu in PRECOND_LADDER:
+            C = B + mu * scale * np.eye(27)
+            try:
+                np.linalg.cholesky(C)
+                M = C
+                break
+            except np.linalg.LinAlgError:
+                continue
+        if M is None:
+            M = np.diag(np.abs(np.diag(B)) + scale)
+        out.append(M)
+    return out
+
+
+def steihaug(g, B, M, delta, max_cg):
+    """Preconditioned conjugate gradients for min g.p + p.B.p/2, |p|_M <= delta, with Steihaug's
+    stopping rules (Nocedal & Wright Alg. 7.2): negative curvature or the boundary -> step to the
+    boundary along the current direction; stop once |r| <= 1e-2 |g|.  M is block-diagonal (list of
+    27 x 27 blocks), g and the vectors are [S, 27].  Returns (p, on_boundary, residual_converged,
+    iterations)."""
+    Minv = lambda v: np.stack([np.linalg.solve(M[s], v[s]) for s in range(len(M))])
+    Mdot = lambda a, b: sum(a[s] @ M[s] @ b[s] for s in range(len(M)))
+    n = g.size
+    x = np.zeros_like(g)
+    r = g.copy()
+    z = Minv(r)
+    d = -z
+    rz = float((r * z).sum())
+    eps = 1e-2 * np.linalg.norm(g)
+    xMx, xMd, dMd = 0.0, 0.0, rz
+
+    def tau():
+        disc = max(xMd * xMd + dMd * (delta * delta - xMx), 0.0)
+        return (-xMd + math.sqrt(disc)) / dMd
+
+    if not (np.linalg.norm(g) > 0 and rz > 0):
+        return x, False, False, 0
+    for j in range(max_cg):
+        Bd = (B @ d.reshape(n)).reshape(g.shape)
+        kappa = float((d * Bd).sum())
+        if not kappa > 0:
+            return x + tau() * d, True, False, j + 1
+        alpha = rz / kappa
+        if xMx + 2 * alpha * xMd + alpha * alpha * dMd >= delta * delta:
+            return x + tau() * d, True, False, j + 1
+        x = x + alpha * d
+        r = r + alpha * Bd
+        xMx += 2 * alpha * xMd + alpha * alpha * dMd
+        if np.linalg.norm(r) <= eps:
+            return x, False, True, j + 1
+        z = Minv(r)
+        rz_new = float((r * z).sum())
+        beta = rz_new / rz
+        rz = rz_new
+        xMd = beta * (xMd + alpha * dMd)
+        dMd = rz + beta * beta * dMd
+        d = -z + beta * d
+    return x, False, False, max_cg
+
+
+def joint_newton_steihaug(orc, theta0, max_iter=100, max_cg=100, ftol=1e-8, gtol=1e-10, delta_max=1e4, eta=0.1,
+                          delta_min=1e-12):
+    """Trust-region Newton on f = -J (Nocedal & Wright Alg. 4.1: acceptance eta, radius x1/4 below
+    rho = 1/4 and x2 above 3/4 on the boundary, ftol on accepted changes and on the Newton
+    decrement of a converged subproblem, gtol on max |grad|) with each subproblem solved by
+    `steihaug` in the norm of `preconditioner`'s blocks; the radius starts at the norm of the
+    block-diagonal Newton step, sqrt(g^T M^-1 g), and is capped at delta_max times that.
+    Returns dict(theta, elbo = J, iters, status, cg_iters)."""
+    J = joint_fn(orc)
+    th = np.asarray(theta0, np.float64).copy()
+    S = th.shape[0]
+    n = S * 27
+
+    def value(t):
+        with torch.no_grad():
+            return float(J(torch.as_tensor(t)))
+
+    def grad_hess(t):
+        tt = torch.as_tensor(t).clone()
+        return torch.func.grad(J)(tt).numpy(), torch.func.hessian(J)(tt).numpy()
+
+    f = -value(th)
+    gJ, H = grad_hess(th)
+    M = preconditioner(H)
+    g0 = -gJ
+    rz0 = float(sum(g0[s] @ np.linalg.solve(M[s], g0[s]) for s in range(S)))
+    delta = math.sqrt(rz0) if rz0 > 0 else 1.0
+    cap = delta_max * delta
+    status, it, cg = STATUS_MAX_ITER, 0, 0
+    while it < max_iter:
+        g = -gJ
+        B = -H.reshape(n, n)
+        p, boundary, rstop, k = steihaug(g, B, M, delta, max_cg)
+        cg += k
+        if not (np.isfinite(f) and np.all(np.isfinite(g))):
+            status = STATUS_NONFINITE
+            break
+        if np.abs(g).max() <= gtol:
+            status = STATUS_CONVERGED
+            break
+        it += 1
+        pred = -(float((g * p).sum()) + 0.5 * float(p.reshape(n) @ B @ p.reshape(n)))
+        if not boundary and rstop and pred <= ftol * abs(f):
+            status = STATUS_CONVERGED
+            break
+        trial = th + p
+        dJ = value(trial) + f   # J(trial) - J(th)
+        rho = dJ / pred if pred > 0 else -1.0
+        if not np.isfinite(dJ):
+            rho = -1.0
+        if rho < 0.25:
+            delta *= 0.25
+        elif rho > 0.75 and boundary:
+            delta = min(2.0 * delta, cap)
+        if rho > eta:
+            f_new = f - dJ
+            done = abs(dJ) <= ftol * abs(f_new)
+            th, f = trial, f_new
+            gJ, H = grad_hess(th)
+            M = preconditioner(H)
+            if done:
+                status = STATUS_CONVERGED
+                break
+        if delta < delta_min:
+            status = STATUS_RADIUS_COLLAPSE
+            break
+    return dict(theta=th, elbo=-f, iters=it, status=status, cg_iters=cg)

@@ -56,7 +56,8 @@ EXPORTED = ["celeste_problem_create", "celeste_problem_workspace_bytes", "celest
             "celeste_profile_stop", "celeste_tr_solve_batch", "celeste_elbo_batch_noalloc", "celeste_cnn_param_count",
             "celeste_cnn_workspace_bytes", "celeste_cnn_init", "celeste_cnn_forward", "celeste_cnn_backward",
             "celeste_cnn_mse", "celeste_cnn_adamw", "celeste_extract_patches", "celeste_covariance_batch",
-            "celeste_render_background_mode", "celeste_joint_pairs", "celeste_joint_cross_hessian"]
+            "celeste_render_background_mode", "celeste_joint_pairs", "celeste_joint_cross_hessian",
+            "celeste_joint_newton", "celeste_joint_value"]
 
 
 def load_library(path=None):
@@ -93,6 +94,10 @@ def load_library(path=None):
         "celeste_render_background_mode": (ctypes.c_int, [vp, dp, ctypes.c_int, vp]),
         "celeste_joint_pairs": (ctypes.c_int, [vp, dp, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
         "celeste_joint_cross_hessian": (ctypes.c_int, [vp, dp, dp, vp]),
+        "celeste_joint_value": (ctypes.c_int, [vp, dp, ctypes.POINTER(ctypes.c_double), vp]),
+        "celeste_joint_newton": (ctypes.c_int, [vp, dp, ctypes.POINTER(NewtonOpts), ctypes.c_int32,
+                                                ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                                ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32), vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -195,6 +200,27 @@ class Problem:
         _check(lib().celeste_joint_pairs(self.handle, out.ctypes.data_as(ctypes.c_void_p), ctypes.c_int64(n.value),
                                          ctypes.byref(n)))
         return out[:n.value]
+
+    def joint_newton(self, theta, max_iter=50, ftol=1e-8, gtol=1e-10, delta_max=1e4, eta=0.1, delta_min=1e-12,
+                     max_cg=100, stream=None):
+        """Trust-region Newton on the joint objective over all sources (theta updated in place).
+        Returns dict(iters, status, J, cg_iters)."""
+        assert theta.dtype == torch.float64 and theta.is_contiguous() and theta.shape == (self.S, NPARAM)
+        o = NewtonOpts(max_iter=max_iter, ftol=ftol, gtol=gtol, delta0=1.0, delta_max=delta_max, eta=eta,
+                       delta_min=delta_min, graph_iters=1)
+        it, st, cg = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
+        J = ctypes.c_double(0.0)
+        _check(lib().celeste_joint_newton(self.handle, _ptr(theta), ctypes.byref(o), ctypes.c_int32(max_cg),
+                                          ctypes.byref(it), ctypes.byref(st), ctypes.byref(J), ctypes.byref(cg),
+                                          _stream(stream)))
+        return {"iters": it.value, "status": st.value, "J": J.value, "cg_iters": cg.value}
+
+    def joint_value(self, theta, stream=None):
+        """The joint objective J at theta (every covered pixel counted once)."""
+        assert theta.dtype == torch.float64 and theta.is_contiguous() and theta.shape == (self.S, NPARAM)
+        J = ctypes.c_double(0.0)
+        _check(lib().celeste_joint_value(self.handle, _ptr(theta), ctypes.byref(J), _stream(stream)))
+        return J.value
 
     def cross_hessian(self, theta, stream=None):
         """Cross-source Hessian blocks of the joint objective, [n_pairs, 27, 27] float64 on theta's

@@ -23,10 +23,14 @@ __global__ void __launch_bounds__(BLOCK) background_kernel(ProblemDev P, const d
   const int tid = threadIdx.x;
   const int nn = pt.nbr_end - pt.nbr_begin;
   float bE[8], bV[8];
+  int cover[8];   // windows holding the pixel (its own and the neighbours'), window mode
   constexpr int MAXPPT = 8;
   const int ppt = (t.count + BLOCK - 1) / BLOCK;
 #pragma unroll
-  for (int r = 0; r < MAXPPT; ++r) bE[r] = bV[r] = 0.f;
+  for (int r = 0; r < MAXPPT; ++r) {
+    bE[r] = bV[r] = 0.f;
+    cover[r] = 1;
+  }
   for (int c0 = 0; c0 < nn; c0 += NB_CHUNK) {
     const int nc = min(NB_CHUNK, nn - c0);
     __syncthreads();
@@ -75,6 +79,7 @@ __global__ void __launch_bounds__(BLOCK) background_kernel(ProblemDev P, const d
       const float fx = (float)col, fy = (float)row;
       for (int q = 0; q < nc; ++q) {
         if (clip && (col < win[q][0] || col >= win[q][2] || row < win[q][1] || row >= win[q][3])) continue;
+        cover[r] += 1;
         float f0 = 0.f, fE = 0.f, fD = 0.f;
 #pragma unroll
         for (int c = 0; c < NSTAR; ++c) f0 += gauss_value(&tab[q][6 * c], fx, fy);
@@ -99,6 +104,7 @@ __global__ void __launch_bounds__(BLOCK) background_kernel(ProblemDev P, const d
     o.y = im.sky + im.iota * bE[r];
     o.z = im.iota * im.iota * bV[r];
     *v = o;
+    if (clip && P.pweight) P.pweight[pt.pix_off + t.start + i] = 1.f / (float)cover[r];
   }
 }
 

@@ -104,6 +104,9 @@ struct ProblemDev {
                                  // then the three queue heads
   int* err;                      // [4] device error words
   unsigned long long* counters;  // [4]: full-kernel pixels, value-kernel pixels
+  float* pweight;                 // [n_pix] or null: 1 / (number of windows holding the pixel), written by the
+                                 // window-mode background and applied by the value kernel (joint objective)
+  float2* refEV;                 // [n_pix] or null: each pixel's (E, V) at the joint solver's current point
   int S, n_patches, n_tiles, tile_pixels, n_sm, hmode;
   double priors[5];
   double log_var_r, log_var_c, log_phi, log1m_phi, logit_phi;   // logs of the priors (host-computed)

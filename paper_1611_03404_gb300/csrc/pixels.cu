@@ -607,17 +607,24 @@ __global__ void __launch_bounds__(BLOCK) elbo_value_kernel(ProblemDev P, int dif
     const float E = pv.y + c.iota * EG;
     const float V = pv.z + c.iota * c.iota * VG;
     const float x = pv.x;
-    if (diff) {
+    if (diff == 2) {
+      // joint objective: every source may have moved; the change from the stored pixel rates at
+      // the reference point, weighted by 1 / (windows holding the pixel)
+      const float2 ref = P.refEV[pt.pix_off + idx];
+      const float w = P.pweight[pt.pix_off + idx];
+      const float dE = E - ref.x;
+      sum += w * (x > 0.f ? x * log1pf(dE / ref.x) - dE - 0.5f * x * (V / (E * E) - ref.y / (ref.x * ref.x)) : -dE);
+    } else if (diff) {
       const float2 ref = P.srcmom[pt.pix_off + idx];
       const float dE = c.iota * (EG - ref.x);                  // E(theta) - E(theta_ref)
       const float Er = pv.y + c.iota * ref.x;
       const float Vr = pv.z + c.iota * c.iota * ref.y;
       sum += x > 0.f ? x * log1pf(dE / Er) - dE - 0.5f * x * (V / (E * E) - Vr / (Er * Er)) : -dE;
-    } else if (x > 0.f) {
-      const float dEx = E - x;
-      sum += pv.w + x * log1pf(dEx / x) - dEx - 0.5f * x * V / (E * E);
     } else {
-      sum += -E;
+      // pixel weight: 1 / (windows holding the pixel) for the joint objective, else 1
+      const float w = P.pweight ? P.pweight[pt.pix_off + idx] : 1.f;
+      const float dEx = E - x;
+      sum += w * (x > 0.f ? pv.w + x * log1pf(dEx / x) - dEx - 0.5f * x * V / (E * E) : -E);
     }
   }
 #pragma unroll
@@ -678,7 +685,7 @@ cudaError_t launch_value(const ProblemDev& P, const double* theta, bool diff, cu
 
 cudaError_t launch_value_kernel(const ProblemDev& P, bool diff, cudaStream_t st) {
   if (P.n_tiles == 0) return cudaSuccess;
-  const int d = diff ? 1 : 0;
+  const int d = diff ? (P.refEV ? 2 : 1) : 0;   // difference from the joint reference rates when set
   const int g = std::max(1, std::min(P.n_tiles, P.n_sm * VALUE_CTAS_PER_SM));
   switch (P.tile_pixels) {
     case 128: elbo_value_kernel<1><<<g, BLOCK, 0, st>>>(P, d); break;

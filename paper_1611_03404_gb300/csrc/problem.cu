@@ -383,6 +383,8 @@ extern "C" int celeste_problem_bind(celeste_problem* p, void* workspace, size_t 
   D.wl = reinterpret_cast<int*>(base + L.wl);
   D.wl_count = reinterpret_cast<int*>(base + L.wl_count);
   D.snc = reinterpret_cast<SNConst*>(base + L.snc);
+  D.pweight = nullptr;   // set only on the joint solver's copies
+  D.refEV = nullptr;
   D.n_sm = std::max(n_sm, 1);
   D.S = p->S;
   D.n_patches = (int)p->patches.size();
@@ -419,6 +421,7 @@ celeste_problem::~celeste_problem() {
   if (newton_exec) cudaGraphExecDestroy(newton_exec);
   if (capture_stream) cudaStreamDestroy(capture_stream);
   if (joint_dev) cudaFree(joint_dev);
+  if (jn_dev) cudaFree(jn_dev);
 }
 
 extern "C" void celeste_problem_destroy(celeste_problem* p) { delete p; }

@@ -48,6 +48,7 @@ struct celeste_problem {
   std::vector<int> joint_pairs;                       // [n_pairs][2] sources s < t
   int joint_n_items = 0, joint_n_tiles = 0;
   void* joint_dev = nullptr;                          // items, tiles, pair CSR, tile partials
+  void* jn_dev = nullptr;                             // joint Newton state (built on first use)
   // profiling (celeste_profile_start/stop)
   bool prof_on = false;
   std::vector<cudaEvent_t> prof_events;

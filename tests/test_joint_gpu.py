@@ -78,3 +78,63 @@ def test_cross_requires_window_background(P):
     prob.render_background(th)
     with pytest.raises(P.CelesteError):
         prob.cross_hessian(th)
+
+
+def _compare_joint(P, orc, got, ref_theta, J_solver):
+    from test_parity_gpu import compare_optimum, stop_slack
+    Jg, _, _ = JO.joint_value_grad_hess(orc, got)
+    Jr, _, Hr = JO.joint_value_grad_hess(orc, ref_theta)
+    assert abs(J_solver - Jg) <= 1e-6 * abs(Jg)          # the solver's own J is J at its result
+    assert abs(Jg - Jr) <= 1e-6 * abs(Jr)
+    S = got.shape[0]
+    slack = stop_slack(Hr.reshape(S * 27, S * 27), Jr).reshape(S, 27)
+    for s in range(S):
+        compare_optimum(got[s], ref_theta[s], slack=slack[s])
+
+
+def test_joint_value_matches_oracle(P):
+    sc = synth.tiny(seed=3, n_sources=5, n_images=2, H=40, W=44, radius=(6, 12))
+    orc = O.Oracle(sc)
+    rng = np.random.default_rng(4)
+    theta = sc.theta0 + 0.03 * rng.standard_normal(sc.theta0.shape)
+    prob = P.Problem(sc, device=torch.device("cuda:0"), tile_pixels=128)
+    J = prob.joint_value(torch.as_tensor(theta, device="cuda:0").contiguous())
+    with torch.no_grad():
+        ref = float(JO.joint_fn(orc)(torch.as_tensor(theta)))
+    check_elbo(J, ref, "joint value")
+
+
+def test_joint_newton_from_the_catalog(P):
+    """From the catalog of a three-source scene the joint solve reaches the oracle's joint maximum
+    (J within the ELBO tolerance, parameters within compare_optimum's bounds widened by the
+    stopping rule's slack along the joint Hessian's weakly curved directions).  The GPU solves each
+    subproblem inexactly (preconditioned CG in the preconditioner's norm) where this oracle solves
+    it exactly, so the paths differ and the GPU gets up to 100 outer iterations."""
+    sc = synth.tiny(seed=11, n_sources=3, n_images=3)
+    orc = O.Oracle(sc)
+    ref = JO.joint_newton(orc, sc.theta0)
+    assert ref["status"] == O.STATUS_CONVERGED
+    prob = P.Problem(sc, device=torch.device("cuda:0"), tile_pixels=256)
+    th = torch.as_tensor(sc.theta0, device="cuda:0").contiguous()
+    res = prob.joint_newton(th, max_iter=100)
+    print(f"JOINT_NEWTON catalog gpu {res} oracle iters {ref['iters']} J {ref['elbo']}")
+    assert res["status"] == P.STATUS_CONVERGED
+    _compare_joint(P, orc, th.cpu().numpy(), ref["theta"], res["J"])
+
+
+def test_joint_newton_returns_to_a_nearby_maximum(P):
+    """Started next to the oracle's joint maximum of a four-source scene (all six pairs overlap),
+    the joint solve returns to it.  (From the catalog the joint objective has several local maxima
+    here, and paths through inexact and exact subproblems may end in different ones.)"""
+    sc = synth.tiny(seed=5, n_sources=4, n_images=2, H=36, W=40, radius=(5, 9))
+    orc = O.Oracle(sc)
+    ref = JO.joint_newton(orc, sc.theta0)
+    assert ref["status"] == O.STATUS_CONVERGED
+    rng = np.random.default_rng(9)
+    start = ref["theta"] + 0.02 * rng.standard_normal(ref["theta"].shape)
+    prob = P.Problem(sc, device=torch.device("cuda:0"), tile_pixels=128)
+    th = torch.as_tensor(start, device="cuda:0").contiguous()
+    res = prob.joint_newton(th, max_iter=100)
+    print(f"JOINT_NEWTON local gpu {res} oracle J {ref['elbo']}")
+    assert res["status"] == P.STATUS_CONVERGED
+    _compare_joint(P, orc, th.cpu().numpy(), ref["theta"], res["J"])
