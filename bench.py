@@ -74,6 +74,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-joint", dest="joint", action="store_false",
+                    help="skip the untimed joint-objective report")
     return ap.parse_args()
 
 
@@ -396,6 +398,10 @@ def main():
         e2e = {"value": e_conv / te, "unit": "sources/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "ms_per_step": 1e3 * te}
 
+    joint = None
+    if rank == 0 and args.joint and args.workload == "field":
+        joint = joint_report(P, prob, theta0)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "field":
         v, n, thr, dt = cpu_baseline(scene, args.cpu_seconds)
@@ -419,7 +425,8 @@ def main():
                              "flops_per_pixel": FLOPS_FULL_PER_PIXEL,
                              "launches": prof["full_launches"], "kernel_ms": full_ms,
                              "share_of_step": full_ms / (1e3 * t_step) if t_step > 0 else None},
-                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": prof["kernel_launches"] + cnn_launches,
+                "cpu_baseline": cpu, "e2e": e2e, "joint": joint,
+                "gpu_launches": prof["kernel_launches"] + cnn_launches,
                 "clocks": clocks}
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -466,6 +473,30 @@ def train_warm_start(args, P, dev, rank):
                  "loss_first_last": [hist[0], hist[-1]], "data_seconds": t_data, "train_seconds": t_train,
                  "train_pairs_per_s": x.shape[0] * args.ws_epochs / t_train,
                  "params_from_network": "type logit, log variances of the log fluxes and colours"}
+
+
+def joint_report(P, prob, theta0):
+    """Untimed: the joint objective over all sources of the field (every covered pixel counted
+    once), after four window-mode block-coordinate passes from the catalog and after the joint
+    trust-region Newton started from their result."""
+    import torch
+    from paper_1611_03404_gb300.blockcoord import block_coordinate
+    cat = theta0.clone().contiguous()
+    J_cat = prob.joint_value(cat)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    th, _ = block_coordinate(prob, cat, passes=4, mode=P.NBR_WINDOW)
+    torch.cuda.synchronize()
+    t_bc = time.perf_counter() - t0
+    J_bc = prob.joint_value(th)
+    t0 = time.perf_counter()
+    res = prob.joint_newton(th, max_iter=100)
+    t_jn = time.perf_counter() - t0
+    return {"what": "joint objective J (every covered pixel once); 4 window-mode block-coordinate passes from the "
+                    "catalog, then joint trust-region Newton (CG-Steihaug subproblems) from their result; untimed",
+            "pairs": int(len(prob.joint_pairs())), "J_catalog": J_cat, "J_blockcoord_4": J_bc, "blockcoord_s": t_bc,
+            "J_joint": res["J"], "joint_s": t_jn, "joint_iters": res["iters"], "joint_status": res["status"],
+            "joint_cg_iters": res["cg_iters"]}
 
 
 def _build_hash(P):
