@@ -423,6 +423,7 @@ struct JNDev {
 };
 
 constexpr int JN_WARPS = 4;
+constexpr int JN_CHUNK = 4;   // CG iterations enqueued between two reads of the stop flag
 
 __device__ inline double jn_warp_sum(double v) {
 #pragma unroll
@@ -980,15 +981,24 @@ extern "C" int celeste_joint_newton(celeste_problem* p, double* theta, const cel
     JN_LAUNCHED("cg init");
     jn_scalar_init_kernel<<<1, 256, 0, st>>>(J, delta);
     JN_LAUNCHED("cg scalars");
-    for (int j = 0; j < ncg; ++j) {
-      jn_matvec_kernel<<<wb, 32 * JN_WARPS, 0, st>>>(J);
-      JN_LAUNCHED("matvec");
-      jn_scalar_a_kernel<<<1, 256, 0, st>>>(J);
-      JN_LAUNCHED("cg step");
-      jn_update_kernel<<<wb, 32 * JN_WARPS, 0, st>>>(J);
-      JN_LAUNCHED("cg update");
-      jn_scalar_b_kernel<<<1, 256, 0, st>>>(J);
-      JN_LAUNCHED("cg direction");
+    // CG iterations in chunks of JN_CHUNK, the stop flag read back after each chunk (a converged
+    // or truncated subproblem usually stops within the first chunk; the kernels of a chunk that
+    // runs past the stop return at once)
+    for (int j = 0; j < ncg; j += JN_CHUNK) {
+      for (int q = 0; q < JN_CHUNK && j + q < ncg; ++q) {
+        jn_matvec_kernel<<<wb, 32 * JN_WARPS, 0, st>>>(J);
+        JN_LAUNCHED("matvec");
+        jn_scalar_a_kernel<<<1, 256, 0, st>>>(J);
+        JN_LAUNCHED("cg step");
+        jn_update_kernel<<<wb, 32 * JN_WARPS, 0, st>>>(J);
+        JN_LAUNCHED("cg update");
+        jn_scalar_b_kernel<<<1, 256, 0, st>>>(J);
+        JN_LAUNCHED("cg direction");
+      }
+      int stop = 0;
+      JN_TRY(cudaMemcpyAsync(&stop, &scd->stop, sizeof(int), cudaMemcpyDeviceToHost, st), "stop flag");
+      JN_TRY(cudaStreamSynchronize(st), "sync");
+      if (stop) break;
     }
     jn_model_kernel<<<wb, 32 * JN_WARPS, 0, st>>>(J);
     JN_LAUNCHED("model");
