@@ -6,6 +6,8 @@ objectives when no windows overlap; the per-source objective with clipped neighb
 gradient and diagonal Hessian blocks; the closed form of the cross blocks from per-pixel
 Jacobians; and, for a neighbour whose window covers the target's, the per-source objective of
 the main oracle (clipping then changes nothing)."""
+import math
+
 import numpy as np
 import pytest
 import torch
@@ -27,6 +29,12 @@ def joint(scene):
     theta = scene.theta0 + 0.05 * rng.standard_normal(scene.theta0.shape)
     val, g, H = JO.joint_value_grad_hess(orc, theta)
     return orc, theta, val, g, H
+
+
+@pytest.fixture(scope="module")
+def exact_joint(scene):
+    orc = O.Oracle(scene)
+    return orc, JO.joint_newton(orc, scene.theta0)
 
 
 def test_scene_has_overlaps(joint):
@@ -110,13 +118,12 @@ def test_covering_neighbour_clips_nothing():
     assert abs(v - ref) <= 1e-12 * abs(ref)
 
 
-def test_joint_newton_reaches_a_joint_maximum(scene):
+def test_joint_newton_reaches_a_joint_maximum(scene, exact_joint):
     # the joint solve ends at a strict local maximum of J (-J's Hessian positive definite) whose
     # Newton decrement g^T (-H)^-1 g is within the stopping rule's 2 ftol |J|; block-coordinate
     # sweeps on the clipped per-source objectives (the per-source method) raise J monotonically
     # towards it from below without passing it
-    orc = O.Oracle(scene)
-    res = JO.joint_newton(orc, scene.theta0)
+    orc, res = exact_joint
     assert res["status"] == O.STATUS_CONVERGED
     val, g, H = JO.joint_value_grad_hess(orc, res["theta"])
     n = scene.n_sources * 27
@@ -142,3 +149,67 @@ def test_joint_newton_reaches_a_joint_maximum(scene):
             th[s] = O.trust_region_newton(value, vgh, prev[s].copy())["theta"]
         vals.append(JO.joint_value_grad_hess(orc, th)[0])
     assert vals[0] < vals[1] < vals[2] <= val + 1e-9 * abs(val)
+
+
+def _random_blocks(rng, S=2, indefinite=False):
+    """A symmetric block-sparse test problem of S sources (27 each): SPD diagonal blocks with
+    spread curvatures, weak cross blocks; optionally one negative eigenvalue."""
+    n = 27 * S
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    lam = np.exp(rng.uniform(-3, 5, n))
+    if indefinite:
+        lam[0] = -0.5
+    B = (Q * lam) @ Q.T
+    H = -B.reshape(S, 27, S, 27).copy()
+    g = rng.standard_normal((S, 27))
+    return B, H, g
+
+
+def test_steihaug_interior_step_is_an_inexact_newton_step():
+    rng = np.random.default_rng(21)
+    B, H, g = _random_blocks(rng)
+    M = JO.preconditioner(H)
+    p, boundary, rstop, k = JO.steihaug(g, B, M, 1e12, 200)
+    assert not boundary and rstop
+    r = B @ p.ravel() + g.ravel()
+    assert np.linalg.norm(r) <= 1e-2 * np.linalg.norm(g) * (1 + 1e-12)
+
+
+def test_steihaug_boundary_and_model_decrease():
+    rng = np.random.default_rng(22)
+    for indefinite in (False, True):
+        B, H, g = _random_blocks(rng, indefinite=indefinite)
+        M = JO.preconditioner(H)
+        Mn = lambda v: math.sqrt(sum(v[s] @ M[s] @ v[s] for s in range(len(M))))
+        q = lambda v: float(g.ravel() @ v.ravel() + 0.5 * v.ravel() @ B @ v.ravel())
+        delta = 0.1 * Mn(np.stack([np.linalg.solve(M[s], g[s]) for s in range(len(M))]))
+        p, boundary, rstop, k = JO.steihaug(g, B, M, delta, 200)
+        assert boundary and not rstop
+        assert abs(Mn(p) - delta) <= 1e-9 * delta
+        # at least the decrease of the preconditioned Cauchy point (Steihaug: the first CG
+        # iterate is that point, and CG only lowers the model along the path)
+        z = np.stack([np.linalg.solve(M[s], g[s]) for s in range(len(M))])
+        zBz = float(z.ravel() @ B @ z.ravel())
+        gz = float((g * z).sum())
+        tmax = delta / Mn(z)
+        t = tmax if zBz <= 0 else min(gz / zBz, tmax)
+        assert q(p) <= q(-t * z) + 1e-12 * abs(q(-t * z))
+        assert q(p) < 0
+
+
+def test_preconditioner_blocks_are_positive_definite():
+    rng = np.random.default_rng(23)
+    B, H, g = _random_blocks(rng, indefinite=True)
+    for Ms, s in zip(JO.preconditioner(H), range(2)):
+        assert np.linalg.eigvalsh(Ms).min() > 0
+        Bs = -H[s, :, s, :]
+        shift = np.diag(Ms - Bs)
+        assert np.allclose(shift, shift[0]) and shift[0] >= 1e-4 * np.abs(np.diag(Bs)).max() * (1 - 1e-12)
+
+
+def test_joint_newton_steihaug_reaches_the_exact_solve_maximum(scene, exact_joint):
+    # the CG-subproblem solve (the GPU's algorithm) ends at the exact-subproblem solve's maximum
+    orc, ref = exact_joint
+    res = JO.joint_newton_steihaug(orc, scene.theta0)
+    assert res["status"] == O.STATUS_CONVERGED
+    assert abs(res["elbo"] - ref["elbo"]) <= 1e-6 * abs(ref["elbo"])
