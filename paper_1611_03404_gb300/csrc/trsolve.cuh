@@ -22,7 +22,9 @@
 //     positive definiteness of T + lambda I (Sylvester: all LDL^T pivots positive) tells the
 //     points left of the pole -lambda_min; lambda = 0 tests the interior step;
 //   * hard case (the bracket closes on the pole with |p| < delta): eigenvector of lambda_min by
-//     inverse iteration on T after a float32 Sturm bracket, p = y + tau z.
+//     inverse iteration on T after a float32 Sturm bracket, p = y + tau z;
+//   * lane-dependent choices are selects and every lane finishes its evaluation, so the warp
+//     stays converged through the float64 passes (a split warp issues them once per part).
 // The step is mapped back with the reflections, p = Q y.
 #pragma once
 
@@ -172,8 +174,9 @@ __device__ inline void tr_take_y(TrSmem& S, int lane, int src) {
 // multipliers: a geometric grid over the bracket, refined around the Newton point of the
 // largest evaluated multiplier on the left (phi < 0; phi is concave and increasing, so Newton
 // from the left stays left).  Non-positive-definite points lie left of -lambda_min <= lambda*.
-// On return S.y holds the step in the T basis; returns 1 for the hard case (the bracket closes
-// on the pole with phi > 0 to its right), in which S.y is not set.
+// spec bounds |eigenvalues of T| (Gershgorin): the bracket counts as closed once it is narrower
+// than 4 ulps of max(|lambda|, spec).  On return S.y holds the step in the T basis; returns 1 for
+// the hard case (the bracket closes on the pole with phi > 0 to its right), in which S.y is not set.
 __device__ inline int tr_lambda_parallel(TrSmem& S, int lane, double lo, double hi, double delta, bool try_zero,
                                          double spec) {
   constexpr double TOL = 1e-10;
