@@ -180,9 +180,9 @@ enum { CELESTE_NBR_FULL = 0, CELESTE_NBR_WINDOW = 1 };
  * in the order celeste_joint_cross_hessian writes their blocks.
  *   pairs:    host int32 [capacity][2], or NULL to query the count only;
  *   capacity: number of pairs `pairs` can hold; n_pairs: host, receives the number of pairs.
- * The pair list and its overlap tiles are built on the host and uploaded on the first call
- * (device memory owned by the problem).  Errors: CELESTE_ERR_STATE before bind;
- * CELESTE_ERR_INVALID_ARG when capacity is too small or n_pairs is NULL. */
+ * Host only (no device memory, usable before bind): the pair list and the overlap tiles are built
+ * from the layout on the first call and kept on the problem; the first device call uploads them.
+ * Errors: CELESTE_ERR_INVALID_ARG when capacity is too small or n_pairs is NULL. */
 int celeste_joint_pairs(celeste_problem* p, int32_t* pairs, int64_t capacity, int64_t* n_pairs);
 
 /* Cross-source Hessian blocks of J at theta, one per pair of celeste_joint_pairs:

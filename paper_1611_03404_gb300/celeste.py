@@ -194,12 +194,7 @@ class Problem:
 
     def joint_pairs(self):
         """[n_pairs, 2] int32 (host numpy): source pairs s < t whose windows overlap."""
-        n = ctypes.c_int64(0)
-        _check(lib().celeste_joint_pairs(self.handle, None, ctypes.c_int64(0), ctypes.byref(n)))
-        out = np.zeros((max(n.value, 1), 2), dtype=np.int32)
-        _check(lib().celeste_joint_pairs(self.handle, out.ctypes.data_as(ctypes.c_void_p), ctypes.c_int64(n.value),
-                                         ctypes.byref(n)))
-        return out[:n.value]
+        return _joint_pairs(self.handle)
 
     def joint_newton(self, theta, max_iter=50, ftol=1e-8, gtol=1e-10, delta_max=1e4, eta=0.1, delta_min=1e-12,
                      max_cg=100, stream=None):
@@ -308,6 +303,15 @@ def tr_solve_batch(B, g, delta, stream=None):
     return p, pred, hard
 
 
+def _joint_pairs(handle):
+    n = ctypes.c_int64(0)
+    _check(lib().celeste_joint_pairs(handle, None, ctypes.c_int64(0), ctypes.byref(n)))
+    out = np.zeros((max(n.value, 1), 2), dtype=np.int32)
+    _check(lib().celeste_joint_pairs(handle, out.ctypes.data_as(ctypes.c_void_p), ctypes.c_int64(n.value),
+                                     ctypes.byref(n)))
+    return out[:n.value]
+
+
 class HostProblem:
     """Layout-only handle (no device memory): validation and counts, usable without a GPU."""
 
@@ -350,6 +354,10 @@ class HostProblem:
 
     def workspace_bytes(self):
         return lib().celeste_problem_workspace_bytes(self.handle)
+
+    def joint_pairs(self):
+        """[n_pairs, 2] int32: source pairs s < t whose windows overlap (host only)."""
+        return _joint_pairs(self.handle)
 
     def __del__(self):
         try:

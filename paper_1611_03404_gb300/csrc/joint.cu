@@ -75,9 +75,10 @@ static JointDev joint_view(const celeste_problem* p) {
 }
 
 // Overlap items of every pair of patches that share an image and whose windows intersect, grouped
-// by source pair; tiles of at most JT_PIX pixels over each rectangle (row-major).
-static int joint_build(celeste_problem* p) {
-  if (p->joint_built) return CELESTE_OK;
+// by source pair; tiles of at most JT_PIX pixels over each rectangle (row-major).  Host only: the
+// lists are kept on the problem (flat int records) until the first device use uploads them.
+static void joint_host(celeste_problem* p) {
+  if (p->joint_host_built) return;
   struct Raw {
     int s, t;
     JointItem it;
@@ -114,27 +115,42 @@ static int joint_build(celeste_problem* p) {
     items.push_back(it);
   }
   pair_items.push_back((int)items.size());
-  const int n_pairs = (int)pairs.size() / 2;
-  const JointLayout L = joint_layout((int)items.size(), (int)tiles.size(), n_pairs);
+  static_assert(sizeof(JointItem) == 8 * sizeof(int) && sizeof(JointTile) == 4 * sizeof(int), "flat records");
+  p->joint_items_h.resize(8 * items.size());
+  p->joint_tiles_h.resize(4 * tiles.size());
+  if (!items.empty()) std::memcpy(p->joint_items_h.data(), items.data(), sizeof(JointItem) * items.size());
+  if (!tiles.empty()) std::memcpy(p->joint_tiles_h.data(), tiles.data(), sizeof(JointTile) * tiles.size());
+  p->joint_pair_items_h = pair_items;
+  p->joint_pairs = pairs;
+  p->joint_n_items = (int)items.size();
+  p->joint_n_tiles = (int)tiles.size();
+  p->joint_host_built = true;
+}
+
+// The host lists uploaded into one device allocation owned by the problem (first use).
+static int joint_build(celeste_problem* p) {
+  joint_host(p);
+  if (p->joint_built) return CELESTE_OK;
+  const int n_pairs = (int)p->joint_pairs.size() / 2;
+  const JointLayout L = joint_layout(p->joint_n_items, p->joint_n_tiles, n_pairs);
   void* dev = nullptr;
   cudaError_t e = cudaMalloc(&dev, L.total);
   if (e != cudaSuccess) return cuda_fail(e, "joint buffers");
   char* b = static_cast<char*>(dev);
-  if (!items.empty()) e = cudaMemcpy(b + L.items, items.data(), sizeof(JointItem) * items.size(), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess && !tiles.empty())
-    e = cudaMemcpy(b + L.tiles, tiles.data(), sizeof(JointTile) * tiles.size(), cudaMemcpyHostToDevice);
+  if (p->joint_n_items)
+    e = cudaMemcpy(b + L.items, p->joint_items_h.data(), sizeof(int) * p->joint_items_h.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && p->joint_n_tiles)
+    e = cudaMemcpy(b + L.tiles, p->joint_tiles_h.data(), sizeof(int) * p->joint_tiles_h.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
-    e = cudaMemcpy(b + L.pair_items, pair_items.data(), sizeof(int) * pair_items.size(), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess && !pairs.empty())
-    e = cudaMemcpy(b + L.pairs, pairs.data(), sizeof(int) * pairs.size(), cudaMemcpyHostToDevice);
+    e = cudaMemcpy(b + L.pair_items, p->joint_pair_items_h.data(), sizeof(int) * p->joint_pair_items_h.size(),
+                   cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && n_pairs)
+    e = cudaMemcpy(b + L.pairs, p->joint_pairs.data(), sizeof(int) * p->joint_pairs.size(), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
     cudaFree(dev);
     return cuda_fail(e, "joint upload");
   }
   p->joint_dev = dev;
-  p->joint_pairs = pairs;
-  p->joint_n_items = (int)items.size();
-  p->joint_n_tiles = (int)tiles.size();
   p->joint_built = true;
   return CELESTE_OK;
 }
@@ -750,10 +766,8 @@ using namespace celeste;
 
 extern "C" int celeste_joint_pairs(celeste_problem* p, int32_t* pairs, int64_t capacity, int64_t* n_pairs) {
   if (!p) return fail(CELESTE_ERR_INVALID_ARG, "null problem");
-  if (!p->bound) return fail(CELESTE_ERR_STATE, "problem is not bound to a workspace");
   if (!n_pairs) return fail(CELESTE_ERR_INVALID_ARG, "null n_pairs");
-  const int rc = joint_build(p);
-  if (rc != CELESTE_OK) return rc;
+  joint_host(p);
   const int64_t n = (int64_t)p->joint_pairs.size() / 2;
   *n_pairs = n;
   if (!pairs) return CELESTE_OK;

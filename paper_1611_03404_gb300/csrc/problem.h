@@ -44,8 +44,9 @@ struct celeste_problem {
   bool background_ready = false;
   int background_mode = 0;                            // CELESTE_NBR_* of the last rendering
   // joint objective (built on first use): overlapping pairs, their overlap items and tiles
-  bool joint_built = false;
+  bool joint_host_built = false, joint_built = false;   // host lists; uploaded to joint_dev
   std::vector<int> joint_pairs;                       // [n_pairs][2] sources s < t
+  std::vector<int> joint_items_h, joint_tiles_h, joint_pair_items_h;   // flat int records
   int joint_n_items = 0, joint_n_tiles = 0;
   void* joint_dev = nullptr;                          // items, tiles, pair CSR, tile partials
   void* jn_dev = nullptr;                             // joint Newton state (built on first use)

@@ -121,3 +121,24 @@ def test_hessian_mode_validation(pkg):
     for mode, tile in ((3, 128), (-1, 128), (pkg.HESS_TF32, 256), (pkg.HESS_BF16X3, 512)):
         with pytest.raises(pkg.CelesteError, match="invalid argument"):
             pkg.HostProblem(sc, tile_pixels=tile, hessian_mode=mode)
+
+
+@pytest.mark.parametrize("seed,kw", [(11, dict(n_sources=3, n_images=3)),
+                                     (3, dict(n_sources=5, n_images=2, H=40, W=44, radius=(6, 12))),
+                                     (21, dict(n_sources=8, n_images=3, H=60, W=64, radius=(3, 12)))])
+def test_joint_pairs_match_the_oracle_geometry(pkg, seed, kw):
+    """The library's overlapping source pairs (host layout, no GPU) equal the oracle's."""
+    from oracle import celeste_oracle as O
+    from oracle import joint_oracle as JO
+    sc = synth.tiny(seed=seed, **kw)
+    got = [tuple(int(v) for v in p) for p in pkg.HostProblem(sc, tile_pixels=128).joint_pairs()]
+    assert got == JO.overlapping_pairs(O.Oracle(sc))
+
+
+def test_joint_pairs_on_a_field(pkg):
+    from oracle import celeste_oracle as O
+    from oracle import joint_oracle as JO
+    sc = synth.field(seed=1622, W=768, H=560, n_sources=200)
+    got = [tuple(int(v) for v in p) for p in pkg.HostProblem(sc, tile_pixels=128).joint_pairs()]
+    ref = JO.overlapping_pairs(O.Oracle(sc))
+    assert got == ref and len(ref) > 20
