@@ -568,7 +568,7 @@ __global__ void __launch_bounds__(32 * JN_WARPS) jn_cg_init_kernel(JNDev J) {
 // Fixed-order sums over the sources of part[q] (one block).
 __device__ inline double jn_block_sum(const double* __restrict__ v, int n, bool take_max) {
   __shared__ double red[256];
-  double a = take_max ? 0.0 : 0.0;
+  double a = 0.0;   // (the maxima taken here are of non-negative values)
   for (int i = threadIdx.x; i < n; i += blockDim.x) a = take_max ? fmax(a, v[i]) : a + v[i];
   red[threadIdx.x] = a;
   __syncthreads();

@@ -142,3 +142,9 @@ def test_joint_pairs_on_a_field(pkg):
     got = [tuple(int(v) for v in p) for p in pkg.HostProblem(sc, tile_pixels=128).joint_pairs()]
     ref = JO.overlapping_pairs(O.Oracle(sc))
     assert got == ref and len(ref) > 20
+
+
+def test_joint_pairs_empty_when_no_window_overlaps(pkg):
+    sc = synth.tiny(seed=11, n_sources=3, n_images=3)
+    sc.radius = np.full_like(sc.radius, 1)
+    assert len(pkg.HostProblem(sc, tile_pixels=128).joint_pairs()) == 0
