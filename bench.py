@@ -269,9 +269,7 @@ def main():
         torch.cuda.synchronize()
         t = float(np.sum([a.elapsed_time(b) for a, b in evs])) / 1e3
         if world > 1:
-            tt = torch.tensor([t], device=dev, dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            t = float(tt)
+            t, _ = reduce_over_ranks(t, 0, dev)
         return t, out
 
     if args.warm_start:
@@ -286,9 +284,7 @@ def main():
         th_cat = theta.clone()
         conv_plain = int((st_cat == P.STATUS_CONVERGED).sum())
         if world > 1:
-            c = torch.tensor([conv_plain], device=dev, dtype=torch.float64)
-            dist.all_reduce(c, op=dist.ReduceOp.SUM)
-            conv_plain_total = float(c)
+            _, conv_plain_total = reduce_over_ranks(0.0, conv_plain, dev)
         else:
             conv_plain_total = conv_plain
         plain = {"value": conv_plain_total / (t_plain / args.steps), "ms_per_step": 1e3 * t_plain / args.steps,
@@ -338,11 +334,7 @@ def main():
     step_ms = [a.elapsed_time(b) for a, b in ev]
     t_step = float(np.sum(step_ms)) / 1e3
     if world > 1:
-        t = torch.tensor([t_step], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        c = torch.tensor([conv], device=dev, dtype=torch.float64)
-        dist.all_reduce(c, op=dist.ReduceOp.SUM)
-        t_step, conv_total = float(t), float(c)
+        t_step, conv_total = reduce_over_ranks(t_step, conv, dev)
         dist.barrier()
     else:
         conv_total = conv
@@ -390,11 +382,7 @@ def main():
                 e_conv = int((out_status == P.STATUS_CONVERGED).sum())
         te = float(np.mean(e_times))
         if world > 1:
-            t = torch.tensor([te], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            c = torch.tensor([e_conv], device=dev, dtype=torch.float64)
-            dist.all_reduce(c, op=dist.ReduceOp.SUM)
-            te, e_conv = float(t), float(c)
+            te, e_conv = reduce_over_ranks(te, e_conv, dev)
         e2e = {"value": e_conv / te, "unit": "sources/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "ms_per_step": 1e3 * te}
 
@@ -473,6 +461,18 @@ def train_warm_start(args, P, dev, rank):
                  "loss_first_last": [hist[0], hist[-1]], "data_seconds": t_data, "train_seconds": t_train,
                  "train_pairs_per_s": x.shape[0] * args.ws_epochs / t_train,
                  "params_from_network": "type logit, log variances of the log fluxes and colours"}
+
+
+def reduce_over_ranks(t, count, dev):
+    """Whole-job figures from per-rank ones (every rank calls it): the slowest rank's time (max)
+    and the sum of the ranks' counts, so value = count / time covers all ranks' work."""
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([float(t)], device=dev, dtype=torch.float64)
+    cc = torch.tensor([float(count)], device=dev, dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    dist.all_reduce(cc, op=dist.ReduceOp.SUM)
+    return float(tt), float(cc)
 
 
 def joint_report(P, prob, theta0):
