@@ -213,3 +213,21 @@ def test_joint_newton_steihaug_reaches_the_exact_solve_maximum(scene, exact_join
     res = JO.joint_newton_steihaug(orc, scene.theta0)
     assert res["status"] == O.STATUS_CONVERGED
     assert abs(res["elbo"] - ref["elbo"]) <= 1e-6 * abs(ref["elbo"])
+
+
+def test_cross_blocks_match_finite_differences_of_the_gradient(joint):
+    # an independent route to the cross blocks: central differences of dJ/dtheta_s under moves
+    # of theta_t
+    orc, theta, _, _, H = joint
+    J = JO.joint_fn(orc)
+    grad = lambda th: torch.func.grad(J)(torch.as_tensor(th).clone()).numpy()
+    rng = np.random.default_rng(7)
+    for (s, t) in JO.overlapping_pairs(orc):
+        for j in rng.choice(27, 3, replace=False):
+            h = 1e-5
+            tp, tm = theta.copy(), theta.copy()
+            tp[t, j] += h
+            tm[t, j] -= h
+            fd = (grad(tp)[s] - grad(tm)[s]) / (2 * h)
+            ref = H[s, :, t, j]
+            assert np.abs(fd - ref).max() <= 1e-5 * max(np.abs(H[s, :, t, :]).max(), 1e-12), (s, t, j)
