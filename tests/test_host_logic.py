@@ -77,3 +77,18 @@ def test_block_coordinate_passes_and_residual():
         assert np.isclose(h["grad_max"], float(gap.max())) and np.isclose(h["grad_median"], float(gap.max(1).values.median()))
         assert h["converged"] == S and h["newton_iters_mean"] == 3.0
     assert hist[0]["max_change"] > hist[1]["max_change"] > hist[2]["max_change"]
+
+
+def test_clock_summary_reads_throttle_reasons():
+    import bench
+    cs = bench.ClockSampler(0)
+    assert cs.summary()["reasons"] == ["unsampled"]
+    na, act = "Not Active", "Active"
+    cs.rows = [["2070", "2070", "900.1", na, na, na, na],
+               ["1980", "2070", "1401.0", na, na, na, act],
+               ["2070", "2070", "1350.7", na, na, na, na]]
+    s = cs.summary()
+    assert s["sm_mhz"] == 2070.0 and s["sm_max_mhz"] == 2070.0 and s["samples"] == 3
+    assert s["reasons"] == ["sw_power_cap"]
+    cs.rows.append(["1410", "2070", "700.0", act, na, act, na])
+    assert bench.ClockSampler.summary(cs)["reasons"] == ["hw_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
