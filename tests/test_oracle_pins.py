@@ -167,6 +167,71 @@ def test_delta_method_error_is_second_order():
         assert abs(exact - approx) < cv2 * cv2
 
 
+def _sample_rate(orc, im, n, s, thetas, px, py, N, rng):
+    """N draws of F at pixels (px, py) of image n: sky + iota * sum over s and its neighbours of
+    l_b * f_type, the latents drawn from q (a, log r, colours), each source independently."""
+    F = np.full((N, len(px)), im.sky)
+    for t in [s] + orc.nbr[s][n]:
+        f0, f1 = O.profiles(torch.as_tensor(thetas[t]), im, px, py, orc.psf_for(t, n), orc.mix)
+        a, logr, c, _ = _sample_latents(rng, thetas[t], N)
+        lb = np.exp(logr + c @ synth.COLOR_MIX[im.band])
+        F += im.iota * lb[:, None] * np.where(a[:, None], f1.numpy()[None], f0.numpy()[None])
+    return F
+
+
+@pytest.mark.parametrize("regime", ["star", "uncertain_type"])
+def test_pixel_term_variance_correction_monte_carlo(tiny_scene, regime):
+    """The pixel term with Var[F] > 0 equals x E_q[log F] - E[F] - log x!, where E_q[log F] is
+    Monte Carlo over the model's own F (the latents drawn from q), within the delta method's
+    remainder and the Monte Carlo error.
+
+    The remainder bound is Taylor's theorem for log(1 + z), z = (F - E)/E:
+    log(1+z) = z - z^2/2 + z^3/3 + R with |R| <= z^4/(4 min(1, 1+z)^4).  With E[z] = 0 and
+    E[z^2] = V/E^2, E[log F] - (log E - V/(2E^2)) = E[z^3]/3 + E[R], bounded by the sample's
+    |mean z^3|/3 + mean |R| bound.  The scenes make V/(2E^2) more than twice that bound at the
+    pixels tested, so a wrong coefficient or sign of the variance term does not pass."""
+    orc = O.Oracle(tiny_scene)
+    s = next(s for s in range(tiny_scene.n_sources) if any(orc.nbr[s][n] for n in orc.nbr[s]))
+    n = next(n for n in orc.nbr[s] if orc.nbr[s][n])
+    thetas = tiny_scene.theta0.copy()
+    thetas[:, 7] = thetas[:, 9] = 5.0                 # bright: the source dominates the sky near its centre
+    thetas[:, 8] = thetas[:, 10] = math.log(0.04)
+    thetas[:, 15:19] = thetas[:, 23:27] = math.log(0.01)
+    thetas[:, 6] = -7.0 if regime == "star" else 0.0
+    data = orc._patch_data(s, thetas)
+    k = [r[0] for r in orc.rects[s]].index(n)
+    im, px, py, x, lgx, bE, bV, psf = data[k]
+    EG, EG2 = O.source_moments(torch.as_tensor(thetas[s]), im, px, py, psf, orc.mix)
+    E = im.sky + im.iota * (bE + EG)
+    V = im.iota ** 2 * (bV + EG2 - EG * EG)
+    cv2 = (V / (E * E)).numpy()
+    sel = torch.as_tensor(np.argsort(cv2)[::-1][:6].copy())      # the pixels where V/E^2 is largest
+    px, py, x, lgx, E, V = px[sel], py[sel], x[sel], lgx[sel], E[sel], V[sel]
+    assert (V / (E * E)).min() > 5e-3
+    rng = np.random.default_rng(17 if regime == "star" else 18)
+    N = 1_000_000
+    F = _sample_rate(orc, im, n, s, thetas, px, py, N, rng)
+    En = E.numpy()
+    z = F / En[None] - 1.0
+    # E[log F] - log E = E[log(1 + z)]; subtracting the sample mean of z (whose expectation is 0)
+    # removes the first-order Monte Carlo noise
+    d = np.log1p(z) - z
+    mc = d.mean(0)
+    se = d.std(0) / math.sqrt(N)
+    rem = np.abs((z ** 3).mean(0)) / 3.0 + (z ** 4 / (4.0 * np.minimum(1.0, 1.0 + z) ** 4)).mean(0)
+    delta_term = 0.5 * (V / (E * E)).numpy()
+    # the sample's own second moment sits within Monte Carlo error of the oracle's V / E^2
+    m2 = (z * z).mean(0)
+    assert np.all(np.abs(m2 - 2.0 * delta_term) < 5 * (z * z).std(0) / math.sqrt(N))
+    # E[log F] by Monte Carlo vs the delta method
+    got = O.pixel_term(x, E, V, lgx).numpy()
+    ref = x.numpy() * (np.log(En) + mc) - En - lgx.numpy()
+    tol = x.numpy() * (rem + 5 * se)
+    assert np.all(np.abs(got - ref) <= tol), (got - ref, tol)
+    # the test resolves the variance term: it is more than twice the tolerance it is held to
+    assert np.all(x.numpy() * delta_term > 2.0 * tol)
+
+
 def test_rate_moments_monte_carlo(tiny_scene):
     """Per-pixel E[F] and Var[F] (target + neighbours, sky, calibration) equal Monte Carlo of the model."""
     orc = O.Oracle(tiny_scene)
