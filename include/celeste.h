@@ -95,10 +95,12 @@ typedef struct {
  *   tile_pixels: pixels per work tile (128, 256, 512 or 1024; 0 = default 128).
  *   hessian_mode: how the pixel kernel forms the Hessian's Jacobian cross-product
  *           sum_m Y_m^T C_m Y_m (the per-tile SYRK; everything else is unchanged):
- *           CELESTE_HESS_FP32 (0) float32 FMAs; CELESTE_HESS_TF32 (1) tensor cores, TF32
- *           operands; CELESTE_HESS_BF16X3 (2) tensor cores, BF16 hi + lo split operands
- *           (hi*hi + hi*lo + lo*hi); float32 accumulation in all three.  Modes 1 and 2 need
- *           tile_pixels 128. */
+ *           CELESTE_HESS_FP32 (0) float32 FMAs; on the tensor cores (mma.sync, float32
+ *           accumulation): CELESTE_HESS_TF32 (1) TF32 operands; CELESTE_HESS_BF16X3 (2) BF16
+ *           hi + lo split operands, hi*hi + hi*lo + lo*hi; CELESTE_HESS_BF16X6 (3) BF16
+ *           hi + mid + lo split operands, the six products down to 2^-16 of the leading one;
+ *           CELESTE_HESS_TF32X3 (4) TF32 big + small split operands, big*big + big*small +
+ *           small*big.  Modes 1-4 need tile_pixels 128. */
 typedef struct {
   int32_t n_images;
   const celeste_image_desc* images;
@@ -112,7 +114,13 @@ typedef struct {
   int32_t hessian_mode;
 } celeste_problem_desc;
 
-enum { CELESTE_HESS_FP32 = 0, CELESTE_HESS_TF32 = 1, CELESTE_HESS_BF16X3 = 2 };
+enum {
+  CELESTE_HESS_FP32 = 0,
+  CELESTE_HESS_TF32 = 1,
+  CELESTE_HESS_BF16X3 = 2,
+  CELESTE_HESS_BF16X6 = 3,
+  CELESTE_HESS_TF32X3 = 4
+};
 
 typedef struct celeste_problem celeste_problem;
 
@@ -231,9 +239,29 @@ int celeste_joint_value(celeste_problem* p, const double* theta, double* J_out, 
  *   theta: device float64 [S][27].
  *   want:  OR of CELESTE_WANT_*; outputs not wanted may be NULL.
  *   elbo:  device float64 [S]; grad: device float64 [S][27]; hess: device float64 [S][27][27].
- * Pixel arithmetic is float32; the cross-pixel sums and the assembly are float64. */
+ * Pixel arithmetic is float32; the cross-pixel sums and the assembly are float64.
+ * Asynchronous: errors found on the device are not in the return value.  The call first clears
+ * the problem's timeout word; a pixel kernel whose bounded wait on a tile's bulk copies runs out
+ * sets it, leaves that CTA's remaining tiles unevaluated and writes NaN for the tile it waited
+ * on, so the outputs are undefined.  celeste_problem_check reports it. */
 int celeste_elbo_batch(celeste_problem* p, const double* theta, unsigned want,
                        double* elbo, double* grad, double* hess, celeste_stream_t stream);
+
+/* Waits for `stream` and reports what the device recorded since the problem's last evaluating
+ * call started (celeste_elbo_batch, celeste_elbo_batch_noalloc, celeste_newton_batch,
+ * celeste_covariance_batch, the joint calls), and since bind for the pixel counts:
+ *   CELESTE_ERR_TIMEOUT       a pixel kernel's bounded wait on its bulk copies ran out;
+ *   CELESTE_ERR_INVALID_ARG   an image holds negative or non-finite counts (found at bind);
+ *   CELESTE_OK                neither.
+ * Synchronous.  celeste_newton_batch and the joint calls return these codes themselves. */
+int celeste_problem_check(celeste_problem* p, celeste_stream_t stream);
+
+/* Budget, in SM clock cycles, of the pixel kernels' first wait on each tile's bulk copies
+ * (default ~2 s: 0 restores it).  A negative budget makes every such wait give up at once,
+ * without waiting: the timeout path runs (error word set, a full-budget wait for the copies
+ * already in flight so that none lands after the CTA exits, NaN tile sums, early exit) on a
+ * healthy device, which is how the tests exercise it.  Takes effect on the next call. */
+int celeste_problem_set_wait_budget(celeste_problem* p, long long cycles);
 
 /* Trust-region Newton on every source's subproblem, all sources in one batch.
  *   theta_inout: device float64 [S][27], start in, optimum out.
@@ -269,8 +297,8 @@ int celeste_tr_solve_batch(const double* B, const double* g, const double* delta
 
 /* Device-time accounting of the library's own kernels, for benchmarks.
  *   celeste_profile_start: reset and start recording.  While recording, every launch of the
- *     ELBO+gradient+Hessian pixel kernel and of the value-only pixel kernel is bracketed by CUDA
- *     events recorded on the stream it is launched on.
+ *     ELBO+gradient+Hessian pixel kernel, of the value-only pixel kernel and of the trust-region
+ *     step kernel is bracketed by CUDA events recorded on the stream it is launched on.
  *   celeste_profile_stop: stop recording, wait for the recorded events and fill *out.
  * Not part of the numerical path; the counters cost one atomic per pixel-kernel CTA. */
 typedef struct {
@@ -281,24 +309,39 @@ typedef struct {
   int64_t value_pixels;       /* pixel evaluations with value only */
   int64_t kernel_launches;    /* every kernel launched by the library while recording */
   int64_t newton_iterations;  /* trust-region iterations run by celeste_newton_batch */
+  double tr_ms;               /* summed duration of trust-region step launches (celeste_newton_batch) */
+  int64_t tr_launches;
 } celeste_profile_stats;
 
 int celeste_profile_start(celeste_problem* p);
 int celeste_profile_stop(celeste_problem* p, celeste_profile_stats* out);
 
+/* Measured rate of one arithmetic pipe of the current device, the denominators of the benchmark's
+ * rooflines (not part of the method):
+ *   kind 0: FP32 fused multiply-add, in flop/s (2 per FMA) - the pixel kernels' bound;
+ *   kind 1: the special-function unit's base-2 exponential (ex2.approx), in operations/s;
+ *   kind 2: FP64 fused multiply-add, in flop/s - the trust-region step's pipe.
+ * Runs independent FMA (or ex2) chains on every SM, grown until a launch lasts ~25 ms, and reports
+ * the best of three launches timed by CUDA events on `stream`; *seconds (may be NULL) gets that
+ * launch's duration.  Synchronous; allocates and frees a few MB of device memory. */
+int celeste_measure_peak(int kind, double* ops_per_s, double* seconds, celeste_stream_t stream);
+
 /* The same evaluation as celeste_elbo_batch with want = ELBO | GRAD | HESS, for callers that may
  * not allocate device memory when they evaluate (a pre-sized arena, an allocator owned by another
  * framework, a request path that must not allocate).  The call allocates nothing: the kernels'
  * scratch (per-patch tables, per-pixel source moments, per-tile partial sums, per-source flags and
- * brightness constants, worklists, counters) lives in one fixed 8 MiB device array inside this library, which every GPU that loads
- * the library keeps until the process exits.
+ * brightness constants, worklists) lives in one fixed 8 MiB device array inside this library,
+ * which every GPU that loads the library keeps until the process exits.
  * The paper has no counterpart; it is a deployment variant of the evaluation above.
  *   p must be bound and have its background rendered; theta, elbo, grad, hess as in
  *   celeste_elbo_batch (all four required).
  *   Limit: 432 * n_tiles, 4 * n_sources, 6880 * n_patches, 8 * n_pixels,
  *   4 * (n_tiles + n_patches + n_sources) and 340 * n_sources bytes, each rounded up to 256, plus
- *   512 must fit in 8 MiB (e.g. ~1000 patches of 17 x 17 pixels); larger problems get
+ *   256 must fit in 8 MiB (e.g. ~1000 patches of 17 x 17 pixels); larger problems get
  *   CELESTE_ERR_INVALID_ARG before any launch.
+ *   The error words and the profiling counters stay in the bound workspace: the call clears the
+ *   timeout word first, a timed-out bulk-copy wait sets it there (celeste_problem_check reports
+ *   it), and celeste_profile_start/stop count this call's pixel-kernel launches and pixels.
  *   The first call on a device looks up the array's device address with that device current;
  *   make that first call before any stream capture.
  *   Every call shares the one array: calls that overlap on the GPU (different streams, threads

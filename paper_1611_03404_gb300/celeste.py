@@ -15,7 +15,7 @@ from . import build as _build
 NPARAM = 27
 WANT_ELBO, WANT_GRAD, WANT_HESS = 1, 2, 4
 STATUS_CONVERGED, STATUS_MAX_ITER, STATUS_NONFINITE, STATUS_RADIUS_COLLAPSE = 0, 1, 2, 3
-HESS_FP32, HESS_TF32, HESS_BF16X3 = 0, 1, 2
+HESS_FP32, HESS_TF32, HESS_BF16X3, HESS_BF16X6, HESS_TF32X3 = 0, 1, 2, 3, 4
 NBR_FULL, NBR_WINDOW = 0, 1
 
 
@@ -47,7 +47,8 @@ class NewtonOpts(ctypes.Structure):
 class ProfileStats(ctypes.Structure):
     _fields_ = [("full_ms", ctypes.c_double), ("value_ms", ctypes.c_double), ("full_launches", ctypes.c_int64),
                 ("value_launches", ctypes.c_int64), ("full_pixels", ctypes.c_int64), ("value_pixels", ctypes.c_int64),
-                ("kernel_launches", ctypes.c_int64), ("newton_iterations", ctypes.c_int64)]
+                ("kernel_launches", ctypes.c_int64), ("newton_iterations", ctypes.c_int64),
+                ("tr_ms", ctypes.c_double), ("tr_launches", ctypes.c_int64)]
 
 
 EXPORTED = ["celeste_problem_create", "celeste_problem_workspace_bytes", "celeste_problem_counts",
@@ -57,7 +58,8 @@ EXPORTED = ["celeste_problem_create", "celeste_problem_workspace_bytes", "celest
             "celeste_cnn_workspace_bytes", "celeste_cnn_init", "celeste_cnn_forward", "celeste_cnn_backward",
             "celeste_cnn_mse", "celeste_cnn_adamw", "celeste_extract_patches", "celeste_covariance_batch",
             "celeste_render_background_mode", "celeste_joint_pairs", "celeste_joint_cross_hessian",
-            "celeste_joint_newton", "celeste_joint_value"]
+            "celeste_joint_newton", "celeste_joint_value", "celeste_problem_check", "celeste_problem_set_wait_budget",
+            "celeste_measure_peak"]
 
 
 def load_library(path=None):
@@ -95,6 +97,10 @@ def load_library(path=None):
         "celeste_joint_pairs": (ctypes.c_int, [vp, dp, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
         "celeste_joint_cross_hessian": (ctypes.c_int, [vp, dp, dp, vp]),
         "celeste_joint_value": (ctypes.c_int, [vp, dp, ctypes.POINTER(ctypes.c_double), vp]),
+        "celeste_problem_check": (ctypes.c_int, [vp, vp]),
+        "celeste_problem_set_wait_budget": (ctypes.c_int, [vp, ctypes.c_longlong]),
+        "celeste_measure_peak": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                                ctypes.POINTER(ctypes.c_double), vp]),
         "celeste_joint_newton": (ctypes.c_int, [vp, dp, ctypes.POINTER(NewtonOpts), ctypes.c_int32,
                                                 ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                                                 ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32), vp]),
@@ -226,7 +232,9 @@ class Problem:
         _check(lib().celeste_joint_cross_hessian(self.handle, _ptr(theta), _ptr(out), _stream(stream)))
         return out[:n]
 
-    def elbo_batch(self, theta, want=WANT_ELBO | WANT_GRAD | WANT_HESS, stream=None):
+    def elbo_batch(self, theta, want=WANT_ELBO | WANT_GRAD | WANT_HESS, stream=None, check=True):
+        """(elbo, grad, hess) per source; with check (default) the stream is synchronised and a device-side
+        error (a bulk-copy wait that ran out) raises."""
         assert theta.dtype == torch.float64 and theta.is_contiguous() and theta.shape == (self.S, NPARAM)
         dev = theta.device
         elbo = torch.empty(self.S, dtype=torch.float64, device=dev) if want & WANT_ELBO else None
@@ -234,7 +242,18 @@ class Problem:
         hess = torch.empty(self.S, NPARAM, NPARAM, dtype=torch.float64, device=dev) if want & WANT_HESS else None
         _check(lib().celeste_elbo_batch(self.handle, _ptr(theta), ctypes.c_uint32(want), _ptr(elbo), _ptr(grad),
                                         _ptr(hess), _stream(stream)))
+        if check:
+            self.check(stream)
         return elbo, grad, hess
+
+    def check(self, stream=None):
+        """Waits for the stream; raises CelesteError if the device recorded a timeout or bad pixel counts."""
+        _check(lib().celeste_problem_check(self.handle, _stream(stream)))
+
+    def set_wait_budget(self, cycles):
+        """Budget (SM cycles) of the pixel kernels' first wait on a tile's bulk copies; 0 restores the default,
+        a negative value makes every such wait give up at once (the timeout path, for tests)."""
+        _check(lib().celeste_problem_set_wait_budget(self.handle, ctypes.c_longlong(int(cycles))))
 
     def newton_batch(self, theta, delta=None, max_iter=50, ftol=1e-8, gtol=1e-10, delta0=1.0, delta_max=1e4,
                      eta=0.1, delta_min=1e-12, graph_iters=4, stream=None):
@@ -301,6 +320,15 @@ def tr_solve_batch(B, g, delta, stream=None):
     _check(lib().celeste_tr_solve_batch(_ptr(B), _ptr(g), _ptr(delta), ctypes.c_int(n), _ptr(p), _ptr(pred), _ptr(hard),
                                         _stream(stream)))
     return p, pred, hard
+
+
+def measure_peak(kind, stream=None):
+    """Measured rate of one pipe of the current device: kind "fp32" (FMA flop/s), "ex2" (special-function
+    exponentials/s) or "fp64" (FMA flop/s).  Returns (rate, seconds of the timed launch)."""
+    k = {"fp32": 0, "ex2": 1, "fp64": 2}[kind]
+    rate, sec = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(lib().celeste_measure_peak(ctypes.c_int(k), ctypes.byref(rate), ctypes.byref(sec), _stream(stream)))
+    return rate.value, sec.value
 
 
 def _joint_pairs(handle):

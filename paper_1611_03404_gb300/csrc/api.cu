@@ -37,8 +37,9 @@ extern "C" int celeste_elbo_batch(celeste_problem* p, const double* theta, unsig
   cudaStream_t st = (cudaStream_t)stream;
   const bool full = (want & (CELESTE_WANT_GRAD | CELESTE_WANT_HESS)) != 0;
   const int flag = full ? FLAG_FULL : FLAG_VALUE;
-  cudaError_t e = launch_set_flags(p->dev, flag, st);
-  if (e != cudaSuccess) return cuda_fail(e, "set flags");
+  cudaError_t e = clear_timeout(p->dev, st);
+  if (e != cudaSuccess) return cuda_fail(e, "clear timeout word");
+  if ((e = launch_set_flags(p->dev, flag, st)) != cudaSuccess) return cuda_fail(e, "set flags");
   if ((e = launch_worklists(p->dev, flag, st)) != cudaSuccess) return cuda_fail(e, "worklists");
   if ((e = launch_tables(p->dev, theta, full, st)) != cudaSuccess) return cuda_fail(e, "tables");
   const int m0 = prof_mark(p, st);
@@ -51,5 +52,18 @@ extern "C" int celeste_elbo_batch(celeste_problem* p, const double* theta, unsig
                              (want & CELESTE_WANT_GRAD) ? grad : nullptr, (want & CELESTE_WANT_HESS) ? hess : nullptr, st)
            : launch_assemble_value(p->dev, theta, nullptr, elbo, st);
   if (e != cudaSuccess) return cuda_fail(e, "assemble kernel");
+  return CELESTE_OK;
+}
+
+extern "C" int celeste_problem_check(celeste_problem* p, celeste_stream_t stream) {
+  if (!p) return fail(CELESTE_ERR_INVALID_ARG, "null problem");
+  if (!p->bound) return fail(CELESTE_ERR_STATE, "problem is not bound to a workspace");
+  return device_errors(p->dev, (cudaStream_t)stream);
+}
+
+extern "C" int celeste_problem_set_wait_budget(celeste_problem* p, long long cycles) {
+  if (!p) return fail(CELESTE_ERR_INVALID_ARG, "null problem");
+  p->wait_budget = cycles;
+  p->dev.wait_budget = cycles ? cycles : WAIT_BUDGET_DEFAULT;
   return CELESTE_OK;
 }

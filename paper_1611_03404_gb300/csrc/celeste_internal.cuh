@@ -108,6 +108,8 @@ struct ProblemDev {
                                  // window-mode background and applied by the value kernel (joint objective)
   float2* refEV;                 // [n_pix] or null: each pixel's (E, V) at the joint solver's current point
   int S, n_patches, n_tiles, tile_pixels, n_sm, hmode;
+  long long wait_budget;         // SM cycles the pixel kernels' first wait on a tile's bulk copies may take
+                                 // (< 0: give up at once, the timeout path's test hook)
   double priors[5];
   double log_var_r, log_var_c, log_phi, log1m_phi, logit_phi;   // logs of the priors (host-computed)
   double inv_var_r, inv_var_c;   // reciprocals of the prior variances (host-computed)
@@ -154,6 +156,10 @@ constexpr int FLAG_VALUE = 2;    // evaluate value only (trial point)
 // Error words.
 constexpr int ERR_BAD_PIXEL = 0;
 constexpr int ERR_TIMEOUT = 1;
+
+// Budget of a bounded wait on a bulk copy: ~2 s of SM clock.  A copy of a few KB completes in
+// microseconds; a wait that runs out means the copy engine is stuck or the phase is wrong.
+constexpr long long WAIT_BUDGET_DEFAULT = 4000000000LL;
 
 // -------------------------------------------------------------------------------- small math
 __host__ __device__ inline double sigmoid_d(double x) {

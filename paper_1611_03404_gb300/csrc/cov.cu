@@ -84,6 +84,7 @@ extern "C" int celeste_covariance_batch(celeste_problem* p, const double* theta,
   double* g = reinterpret_cast<double*>(p->base + L.nt_g);
   double* H = reinterpret_cast<double*>(p->base + L.nt_H);
   cudaError_t e;
+  if ((e = clear_timeout(D, st)) != cudaSuccess) return cuda_fail(e, "clear timeout word");
   if ((e = launch_set_flags(D, FLAG_FULL, st)) != cudaSuccess) return cuda_fail(e, "set flags");
   if ((e = launch_worklists(D, FLAG_FULL, st)) != cudaSuccess) return cuda_fail(e, "worklists");
   if ((e = launch_full(D, theta, st)) != cudaSuccess) return cuda_fail(e, "pixel kernel");

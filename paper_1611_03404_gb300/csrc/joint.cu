@@ -977,6 +977,7 @@ extern "C" int celeste_joint_newton(celeste_problem* p, double* theta, const cel
   };
 
   double Jcur = 0.0;
+  JN_TRY(clear_timeout(Dj, st), "clear timeout word");
   if ((rc = value_eval(theta, nullptr, Jcur)) != CELESTE_OK) return rc;
   if ((rc = full_eval(theta)) != CELESTE_OK) return rc;
   // initial radius: the M-norm of the block-diagonal Newton step, sqrt(g^T M^-1 g)
@@ -1074,7 +1075,7 @@ extern "C" int celeste_joint_newton(celeste_problem* p, double* theta, const cel
   prof_count(p, (int)std::min(launches, (long long)1 << 30));
 #undef JN_TRY
 #undef JN_LAUNCHED
-  return CELESTE_OK;
+  return device_errors(Dj, st);
 }
 
 extern "C" int celeste_joint_value(celeste_problem* p, const double* theta, double* J_out, celeste_stream_t stream) {
@@ -1093,6 +1094,7 @@ extern "C" int celeste_joint_value(celeste_problem* p, const double* theta, doub
   double* vals = reinterpret_cast<double*>(b + L.vals);
   JNScalars* scd = reinterpret_cast<JNScalars*>(b + L.sc);
   cudaError_t e;
+  if ((e = clear_timeout(Dj, st)) != cudaSuccess) return cuda_fail(e, "clear timeout word");
   if ((e = launch_background(Dj, theta, 1, st)) != cudaSuccess) return cuda_fail(e, "background");
   if ((e = launch_set_flags(Dj, FLAG_VALUE, st)) != cudaSuccess) return cuda_fail(e, "set flags");
   if ((e = launch_worklists(Dj, FLAG_VALUE, st)) != cudaSuccess) return cuda_fail(e, "worklists");
@@ -1107,5 +1109,5 @@ extern "C" int celeste_joint_value(celeste_problem* p, const double* theta, doub
   p->background_mode = CELESTE_NBR_WINDOW;
   *J_out = h.dJ;
   prof_count(p, 8);
-  return CELESTE_OK;
+  return device_errors(Dj, st);
 }

@@ -209,12 +209,15 @@ __global__ void newton_finish_kernel(NewtonDev N, int32_t* iters, int32_t* statu
   if (elbo) elbo[s] = N.L[s];
 }
 
-// Kernels launched by one Newton iteration (newton_iteration below).
+// Kernels launched by one Newton iteration (newton_iteration below), and profiling events recorded
+// by it: value kernel (0, 1), full kernel (2, 3), subproblem step (4, 5).
 constexpr int NEWTON_KERNELS_PER_ITER = 12;
+constexpr int EV_PER_ITER = 6;
 
 // The launches of one Newton iteration: subproblem step, value at the trial point, accept/reject,
-// full evaluation at the accepted points.  ev (4 events, or null) brackets the value and the full
-// pixel kernels; inside a stream capture they become event-record nodes.
+// full evaluation at the accepted points.  ev (EV_PER_ITER events, or null) brackets the value and
+// the full pixel kernels and the subproblem step; inside a stream capture they become event-record
+// nodes.
 static cudaError_t newton_iteration(const ProblemDev& D, const NewtonDev& N, cudaStream_t st, cudaEvent_t* ev,
                                     bool capturing) {
   auto mark = [&](int k) -> cudaError_t {
@@ -223,8 +226,10 @@ static cudaError_t newton_iteration(const ProblemDev& D, const NewtonDev& N, cud
   };
   const int S = N.S;
   cudaError_t e;
+  if ((e = mark(4)) != cudaSuccess) return e;
   tr_step_kernel<<<(S + TR_WARPS - 1) / TR_WARPS, 32 * TR_WARPS, 0, st>>>(N, D.flags);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = mark(5)) != cudaSuccess) return e;
   if ((e = launch_worklists(D, FLAG_VALUE, st)) != cudaSuccess) return e;
   if ((e = launch_tables(D, N.trial, false, st)) != cudaSuccess) return e;
   if ((e = mark(0)) != cudaSuccess) return e;
@@ -283,7 +288,7 @@ extern "C" int celeste_newton_batch(celeste_problem* p, double* theta, const cel
   const bool prof = p->prof_on;
   cudaError_t e;
   // events bracketing each iteration's value and full evaluation (profiling only)
-  while (prof && p->iter_events.size() < (size_t)(4 * K)) {
+  while (prof && p->iter_events.size() < (size_t)(EV_PER_ITER * K)) {
     cudaEvent_t ev;
     if ((e = cudaEventCreate(&ev)) != cudaSuccess) return cuda_fail(e, "event create");
     p->iter_events.push_back(ev);
@@ -291,13 +296,17 @@ extern "C" int celeste_newton_batch(celeste_problem* p, double* theta, const cel
   auto read_events = [&](int n_iter) -> cudaError_t {
     if (!prof) return cudaSuccess;
     for (int k = 0; k < n_iter; ++k) {
-      float tv = 0.f, tf = 0.f;
-      cudaError_t e2 = cudaEventElapsedTime(&tv, p->iter_events[4 * k], p->iter_events[4 * k + 1]);
-      if (e2 == cudaSuccess) e2 = cudaEventElapsedTime(&tf, p->iter_events[4 * k + 2], p->iter_events[4 * k + 3]);
+      float tv = 0.f, tf = 0.f, tt = 0.f;
+      const cudaEvent_t* ev = &p->iter_events[EV_PER_ITER * k];
+      cudaError_t e2 = cudaEventElapsedTime(&tv, ev[0], ev[1]);
+      if (e2 == cudaSuccess) e2 = cudaEventElapsedTime(&tf, ev[2], ev[3]);
+      if (e2 == cudaSuccess) e2 = cudaEventElapsedTime(&tt, ev[4], ev[5]);
       if (e2 != cudaSuccess) return e2;
       p->prof_value_acc += tv;
       p->prof_full_acc += tf;
+      p->prof_tr_acc += tt;
     }
+    p->prof_tr_n += n_iter;
     p->prof_value_n += n_iter;
     p->prof_full_n += n_iter;
     p->prof_iters += n_iter;
@@ -310,6 +319,7 @@ extern "C" int celeste_newton_batch(celeste_problem* p, double* theta, const cel
     return e2;
   };
 
+  if ((e = clear_timeout(D, st)) != cudaSuccess) return cuda_fail(e, "clear timeout word");
   newton_init_kernel<<<(S + 127) / 128, 128, 0, st>>>(N, D.flags);
   if ((e = launch_worklists(D, FLAG_FULL, st)) != cudaSuccess) return cuda_fail(e, "worklists");
   {
@@ -328,11 +338,13 @@ extern "C" int celeste_newton_batch(celeste_problem* p, double* theta, const cel
     struct {
       NewtonDev N;
       const char* base;
+      long long wait_budget;
       int K, prof;
     } key;
     std::memset(&key, 0, sizeof(key));
     key.N = N;
     key.base = p->base;
+    key.wait_budget = D.wait_budget;
     key.K = K;
     key.prof = prof ? 1 : 0;
     const unsigned char* kb = reinterpret_cast<const unsigned char*>(&key);
@@ -351,7 +363,7 @@ extern "C" int celeste_newton_batch(celeste_problem* p, double* theta, const cel
         return cuda_fail(e, "begin capture");
       cudaError_t ec = cudaSuccess;
       for (int k = 0; k < K && ec == cudaSuccess; ++k)
-        ec = newton_iteration(D, N, cs, prof ? &p->iter_events[4 * k] : nullptr, true);
+        ec = newton_iteration(D, N, cs, prof ? &p->iter_events[EV_PER_ITER * k] : nullptr, true);
       cudaGraph_t graph = nullptr;
       e = cudaStreamEndCapture(cs, &graph);
       if (ec != cudaSuccess || e != cudaSuccess) {
@@ -384,12 +396,7 @@ extern "C" int celeste_newton_batch(celeste_problem* p, double* theta, const cel
   newton_finish_kernel<<<(S + 127) / 128, 128, 0, st>>>(N, iters_out, status_out, elbo_out);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "finish");
   prof_count(p, 4);
-  int err[4];
-  if ((e = cudaMemcpyAsync(err, D.err, sizeof(err), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return cuda_fail(e, "err read");
-  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "newton finish");
-  if (err[ERR_TIMEOUT]) return fail(CELESTE_ERR_TIMEOUT, "a pixel kernel's bulk copy did not complete in time");
-  if (err[ERR_BAD_PIXEL]) return fail(CELESTE_ERR_INVALID_ARG, "an image holds negative or non-finite counts");
-  return CELESTE_OK;
+  return device_errors(D, st);
 }
 
 extern "C" int celeste_tr_solve_batch(const double* B, const double* g, const double* delta, int n, double* p,

@@ -30,10 +30,10 @@ static void* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
 
 static size_t round256(size_t x) { return (x + 255) & ~size_t(255); }
 
-// Layout of the array for one problem: partial sums, flags, counters, tables, source moments,
-// worklists and their counts, per-source brightness constants.
+// Layout of the array for one problem: partial sums, flags, tables, source moments, worklists and
+// their counts, per-source brightness constants.
 struct NoallocLayout {
-  size_t partials, flags, counters, ptab, srcmom, wl, wl_count, snc, total;
+  size_t partials, flags, ptab, srcmom, wl, wl_count, snc, total;
 };
 static NoallocLayout noalloc_layout(const celeste_problem* p) {
   NoallocLayout L;
@@ -42,8 +42,6 @@ static NoallocLayout noalloc_layout(const celeste_problem* p) {
   o += round256(sizeof(float) * NACC * p->tiles.size());
   L.flags = o;
   o += round256(sizeof(int) * p->S);
-  L.counters = o;
-  o += round256(sizeof(unsigned long long) * 4);
   L.ptab = o;
   o += round256(sizeof(float) * TB_FLOATS * p->patches.size());
   L.srcmom = o;
@@ -98,22 +96,28 @@ extern "C" int celeste_elbo_batch_noalloc(celeste_problem* p, const double* thet
   ProblemDev D = p->dev;   // inputs from the bound problem, scratch from the fixed array
   D.partials = reinterpret_cast<float*>(b + NL.partials);
   D.flags = reinterpret_cast<int*>(b + NL.flags);
-  D.counters = reinterpret_cast<unsigned long long*>(b + NL.counters);
   D.ptab = reinterpret_cast<float*>(b + NL.ptab);
   D.srcmom = reinterpret_cast<float2*>(b + NL.srcmom);
   D.wl = reinterpret_cast<int*>(b + NL.wl);
   D.wl_count = reinterpret_cast<int*>(b + NL.wl_count);
   D.snc = reinterpret_cast<SNConst*>(b + NL.snc);
   cudaStream_t st = (cudaStream_t)stream;
-  // The array keeps the previous call's contents: the counters must start at zero; the flags,
-  // worklists, brightness constants, tables, source moments and partial sums are fully rewritten
-  // below before they are read.
-  cudaError_t e = cudaMemsetAsync(D.counters, 0, sizeof(unsigned long long) * 4, st);
-  if (e != cudaSuccess) return cuda_fail(e, "clear counters");
+  // The array keeps the previous call's contents: the flags, worklists, brightness constants,
+  // tables, source moments and partial sums are fully rewritten below before they are read.  The
+  // error words and the pixel counters stay in the bound workspace (a timed-out bulk-copy wait
+  // sets the workspace's timeout word, read by celeste_problem_check; the profiling counters count
+  // these pixels); the timeout word is cleared first, as in celeste_elbo_batch.
+  cudaError_t e = clear_timeout(D, st);
+  if (e != cudaSuccess) return cuda_fail(e, "clear timeout word");
   if ((e = launch_set_flags(D, FLAG_FULL, st)) != cudaSuccess) return cuda_fail(e, "set flags");
   if ((e = launch_worklists(D, FLAG_FULL, st)) != cudaSuccess) return cuda_fail(e, "worklists");
-  if ((e = launch_full(D, theta, st)) != cudaSuccess) return cuda_fail(e, "pixel kernel");
+  if ((e = launch_tables(D, theta, true, st)) != cudaSuccess) return cuda_fail(e, "tables");
+  const int m0 = prof_mark(p, st);
+  if ((e = launch_full_kernel(D, st)) != cudaSuccess) return cuda_fail(e, "pixel kernel");
+  const int m1 = prof_mark(p, st);
+  if (p->prof_on) p->prof_full.push_back({m0, m1});
   if ((e = launch_assemble(D, theta, true, elbo, grad, hess, st)) != cudaSuccess)
     return cuda_fail(e, "assemble kernel");
+  prof_count(p, 6);
   return CELESTE_OK;
 }

@@ -49,8 +49,6 @@ __host__ __device__ constexpr int tri_col(int q, int n) {
   return i + q;
 }
 
-constexpr long long WAIT_BUDGET = 4000000000LL;   // ~2 s of SM clock for the bulk copies
-
 // Warp reduce-scatter: on return lane l holds the warp sum of v[l] (v is clobbered).
 __device__ __forceinline__ float warp_reduce_scatter32(float (&v)[32], int lane) {
 #pragma unroll
@@ -78,18 +76,18 @@ __device__ __forceinline__ void issue_tile(const ProblemDev& P, int tile, float*
   bulk_copy(spix, P.pix + P.patches[t.patch].pix_off + t.start, pb, bar);
 }
 
-// All threads: wait (bounded) for a staged buffer.  On a timeout: error word, a last bounded wait
-// for these copies and for the other buffer's when they are in flight (so that no copy lands
-// after the CTA has left), and false on every thread.
+// All threads: wait (bounded by P.wait_budget) for a staged buffer.  On a timeout: error word, a
+// last wait with the full budget for these copies and for the other buffer's when they are in
+// flight (so that no copy lands after the CTA has left), and false on every thread.
 __device__ __forceinline__ bool wait_tile(const ProblemDev& P, uint64_t* bar, uint32_t phase, uint64_t* other,
                                           uint32_t other_phase, bool other_busy) {
-  bool ok = mbar_wait(bar, phase, WAIT_BUDGET);
+  bool ok = P.wait_budget >= 0 && mbar_wait(bar, phase, P.wait_budget);
   if (!ok) {
     atomicExch(P.err + ERR_TIMEOUT, 1);
-    mbar_wait(bar, phase, WAIT_BUDGET);
+    mbar_wait(bar, phase, WAIT_BUDGET_DEFAULT);
   }
   ok = __syncthreads_and(ok);
-  if (!ok && other_busy && threadIdx.x == 0) mbar_wait(other, other_phase, WAIT_BUDGET);
+  if (!ok && other_busy && threadIdx.x == 0) mbar_wait(other, other_phase, WAIT_BUDGET_DEFAULT);
   return ok;
 }
 
@@ -147,9 +145,16 @@ __device__ __forceinline__ void fill_chunk(float (&v)[32], const PixelCtx& c, st
 // warp and 32 pixels: M = A' B' with A' = [ta | ua] (11 x 64, padded to 16 rows) and
 // B' = [yE ; yV] (64 x 11, padded to 16 columns), K = 2 x 32 pixel terms.  Each lane stages its
 // pixel's 44 numbers in shared memory (A' rows and B'^T rows of 68 floats: conflict-free stores
-// and fragment loads), then the warp issues mma.sync: TF32 (m16n8k8, 8 k-steps x 2 n-tiles) or
-// BF16 with each operand split into hi + lo (m16n8k16, 4 k-steps x 2 n-tiles x 3 products);
-// float32 accumulators stay in registers across the tile's pixels.
+// and fragment loads), then the warp issues mma.sync with float32 accumulators kept in registers
+// across the tile's pixels.  Operand forms (HM):
+//   1  TF32 (m16n8k8, 8 k-steps x 2 n-tiles): 11 significant bits per operand;
+//   2  BF16 hi + lo (m16n8k16, 4 k-steps x 2 n-tiles x 3 products hi.hi + hi.lo + lo.hi): the
+//      dropped lo.lo and the split's remainder leave ~2^-17 of each product;
+//   3  BF16 hi + mid + lo (x 6 products: every pair whose bit weights reach 2^-16 of the product,
+//      hi.hi, hi.mid, mid.hi, hi.lo, lo.hi, mid.mid): ~2^-24 of each product, float32's own level;
+//   4  TF32 big + small (m16n8k8 x 3 products big.big + big.small + small.big): ~2^-21.
+// A split takes x -> hi = round(x), then the remainder's rounding, and so on; each remainder is
+// exact in float32, so the parts sum to x up to the last part's rounding.
 constexpr int SYRK_LD = 68;
 
 __device__ __forceinline__ uint32_t to_tf32(float x) {
@@ -184,12 +189,71 @@ __device__ __forceinline__ void split_bf16x2(const float* p, uint32_t& hi, uint3
   lo = *reinterpret_cast<const uint32_t*>(&l);
 }
 
+// Two consecutive floats split into bf16 hi, mid and lo pairs (each pair the lower k in the low half).
+__device__ __forceinline__ void split3_bf16x2(const float* p, uint32_t& hi, uint32_t& mid, uint32_t& lo) {
+  const float2 x = *reinterpret_cast<const float2*>(p);
+  const __nv_bfloat162 h = __floats2bfloat162_rn(x.x, x.y);
+  const float2 hf = __bfloat1622float2(h);
+  const float r0 = x.x - hf.x, r1 = x.y - hf.y;
+  const __nv_bfloat162 m = __floats2bfloat162_rn(r0, r1);
+  const float2 mf = __bfloat1622float2(m);
+  const __nv_bfloat162 l = __floats2bfloat162_rn(r0 - mf.x, r1 - mf.y);
+  hi = *reinterpret_cast<const uint32_t*>(&h);
+  mid = *reinterpret_cast<const uint32_t*>(&m);
+  lo = *reinterpret_cast<const uint32_t*>(&l);
+}
+
+// x split into TF32 big + small (the remainder x - big is exact in float32).
+__device__ __forceinline__ void split_tf32(float x, uint32_t& big, uint32_t& small) {
+  big = to_tf32(x);
+  small = to_tf32(x - __uint_as_float(big));
+}
+
 // D[nt] (16 x 8 tiles nt = 0, 1) += A' B' for this warp's staged 32 pixels.
 template <int HM>
 __device__ __forceinline__ void syrk_mma(const float (*As)[SYRK_LD], const float (*Bt)[SYRK_LD], float (&d)[2][4],
                                          int lane) {
   const int g = lane >> 2, t = lane & 3;
-  if constexpr (HM == 1) {
+  if constexpr (HM == 4) {
+#pragma unroll
+    for (int k0 = 0; k0 < 64; k0 += 8) {
+      uint32_t ab[4], as[4];
+      split_tf32(As[g][k0 + t], ab[0], as[0]);
+      split_tf32(As[g + 8][k0 + t], ab[1], as[1]);
+      split_tf32(As[g][k0 + t + 4], ab[2], as[2]);
+      split_tf32(As[g + 8][k0 + t + 4], ab[3], as[3]);
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt) {
+        uint32_t bb0, bs0, bb1, bs1;
+        split_tf32(Bt[8 * nt + g][k0 + t], bb0, bs0);
+        split_tf32(Bt[8 * nt + g][k0 + t + 4], bb1, bs1);
+        mma_tf32(d[nt], as[0], as[1], as[2], as[3], bb0, bb1);   // small terms first
+        mma_tf32(d[nt], ab[0], ab[1], ab[2], ab[3], bs0, bs1);
+        mma_tf32(d[nt], ab[0], ab[1], ab[2], ab[3], bb0, bb1);
+      }
+    }
+  } else if constexpr (HM == 3) {
+#pragma unroll
+    for (int k0 = 0; k0 < 64; k0 += 16) {
+      uint32_t ah[4], am[4], al[4];
+      split3_bf16x2(&As[g][k0 + 2 * t], ah[0], am[0], al[0]);
+      split3_bf16x2(&As[g + 8][k0 + 2 * t], ah[1], am[1], al[1]);
+      split3_bf16x2(&As[g][k0 + 2 * t + 8], ah[2], am[2], al[2]);
+      split3_bf16x2(&As[g + 8][k0 + 2 * t + 8], ah[3], am[3], al[3]);
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt) {
+        uint32_t bh0, bm0, bl0, bh1, bm1, bl1;
+        split3_bf16x2(&Bt[8 * nt + g][k0 + 2 * t], bh0, bm0, bl0);
+        split3_bf16x2(&Bt[8 * nt + g][k0 + 2 * t + 8], bh1, bm1, bl1);
+        mma_bf16(d[nt], al[0], al[1], al[2], al[3], bh0, bh1);   // small terms first
+        mma_bf16(d[nt], ah[0], ah[1], ah[2], ah[3], bl0, bl1);
+        mma_bf16(d[nt], am[0], am[1], am[2], am[3], bm0, bm1);
+        mma_bf16(d[nt], am[0], am[1], am[2], am[3], bh0, bh1);
+        mma_bf16(d[nt], ah[0], ah[1], ah[2], ah[3], bm0, bm1);
+        mma_bf16(d[nt], ah[0], ah[1], ah[2], ah[3], bh0, bh1);
+      }
+    }
+  } else if constexpr (HM == 1) {
 #pragma unroll
     for (int k0 = 0; k0 < 64; k0 += 8) {
       const uint32_t a0 = to_tf32(As[g][k0 + t]), a1 = to_tf32(As[g + 8][k0 + t]);
@@ -665,6 +729,14 @@ cudaError_t launch_full_kernel(const ProblemDev& P, cudaStream_t st) {
   }
   if (P.hmode == 2) {
     elbo_full_kernel<1, 2><<<g, BLOCK, 0, st>>>(P);
+    return cudaGetLastError();
+  }
+  if (P.hmode == 3) {
+    elbo_full_kernel<1, 3><<<g, BLOCK, 0, st>>>(P);
+    return cudaGetLastError();
+  }
+  if (P.hmode == 4) {
+    elbo_full_kernel<1, 4><<<g, BLOCK, 0, st>>>(P);
     return cudaGetLastError();
   }
   switch (P.tile_pixels) {

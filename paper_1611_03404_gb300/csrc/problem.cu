@@ -34,6 +34,20 @@ int cuda_fail(cudaError_t e, const char* what) {
   return fail(CELESTE_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
+cudaError_t clear_timeout(const ProblemDev& D, cudaStream_t st) {
+  return cudaMemsetAsync(D.err + ERR_TIMEOUT, 0, sizeof(int), st);
+}
+
+int device_errors(const ProblemDev& D, cudaStream_t st) {
+  int err[4];
+  cudaError_t e = cudaMemcpyAsync(err, D.err, sizeof(err), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "reading the device error words");
+  if (err[ERR_TIMEOUT]) return fail(CELESTE_ERR_TIMEOUT, "a pixel kernel's bulk copy did not complete in time");
+  if (err[ERR_BAD_PIXEL]) return fail(CELESTE_ERR_INVALID_ARG, "an image holds negative or non-finite counts");
+  return CELESTE_OK;
+}
+
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // ------------------------------------------------------------------------------ kernels
@@ -116,8 +130,8 @@ extern "C" int celeste_problem_create(const celeste_problem_desc* d, celeste_pro
   int tp = d->tile_pixels ? d->tile_pixels : 128;
   if (tp != 128 && tp != 256 && tp != 512 && tp != 1024)
     return fail(CELESTE_ERR_INVALID_ARG, "tile_pixels must be 128, 256, 512 or 1024");
-  if (d->hessian_mode < CELESTE_HESS_FP32 || d->hessian_mode > CELESTE_HESS_BF16X3)
-    return fail(CELESTE_ERR_INVALID_ARG, "hessian_mode must be 0, 1 or 2");
+  if (d->hessian_mode < CELESTE_HESS_FP32 || d->hessian_mode > CELESTE_HESS_TF32X3)
+    return fail(CELESTE_ERR_INVALID_ARG, "hessian_mode must be 0 to 4");
   if (d->hessian_mode != CELESTE_HESS_FP32 && tp != 128)
     return fail(CELESTE_ERR_INVALID_ARG, "tensor-core hessian modes need tile_pixels 128");
   for (int n = 0; n < d->n_images; ++n) {
@@ -386,6 +400,7 @@ extern "C" int celeste_problem_bind(celeste_problem* p, void* workspace, size_t 
   D.pweight = nullptr;   // set only on the joint solver's copies
   D.refEV = nullptr;
   D.n_sm = std::max(n_sm, 1);
+  D.wait_budget = p->wait_budget ? p->wait_budget : WAIT_BUDGET_DEFAULT;
   D.S = p->S;
   D.n_patches = (int)p->patches.size();
   D.n_tiles = (int)p->tiles.size();
@@ -450,8 +465,8 @@ extern "C" int celeste_profile_start(celeste_problem* p) {
   p->prof_value.clear();
   p->prof_launches = 0;
   p->prof_iters = 0;
-  p->prof_full_acc = p->prof_value_acc = 0.0;
-  p->prof_full_n = p->prof_value_n = 0;
+  p->prof_full_acc = p->prof_value_acc = p->prof_tr_acc = 0.0;
+  p->prof_full_n = p->prof_value_n = p->prof_tr_n = 0;
   return CELESTE_OK;
 }
 
@@ -485,6 +500,8 @@ extern "C" int celeste_profile_stop(celeste_problem* p, celeste_profile_stats* o
   out->value_pixels = (int64_t)c[1];
   out->kernel_launches = p->prof_launches;
   out->newton_iterations = p->prof_iters;
+  out->tr_ms = p->prof_tr_acc;
+  out->tr_launches = p->prof_tr_n;
   return CELESTE_OK;
 }
 

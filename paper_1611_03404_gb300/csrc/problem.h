@@ -17,6 +17,10 @@ struct WsLayout {
 
 int fail(int code, const char* fmt, ...);
 int cuda_fail(cudaError_t e, const char* what);
+// Clears the bound problem's timeout word on st (at the start of every call that stages tiles).
+cudaError_t clear_timeout(const ProblemDev& D, cudaStream_t st);
+// Waits for st, then maps the problem's error words to a return code (CELESTE_OK when clear).
+int device_errors(const ProblemDev& D, cudaStream_t st);
 
 }  // namespace celeste
 
@@ -24,6 +28,7 @@ struct celeste_problem {
   int S = 0;
   int tile_pixels = 256;
   int hessian_mode = 0;
+  long long wait_budget = 0;                          // celeste_problem_set_wait_budget (0: default)
   std::vector<celeste_image_desc> images;
   std::vector<double> u0;
   std::vector<int> radius;
@@ -57,12 +62,13 @@ struct celeste_problem {
   std::vector<std::pair<int, int>> prof_full, prof_value;
   long long prof_launches = 0, prof_iters = 0;
   double prof_full_acc = 0.0, prof_value_acc = 0.0;   // ms of event pairs already read back
-  long long prof_full_n = 0, prof_value_n = 0;
+  double prof_tr_acc = 0.0;                           // ms of trust-region step launches
+  long long prof_full_n = 0, prof_value_n = 0, prof_tr_n = 0;
   // Newton iterations as a CUDA graph (celeste_newton_batch), kept while its arguments repeat
   cudaStream_t capture_stream = nullptr;
   cudaGraphExec_t newton_exec = nullptr;
   std::vector<unsigned char> newton_key;
-  std::vector<cudaEvent_t> iter_events;               // 4 per captured iteration
+  std::vector<cudaEvent_t> iter_events;               // 6 per captured iteration
   ~celeste_problem();
 };
 

@@ -92,3 +92,44 @@ def test_clock_summary_reads_throttle_reasons():
     assert s["reasons"] == ["sw_power_cap"]
     cs.rows.append(["1410", "2070", "700.0", act, na, act, na])
     assert bench.ClockSampler.summary(cs)["reasons"] == ["hw_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+
+def test_bench_subscene_keeps_the_oracle_objective():
+    """The CPU baseline times the oracle on a sub-scene per sampled source (the source, every source
+    whose patch can overlap one of its patches, the images holding its patch centre); the source's
+    objective there is the one on the whole scene: same patches, same neighbours, same ELBO."""
+    import bench
+    import synth
+    from oracle import celeste_oracle as O
+    sc = synth.tiny(seed=31, n_sources=14, n_images=3, H=90, W=100, radius=(4, 12))
+    full = O.Oracle(sc)
+    for s in (0, 5, 9):
+        sub = bench.subscene(sc, s)
+        orc = O.Oracle(sub)
+        assert [r[1:] for r in orc.rects[0]] == [r[1:] for r in full.rects[s]]
+        mapped = {int(np.nonzero((sc.u0 == sub.u0[t]).all(1))[0][0]) for lst in orc.nbr[0].values() for t in lst}
+        assert mapped == {t for lst in full.nbr[s].values() for t in lst}
+        if full.rects[s]:
+            assert orc.elbo(0, sub.theta0[0], sub.theta0) == full.elbo(s, sc.theta0[s], sc.theta0)
+
+
+def test_bench_parses_the_driver_command_line():
+    import bench
+    a = bench.parse(["--gpus", "1", "--steps", "20", "--warmup", "5"])
+    assert a.workload == "mosaic" and a.hessian == "auto" and a.tile == 0 and a.warm_start
+    assert bench.workload_config(a)["workload"] == "mosaic_10x10_fields_100000src"
+    # the reference arm prints the same config as the GPU arm
+    b = bench.parse(["--impl", "reference", "--steps", "20", "--warmup", "5"])
+    assert bench.workload_config(a) == bench.workload_config(b)
+
+
+def test_bench_patch_pixel_count_matches_the_library_layout():
+    import bench
+    import synth
+    import paper_1611_03404_gb300 as P
+    import __graft_entry__
+    __graft_entry__.build()
+    for seed in (3, 4):
+        sc = synth.tiny(seed=seed, n_sources=30, n_images=3, H=80, W=90, radius=(3, 20))
+        c = P.HostProblem(sc, tile_pixels=128).counts()
+        assert bench.mean_patch_pixels(sc, chunk=7) == c["pixels"] / c["sources"]
