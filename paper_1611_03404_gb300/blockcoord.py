@@ -14,13 +14,15 @@ import torch
 from .celeste import NBR_FULL, WANT_GRAD
 
 
-def block_coordinate(prob, theta0, passes=2, mode=NBR_FULL, residual=False, **newton_opts):
+def block_coordinate(prob, theta0, passes=2, mode=NBR_FULL, residual=False, radius_world=None, **newton_opts):
     """Runs `passes` sweeps: the first with the neighbours fixed at theta0 (the catalog), each later
     one with the neighbours at the previous sweep's result.  Returns the final parameters and, per
     pass, the largest and mean absolute parameter change, the largest position change, the mean
     Newton iteration count and the number of converged sources; with `residual`, also the largest
     and median over sources of max_i |dL/dtheta_i| at the pass's result with every neighbour at its
-    new value (the joint objective's gradient when mode is NBR_WINDOW)."""
+    new value (the joint objective's gradient when mode is NBR_WINDOW).  With radius_world (a tensor
+    [S] of patch half-widths in world units) each pass also counts the sources whose position has
+    moved further than that from theta0: their light has left the patch their objective covers."""
     theta = theta0.clone().contiguous()
     history = []
     for k in range(passes):
@@ -33,7 +35,12 @@ def block_coordinate(prob, theta0, passes=2, mode=NBR_FULL, residual=False, **ne
                          "max_position_change": float(pos.max()),
                          "p99_position_change": float(torch.quantile(pos, 0.99)),
                          "newton_iters_mean": float(iters.double().mean()),
-                         "converged": int((status == 0).sum()), "elbo_sum": float(elbo.sum())})
+                         "converged": int((status == 0).sum()),
+                         "status_counts": [int((status == k).sum()) for k in range(4)],
+                         "left_window": None if radius_world is None else
+                         int(((theta[:, 0:2] - theta0[:, 0:2]).abs().max(1).values > radius_world).sum()),
+                         "elbo_sum_finite": float(elbo[torch.isfinite(elbo)].sum()),
+                         "nonfinite": int((~torch.isfinite(elbo)).sum())})
         if residual:
             prob.render_background(theta, mode=mode)
             _, g, _ = prob.elbo_batch(theta, want=WANT_GRAD)

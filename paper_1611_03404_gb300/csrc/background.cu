@@ -10,64 +10,73 @@
 namespace celeste {
 
 // ------------------------------------------------------------------------------ background
+// The neighbours' value tables come from the table kernel, run once per rendering on every patch
+// at nbr_theta (component means relative to the neighbour's own patch origin, precisions, weighted
+// normalisers, brightness constants): per tile only a shift of the means and float4 copies remain.
 constexpr int NB_CHUNK = 8;   // neighbours staged per pass
 
-__global__ void __launch_bounds__(BLOCK) background_kernel(ProblemDev P, const double* __restrict__ nbr_theta,
-                                                           int clip) {
-  __shared__ __align__(16) float tab[NB_CHUNK][NCOMP * 6];
-  __shared__ float cst[NB_CHUNK][10];   // A0 A1 C0 C1 Cx L10 L11 e
-  __shared__ int win[NB_CHUNK][4];      // neighbour's window relative to this patch: x0, y0, x1, y1 (exclusive)
+struct NbrStage {
+  float4 gal[NGAL];            // (P00, P01, P11) * (-1/2 log2 e), weighted normaliser
+  float4 star[NSTAR];
+  float mu[2 * CELESTE_NPSF];  // component means relative to the target patch's origin
+  float c[8];                  // A0 A1 C0 C1 Cx L10 L11 e
+  int win[4];                  // the neighbour's window relative to the target patch: x0, y0, x1, y1 (exclusive)
+};
+
+__global__ void __launch_bounds__(BLOCK) background_kernel(ProblemDev P, int clip) {
+  __shared__ NbrStage nbs[NB_CHUNK];
   const TileDev t = P.tiles[blockIdx.x];
   const PatchDev pt = P.patches[t.patch];
   const ImageDev im = P.images[pt.image];
   const int tid = threadIdx.x;
   const int nn = pt.nbr_end - pt.nbr_begin;
-  float bE[8], bV[8];
-  int cover[8];   // windows holding the pixel (its own and the neighbours'), window mode
   constexpr int MAXPPT = 8;
+  constexpr float NL2 = -0.5f * LOG2E;
+  float bE[MAXPPT], bV[MAXPPT];
+  int cover[MAXPPT];   // windows holding the pixel (its own and the neighbours'), window mode
   const int ppt = (t.count + BLOCK - 1) / BLOCK;
 #pragma unroll
   for (int r = 0; r < MAXPPT; ++r) {
     bE[r] = bV[r] = 0.f;
     cover[r] = 1;
   }
+  constexpr int ITEMS = NGAL + NSTAR + 2;
   for (int c0 = 0; c0 < nn; c0 += NB_CHUNK) {
     const int nc = min(NB_CHUNK, nn - c0);
     __syncthreads();
-    for (int w = tid; w < nc * (NCOMP + 1); w += BLOCK) {
-      const int q = w / (NCOMP + 1), c = w % (NCOMP + 1);
+    for (int w = tid; w < nc * ITEMS; w += BLOCK) {
+      const int q = w / ITEMS, e = w % ITEMS;
       const int np = P.nbr[pt.nbr_begin + c0 + q];
-      const PatchDev nb = P.patches[np];
-      const double* th = nbr_theta + (size_t)nb.source * NP;
-      if (c < NSTAR) {
-        PsfComp pc = load_psf(P.psf + (size_t)np * 18, c);
-        double px, py;
-        source_pixel_pos(im, th, pt.x0, pt.y0, px, py);
-        star_value_entry(pc, px, py, &tab[q][6 * c]);
-      } else if (c < NCOMP) {
-        const int g = c - NSTAR, k = g / NMIX, j = g % NMIX;
-        PsfComp pc = load_psf(P.psf + (size_t)np * 18, k);
-        double px, py;
-        source_pixel_pos(im, th, pt.x0, pt.y0, px, py);
-        GalShape gs;
-        galaxy_shape(th[3], th[4], th[5], gs);
-        const float A[4] = {(float)im.A[0], (float)im.A[1], (float)im.A[2], (float)im.A[3]};
-        gal_value_entry(pc, congruence(A, gs.S), P.nu[j], P.tau[j], px, py, &tab[q][6 * c]);
+      const float* tb = P.ptab + (size_t)np * TB_FLOATS;
+      NbrStage& S = nbs[q];
+      if (e < NGAL) {
+        const float4 g = *reinterpret_cast<const float4*>(tb + TB_GAL + e * GT_STRIDE);
+        S.gal[e] = make_float4(g.x * NL2, g.y * NL2, g.z * NL2, g.w);
+      } else if (e < NGAL + NSTAR) {
+        const float4 g = *reinterpret_cast<const float4*>(tb + TB_STAR + 4 * (e - NGAL));
+        S.star[e - NGAL] = make_float4(g.x, g.y * NL2, g.z * NL2, g.w * NL2);
+      } else if (e == NGAL + NSTAR) {
+        const PatchDev nb = P.patches[np];
+        const float dx = (float)(nb.x0 - pt.x0), dy = (float)(nb.y0 - pt.y0);
+#pragma unroll
+        for (int k = 0; k < CELESTE_NPSF; ++k) {
+          S.mu[2 * k] = tb[TB_MU + 2 * k] + dx;
+          S.mu[2 * k + 1] = tb[TB_MU + 2 * k + 1] + dy;
+        }
+        S.win[0] = nb.x0 - pt.x0;
+        S.win[1] = nb.y0 - pt.y0;
+        S.win[2] = nb.x0 - pt.x0 + nb.w;
+        S.win[3] = nb.y0 - pt.y0 + nb.h;
       } else {
-        win[q][0] = nb.x0 - pt.x0;
-        win[q][1] = nb.y0 - pt.y0;
-        win[q][2] = nb.x0 - pt.x0 + nb.w;
-        win[q][3] = nb.y0 - pt.y0 + nb.h;
-        SNConst sc;
-        sn_constants(th, im.band, im.iota, sc);
-        cst[q][0] = sc.A0;
-        cst[q][1] = sc.A1;
-        cst[q][2] = sc.C0;
-        cst[q][3] = sc.C1;
-        cst[q][4] = sc.Cx;
-        cst[q][5] = sc.L10;
-        cst[q][6] = sc.L11;
-        cst[q][7] = sc.e;
+        const SNConst& sc = *reinterpret_cast<const SNConst*>(tb + TB_SNC);
+        S.c[0] = sc.A0;
+        S.c[1] = sc.A1;
+        S.c[2] = sc.C0;
+        S.c[3] = sc.C1;
+        S.c[4] = sc.Cx;
+        S.c[5] = sc.L10;
+        S.c[6] = sc.L11;
+        S.c[7] = sc.e;
       }
     }
     __syncthreads();
@@ -78,21 +87,30 @@ __global__ void __launch_bounds__(BLOCK) background_kernel(ProblemDev P, const d
       const int row = idx / pt.w, col = idx - row * pt.w;
       const float fx = (float)col, fy = (float)row;
       for (int q = 0; q < nc; ++q) {
-        if (clip && (col < win[q][0] || col >= win[q][2] || row < win[q][1] || row >= win[q][3])) continue;
+        const NbrStage& S = nbs[q];
+        if (clip && (col < S.win[0] || col >= S.win[2] || row < S.win[1] || row >= S.win[3])) continue;
         cover[r] += 1;
         float f0 = 0.f, fE = 0.f, fD = 0.f;
 #pragma unroll
-        for (int c = 0; c < NSTAR; ++c) f0 += gauss_value(&tab[q][6 * c], fx, fy);
         for (int k = 0; k < CELESTE_NPSF; ++k) {
+          const float d0 = fx - S.mu[2 * k], d1 = fy - S.mu[2 * k + 1];
+          const float s0 = d0 * d0, s1 = 2.f * d0 * d1, s2 = d1 * d1;
+          const float4 st = S.star[k];
+          f0 += st.x * exp2f(st.y * s0 + st.z * s1 + st.w * s2);
 #pragma unroll
-          for (int j = 0; j < CELESTE_NEXP; ++j) fE += gauss_value(&tab[q][6 * (NSTAR + k * NMIX + j)], fx, fy);
-#pragma unroll
-          for (int j = CELESTE_NEXP; j < NMIX; ++j) fD += gauss_value(&tab[q][6 * (NSTAR + k * NMIX + j)], fx, fy);
+          for (int j = 0; j < NMIX; ++j) {
+            const float4 g = S.gal[k * NMIX + j];
+            const float v = g.w * exp2f(g.x * s0 + g.y * s1 + g.z * s2);
+            if (j < CELESTE_NEXP)
+              fE += v;
+            else
+              fD += v;
+          }
         }
-        const float f1 = fE + cst[q][7] * (fD - fE);
-        bE[r] += cst[q][0] * f0 + cst[q][1] * f1;
-        const float dx = cst[q][5] * f0 - cst[q][6] * f1;
-        bV[r] += cst[q][2] * f0 * f0 + cst[q][3] * f1 * f1 + cst[q][4] * dx * dx;
+        const float f1 = fE + S.c[7] * (fD - fE);
+        bE[r] += S.c[0] * f0 + S.c[1] * f1;
+        const float dx = S.c[5] * f0 - S.c[6] * f1;
+        bV[r] += S.c[2] * f0 * f0 + S.c[3] * f1 * f1 + S.c[4] * dx * dx;
       }
     }
   }
@@ -108,9 +126,15 @@ __global__ void __launch_bounds__(BLOCK) background_kernel(ProblemDev P, const d
   }
 }
 
+// Value tables of every patch at nbr_theta (all sources flagged; the flags, worklists and tables are
+// working state that every later evaluation rebuilds), then the background of every tile.
 cudaError_t launch_background(const ProblemDev& P, const double* nbr_theta, int clip, cudaStream_t st) {
   if (P.n_tiles == 0) return cudaSuccess;
-  background_kernel<<<P.n_tiles, BLOCK, 0, st>>>(P, nbr_theta, clip);
+  cudaError_t e = launch_set_flags(P, FLAG_VALUE, st);
+  if (e == cudaSuccess) e = launch_worklists(P, FLAG_VALUE, st);
+  if (e == cudaSuccess) e = launch_tables(P, nbr_theta, false, st);
+  if (e != cudaSuccess) return e;
+  background_kernel<<<P.n_tiles, BLOCK, 0, st>>>(P, clip);
   return cudaGetLastError();
 }
 

@@ -205,9 +205,9 @@ __device__ inline PsfComp load_psf(const float* psf_patch, int k) {
   return {q[0], q[1], q[2], {q[3], q[4], q[5]}};
 }
 
-// Brightness moments of a lognormal flux in band b for type i: log l_b ~ N(m, v),
-// m = r1 + a_b.c1, v = exp(rho) + (a_b^2).exp(gam); E[l] = exp(m + v/2), E[l^2] = exp(2m + 2v).
-// Brightness parameter indices of type t (r1, rho, c1 x4, gamma x4).
+// Brightness parameter indices of type t (r1, rho, c1 x4, gamma x4).  In band b the log flux of
+// type t is normal, log l_b ~ N(m, v) with m = r1 + a_b.c1 and v = exp(rho) + (a_b^2).exp(gam), so
+// E[l] = exp(m + v/2) and E[l^2] = exp(2m + 2v).
 __device__ inline int bvar(int type, int v) {
   if (v == 0) return type ? 9 : 7;
   if (v == 1) return type ? 10 : 8;
@@ -234,76 +234,18 @@ __host__ __device__ inline double color_coef(int band, int j) {
 __host__ __device__ inline void color_row(int band, double a[4]) {
   for (int j = 0; j < 4; ++j) a[j] = color_coef(band, j);
 }
-__host__ __device__ inline void lognormal_moments(const double* th, int type, int band, double& L1, double& L2,
-                                                  double* var_log = nullptr) {
-  const int r1 = type ? 9 : 7, rho = type ? 10 : 8, c1 = type ? 19 : 11, gam = type ? 23 : 15;
-  double a[4];
-  color_row(band, a);
-  double m = th[r1], v = exp(th[rho]);
-  for (int j = 0; j < 4; ++j) {
-    m += a[j] * th[c1 + j];
-    v += a[j] * a[j] * exp(th[gam + j]);
-  }
-  L1 = exp(m + 0.5 * v);
-  L2 = exp(2.0 * m + 2.0 * v);
-  if (var_log) *var_log = v;
-}
 
-__device__ inline void sn_constants(const double* th, int band, float iota, SNConst& c) {
-  double a1 = sigmoid_d(th[6]), a0 = sigmoid_d(-th[6]);
-  double L10, L20, L11, L21, v0, v1;
-  lognormal_moments(th, 0, band, L10, L20, &v0);
-  lognormal_moments(th, 1, band, L11, L21, &v1);
-  c.C0 = (float)(a0 * L10 * L10 * expm1(v0));
-  c.C1 = (float)(a1 * L11 * L11 * expm1(v1));
-  c.Cx = (float)(a0 * a1);
-  c.L10 = (float)L10;
-  c.L11 = (float)L11;
-  c.A0 = (float)(a0 * L10);
-  c.A1 = (float)(a1 * L11);
-  c.B0 = (float)(a0 * L20);
-  c.B1 = (float)(a1 * L21);
-  double aa = a0 * a1;
-  c.aE0 = (float)(aa * L10);
-  c.aE1 = (float)(aa * L11);
-  c.aV0 = (float)(aa * L20);
-  c.aV1 = (float)(aa * L21);
-  c.iota = iota;
-  double e = sigmoid_d(th[2]), ee = e * sigmoid_d(-th[2]);
-  c.e = (float)e;
-  c.e1 = (float)ee;
-  c.e2 = (float)(ee * (1.0 - 2.0 * e));
-}
+// float64 -> float32 saturating at the float32 maximum (NaN stays NaN).  A brightness moment can
+// exceed float32's range where a type's probability has all but vanished: its brightness
+// parameters then barely move the objective, and Newton may carry their variance far out.  An
+// infinite constant would turn the profile's zeros far from the source into inf * 0 = NaN.
+__host__ __device__ inline float sat_f(double x) { return (float)(x > 3.4028234663852886e38 ? 3.4028234663852886e38 : x); }
 
 // Galaxy world covariance Sigma_g = scale^2 R diag(1, axis^2) R^T and its first/second
 // derivatives w.r.t. (logit axis, angle, log scale); pairs ordered 00 01 02 11 12 22.
 struct GalShape {
   Sym2 S, d[3], d2[6];
 };
-__device__ inline void galaxy_shape(double eta, double phi, double kappa, GalShape& g) {
-  float e = (float)sigmoid_d(eta), e2 = e * e;
-  float s2 = (float)exp(2.0 * kappa);
-  float c = (float)cos(phi), sn = (float)sin(phi);
-  Sym2 A = {c * c, c * sn, sn * sn};
-  Sym2 B = {sn * sn, -c * sn, c * c};
-  Sym2 dA = {-2.f * c * sn, c * c - sn * sn, 2.f * c * sn};
-  Sym2 d2A = {-2.f * (c * c - sn * sn), -4.f * c * sn, 2.f * (c * c - sn * sn)};
-  const float em = (float)sigmoid_d(-eta);
-  float de2 = 2.f * e2 * em;
-  float d2e2 = 2.f * e2 * em * (2.f - 3.f * e);
-  g.S = {s2 * (A.a + e2 * B.a), s2 * (A.b + e2 * B.b), s2 * (A.c + e2 * B.c)};
-  g.d[0] = {s2 * de2 * B.a, s2 * de2 * B.b, s2 * de2 * B.c};
-  float k1 = s2 * em * (1.f + e);
-  g.d[1] = {k1 * dA.a, k1 * dA.b, k1 * dA.c};
-  g.d[2] = {2.f * g.S.a, 2.f * g.S.b, 2.f * g.S.c};
-  g.d2[0] = {s2 * d2e2 * B.a, s2 * d2e2 * B.b, s2 * d2e2 * B.c};
-  g.d2[1] = {-s2 * de2 * dA.a, -s2 * de2 * dA.b, -s2 * de2 * dA.c};
-  g.d2[2] = {2.f * g.d[0].a, 2.f * g.d[0].b, 2.f * g.d[0].c};
-  g.d2[3] = {k1 * d2A.a, k1 * d2A.b, k1 * d2A.c};
-  g.d2[4] = {2.f * g.d[1].a, 2.f * g.d[1].b, 2.f * g.d[1].c};
-  g.d2[5] = {4.f * g.S.a, 4.f * g.S.b, 4.f * g.S.c};
-}
-
 __device__ inline Sym2 inv2(const Sym2& S, float& logdet) {
   // det = a c - b^2 with the rounding of b^2 compensated (one FMA recovers its exact error)
   const float bb = S.b * S.b;
@@ -320,37 +262,6 @@ constexpr float LOG_2PI = 1.8378770664093453f;
 __device__ inline void source_pixel_pos(const ImageDev& im, const double* th, double ox, double oy, double& px, double& py) {
   px = im.A[0] * th[0] + im.A[1] * th[1] + im.o[0] - ox;
   py = im.A[2] * th[0] + im.A[3] * th[1] + im.o[1] - oy;
-}
-
-// Value-only table entry (mu, lw2, P) of star component k and galaxy component (k, j) for a source
-// at relative pixel position (px, py).  Used for neighbours and for trial points.
-__device__ inline void star_value_entry(const PsfComp& pc, double px, double py, float* out) {
-  float ld;
-  Sym2 P = inv2(pc.S, ld);
-  out[0] = (float)(px + pc.mx);
-  out[1] = (float)(py + pc.my);
-  out[2] = (logf(pc.w) - 0.5f * ld - LOG_2PI) * LOG2E;
-  out[3] = P.a;
-  out[4] = P.b;
-  out[5] = P.c;
-}
-__device__ inline void gal_value_entry(const PsfComp& pc, const Sym2& Spix, float nu, float tau, double px, double py,
-                                       float* out) {
-  Sym2 S = {tau * Spix.a + pc.S.a, tau * Spix.b + pc.S.b, tau * Spix.c + pc.S.c};
-  float ld;
-  Sym2 P = inv2(S, ld);
-  out[0] = (float)(px + pc.mx);
-  out[1] = (float)(py + pc.my);
-  out[2] = (logf(pc.w * nu) - 0.5f * ld - LOG_2PI) * LOG2E;
-  out[3] = P.a;
-  out[4] = P.b;
-  out[5] = P.c;
-}
-
-__device__ inline float gauss_value(const float* t, float dx, float dy) {
-  float d0 = dx - t[0], d1 = dy - t[1];
-  float q = t[3] * d0 * d0 + 2.f * t[4] * d0 * d1 + t[5] * d1 * d1;
-  return exp2f(fmaf(q, -0.5f * LOG2E, t[2]));
 }
 
 // Weight times Gaussian normaliser, w / (2 pi sqrt(det)): a few correctly rounded float32 steps

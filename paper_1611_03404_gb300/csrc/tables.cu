@@ -90,19 +90,19 @@ __global__ void source_const_kernel(ProblemDev P, const double* __restrict__ the
       const double a1 = sigmoid_d(th[6]), a0 = sigmoid_d(-th[6]), aa = a0 * a1;
       const double e = sigmoid_d(th[2]), ee = e * sigmoid_d(-th[2]);
       SNConst c;
-      c.C0 = (float)(a0 * L10 * L10 * em0);
-      c.C1 = (float)(a1 * L11 * L11 * em1);
+      c.C0 = sat_f(a0 * L10 * L10 * em0);
+      c.C1 = sat_f(a1 * L11 * L11 * em1);
       c.Cx = (float)aa;
-      c.L10 = (float)L10;
-      c.L11 = (float)L11;
-      c.A0 = (float)(a0 * L10);
-      c.A1 = (float)(a1 * L11);
-      c.B0 = (float)(a0 * L20);
-      c.B1 = (float)(a1 * L21);
-      c.aE0 = (float)(aa * L10);
-      c.aE1 = (float)(aa * L11);
-      c.aV0 = (float)(aa * L20);
-      c.aV1 = (float)(aa * L21);
+      c.L10 = sat_f(L10);
+      c.L11 = sat_f(L11);
+      c.A0 = sat_f(a0 * L10);
+      c.A1 = sat_f(a1 * L11);
+      c.B0 = sat_f(a0 * L20);
+      c.B1 = sat_f(a1 * L21);
+      c.aE0 = sat_f(aa * L10);
+      c.aE1 = sat_f(aa * L11);
+      c.aV0 = sat_f(aa * L20);
+      c.aV1 = sat_f(aa * L21);
       c.iota = 0.f;
       c.e = (float)e;
       c.e1 = (float)ee;
