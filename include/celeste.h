@@ -128,7 +128,9 @@ typedef struct celeste_problem celeste_problem;
  * machine tolerance within 50 iterations).  Zero-initialised fields take the defaults shown. */
 typedef struct {
   int32_t max_iter;   /* 50 */
-  double ftol;        /* 1e-8: stop after an accepted step with |f_k - f_k+1| <= ftol |f_k+1| */
+  double ftol;        /* 1e-8: stop after an accepted step with |f_k - f_k+1| <= ftol |f_k+1|, when an
+                         interior (full Newton) step predicts a decrease <= ftol |f|, or when a
+                         rejected step had predicted a decrease <= ftol |f| */
   double gtol;        /* 1e-10: stop when max |grad| <= gtol */
   double delta0;      /* 1.0: initial radius (used where delta_inout[s] <= 0) */
   double delta_max;   /* 1e4 */
@@ -206,7 +208,8 @@ int celeste_joint_cross_hessian(celeste_problem* p, const double* theta, double*
 
 /* Trust-region Newton on the joint objective J over all sources at once (paper, concluding
  * section), with the per-source solve's rules (Nocedal & Wright Alg. 4.1: eta, the radius update
- * by 1/4 and 2, ftol on accepted changes and on the Newton decrement, gtol on max |grad|).  The
+ * by 1/4 and 2, ftol on accepted changes, on the Newton decrement and on the prediction of a
+ * rejected step, gtol on max |grad|).  The
  * subproblem is solved by preconditioned conjugate gradients with Steihaug's stopping rules
  * (Nocedal & Wright Alg. 7.2) over the block-sparse Hessian (celeste_elbo_batch's per-source
  * blocks in window mode and celeste_joint_cross_hessian's cross blocks); the preconditioner is

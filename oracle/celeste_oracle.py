@@ -350,8 +350,11 @@ def trust_region_newton(value, vgh, theta0, max_iter=50, delta0=1.0, delta_max=1
     """Maximise the ELBO by minimising f = -L with a trust region (Nocedal & Wright Alg. 4.1).
 
     Stops when max |grad| <= gtol, when an interior (full Newton) step predicts a decrease
-    <= ftol |f|, when an accepted step changes f by <= ftol |f|, when the radius falls below
-    delta_min, or after max_iter subproblem solves.  Returns dict(theta, elbo, iters, status)."""
+    <= ftol |f|, when an accepted step changes f by <= ftol |f|, when a rejected step had
+    predicted a decrease <= ftol |f| (the radius only shrinks after a rejection, so the model
+    promises no more than the tolerance from here: the evaluation's rounding floor has been
+    reached), when the radius falls below delta_min, or after max_iter subproblem solves.
+    Returns dict(theta, elbo, iters, status)."""
     th = theta0.copy()
     L, gL, HL = vgh(th)
     f, g, B = -L, -gL, -HL
@@ -376,6 +379,9 @@ def trust_region_newton(value, vgh, theta0, max_iter=50, delta0=1.0, delta_max=1
         rho = (f - f_new) / pred if pred > 0 else -1.0
         if not np.isfinite(f_new):
             rho = -1.0
+        if rho <= eta and pred <= ftol * abs(f):
+            status = STATUS_CONVERGED
+            break
         if rho < 0.25:
             delta = 0.25 * delta
         elif rho > 0.75 and pnorm >= (1.0 - 1e-9) * delta:

@@ -286,10 +286,11 @@ def steihaug(g, B, M, delta, max_cg):
 def joint_newton_steihaug(orc, theta0, max_iter=100, max_cg=100, ftol=1e-8, gtol=1e-10, delta_max=1e4, eta=0.1,
                           delta_min=1e-12):
     """Trust-region Newton on f = -J (Nocedal & Wright Alg. 4.1: acceptance eta, radius x1/4 below
-    rho = 1/4 and x2 above 3/4 on the boundary, ftol on accepted changes and on the Newton
-    decrement of a converged subproblem, gtol on max |grad|) with each subproblem solved by
-    `steihaug` in the norm of `preconditioner`'s blocks; the radius starts at the norm of the
-    block-diagonal Newton step, sqrt(g^T M^-1 g), and is capped at delta_max times that.
+    rho = 1/4 and x2 above 3/4 on the boundary, ftol on accepted changes, on the Newton decrement
+    of a converged subproblem and on the prediction of a rejected step, gtol on max |grad|) with
+    each subproblem solved by `steihaug` in the norm of `preconditioner`'s blocks; the radius
+    starts at the norm of the block-diagonal Newton step, sqrt(g^T M^-1 g), and is capped at
+    delta_max times that.
     Returns dict(theta, elbo = J, iters, status, cg_iters)."""
     J = joint_fn(orc)
     th = np.asarray(theta0, np.float64).copy()
@@ -333,6 +334,9 @@ def joint_newton_steihaug(orc, theta0, max_iter=100, max_cg=100, ftol=1e-8, gtol
         rho = dJ / pred if pred > 0 else -1.0
         if not np.isfinite(dJ):
             rho = -1.0
+        if rho <= eta and pred <= ftol * abs(f):
+            status = STATUS_CONVERGED      # a rejected step that promised no more than ftol |f|
+            break
         if rho < 0.25:
             delta *= 0.25
         elif rho > 0.75 and boundary:

@@ -166,32 +166,44 @@ __host__ __device__ inline double sigmoid_d(double x) {
   return x >= 0 ? 1.0 / (1.0 + exp(-x)) : exp(x) / (1.0 + exp(x));
 }
 
-// Symmetric 2x2 stored as (00, 01, 11).
-struct Sym2 {
-  float a, b, c;
+// Symmetric 2x2 stored as (00, 01, 11), and a general 2x2, in float (the kernels' arithmetic) or
+// double (the table kernel's path for ill-conditioned galaxy components).
+template <class T>
+struct Sym2T {
+  T a, b, c;
 };
-struct Mat2 {
-  float m00, m01, m10, m11;
+template <class T>
+struct Mat2T {
+  T m00, m01, m10, m11;
 };
+using Sym2 = Sym2T<float>;
+using Mat2 = Mat2T<float>;
 
-__device__ inline Mat2 mul(const Sym2& x, const Sym2& y) {
+template <class T>
+__device__ inline Mat2T<T> mul(const Sym2T<T>& x, const Sym2T<T>& y) {
   return {x.a * y.a + x.b * y.b, x.a * y.b + x.b * y.c, x.b * y.a + x.c * y.b, x.b * y.b + x.c * y.c};
 }
-__device__ inline Mat2 mul(const Mat2& x, const Sym2& y) {
+template <class T>
+__device__ inline Mat2T<T> mul(const Mat2T<T>& x, const Sym2T<T>& y) {
   return {x.m00 * y.a + x.m01 * y.b, x.m00 * y.b + x.m01 * y.c, x.m10 * y.a + x.m11 * y.b, x.m10 * y.b + x.m11 * y.c};
 }
-__device__ inline Mat2 mul(const Mat2& x, const Mat2& y) {
+template <class T>
+__device__ inline Mat2T<T> mul(const Mat2T<T>& x, const Mat2T<T>& y) {
   return {x.m00 * y.m00 + x.m01 * y.m10, x.m00 * y.m01 + x.m01 * y.m11, x.m10 * y.m00 + x.m11 * y.m10,
           x.m10 * y.m01 + x.m11 * y.m11};
 }
-__device__ inline float trace(const Mat2& x) { return x.m00 + x.m11; }
+template <class T>
+__device__ inline T trace(const Mat2T<T>& x) { return x.m00 + x.m11; }
 // symmetric part of x + x^T stored as Sym2
-__device__ inline Sym2 sym_plus_t(const Mat2& x) { return {2.f * x.m00, x.m01 + x.m10, 2.f * x.m11}; }
-__device__ inline Sym2 to_sym(const Mat2& x) { return {x.m00, 0.5f * (x.m01 + x.m10), x.m11}; }
+template <class T>
+__device__ inline Sym2T<T> sym_plus_t(const Mat2T<T>& x) { return {T(2) * x.m00, x.m01 + x.m10, T(2) * x.m11}; }
+template <class T>
+__device__ inline Sym2T<T> to_sym(const Mat2T<T>& x) { return {x.m00, T(0.5) * (x.m01 + x.m10), x.m11}; }
 // A S A^T for a general 2x2 A (row-major a00 a01 a10 a11)
-__device__ inline Sym2 congruence(const float A[4], const Sym2& S) {
-  float t00 = A[0] * S.a + A[1] * S.b, t01 = A[0] * S.b + A[1] * S.c;
-  float t10 = A[2] * S.a + A[3] * S.b, t11 = A[2] * S.b + A[3] * S.c;
+template <class T>
+__device__ inline Sym2T<T> congruence(const T A[4], const Sym2T<T>& S) {
+  T t00 = A[0] * S.a + A[1] * S.b, t01 = A[0] * S.b + A[1] * S.c;
+  T t10 = A[2] * S.a + A[3] * S.b, t11 = A[2] * S.b + A[3] * S.c;
   return {t00 * A[0] + t01 * A[1], t10 * A[0] + t11 * A[1], t10 * A[2] + t11 * A[3]};
 }
 
@@ -243,9 +255,11 @@ __host__ __device__ inline float sat_f(double x) { return (float)(x > 3.40282346
 
 // Galaxy world covariance Sigma_g = scale^2 R diag(1, axis^2) R^T and its first/second
 // derivatives w.r.t. (logit axis, angle, log scale); pairs ordered 00 01 02 11 12 22.
-struct GalShape {
-  Sym2 S, d[3], d2[6];
+template <class T>
+struct GalShapeT {
+  Sym2T<T> S, d[3], d2[6];
 };
+using GalShape = GalShapeT<float>;
 __device__ inline Sym2 inv2(const Sym2& S, float& logdet) {
   // det = a c - b^2 with the rounding of b^2 compensated (one FMA recovers its exact error)
   const float bb = S.b * S.b;

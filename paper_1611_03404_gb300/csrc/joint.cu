@@ -1042,6 +1042,10 @@ extern "C" int celeste_joint_newton(celeste_problem* p, double* theta, const cel
     if ((rc = value_eval(trial, theta, dJ)) != CELESTE_OK) return rc;   // J(trial) - J(theta)
     double rho = pred > 0.0 ? dJ / pred : -1.0;
     if (!std::isfinite(dJ)) rho = -1.0;
+    if (rho <= eta && pred <= ftol * std::fabs(f)) {   // a rejected step that promised <= ftol |f|
+      status = CELESTE_STATUS_CONVERGED;
+      break;
+    }
     if (rho < 0.25)
       delta *= 0.25;
     else if (rho > 0.75 && h.boundary)

@@ -163,32 +163,39 @@ __global__ void tr_update_kernel(NewtonDev N, int* flags) {
       const double dL = N.Ltrial[s], pred = N.pred[s];   // f - f_new = L_new - L = dL
       double rho = pred > 0 ? dL / pred : -1.0;
       if (!isfinite(dL)) rho = -1.0;
-      double delta = N.delta[s];
-      if (rho < 0.25)
-        delta = 0.25 * delta;
-      else if (rho > 0.75 && st[ST_BOUNDARY])
-        delta = fmin(2.0 * delta, N.delta_max);
-      N.delta[s] = delta;
       int fl = 0;
-      st[ST_SAME] = 1;   // until accepted below
-      if (rho > N.eta) {
-        st[ST_SAME] = 0;
-        st[ST_CACHED] = 0;
-        const double Lnew = N.L[s] + dL;
-        const bool done = fabs(dL) <= N.ftol * fabs(Lnew);
-        for (int k = 0; k < NP; ++k) N.theta[(size_t)s * NP + k] = N.trial[(size_t)s * NP + k];
-        N.L[s] = Lnew;
-        if (done) {
-          st[ST_ACTIVE] = 0;
-          st[ST_STATUS] = CELESTE_STATUS_CONVERGED;
-        } else {
-          fl = FLAG_FULL;
-        }
-      }
-      if (st[ST_ACTIVE] && delta < N.delta_min) {
+      if (rho <= N.eta && pred <= N.ftol * fabs(N.L[s])) {
+        // a rejected step that had promised no more than ftol |f|: the radius only shrinks from
+        // here, so the model has nothing left above the tolerance (the evaluation's rounding floor)
         st[ST_ACTIVE] = 0;
-        st[ST_STATUS] = CELESTE_STATUS_RADIUS_COLLAPSE;
-        fl = 0;
+        st[ST_STATUS] = CELESTE_STATUS_CONVERGED;
+      } else {
+        double delta = N.delta[s];
+        if (rho < 0.25)
+          delta = 0.25 * delta;
+        else if (rho > 0.75 && st[ST_BOUNDARY])
+          delta = fmin(2.0 * delta, N.delta_max);
+        N.delta[s] = delta;
+        st[ST_SAME] = 1;   // until accepted below
+        if (rho > N.eta) {
+          st[ST_SAME] = 0;
+          st[ST_CACHED] = 0;
+          const double Lnew = N.L[s] + dL;
+          const bool done = fabs(dL) <= N.ftol * fabs(Lnew);
+          for (int k = 0; k < NP; ++k) N.theta[(size_t)s * NP + k] = N.trial[(size_t)s * NP + k];
+          N.L[s] = Lnew;
+          if (done) {
+            st[ST_ACTIVE] = 0;
+            st[ST_STATUS] = CELESTE_STATUS_CONVERGED;
+          } else {
+            fl = FLAG_FULL;
+          }
+        }
+        if (st[ST_ACTIVE] && delta < N.delta_min) {
+          st[ST_ACTIVE] = 0;
+          st[ST_STATUS] = CELESTE_STATUS_RADIUS_COLLAPSE;
+          fl = 0;
+        }
       }
       flags[s] = fl;
     } else {

@@ -45,6 +45,81 @@ __device__ inline void galaxy_shape_f(double eta, double phi, double kappa, GalS
   g.d2[5] = {4.f * g.S.a, 4.f * g.S.b, 4.f * g.S.c};
 }
 
+// The same derivatives in float64, for components whose covariance is ill-conditioned (below).
+__device__ inline void galaxy_shape_d(double eta, double phi, double kappa, GalShapeT<double>& g) {
+  const double e = sigmoid_d(eta), em = sigmoid_d(-eta), e2 = e * e;
+  const double s2 = exp(2.0 * kappa);
+  double sn, c;
+  sincos(phi, &sn, &c);
+  const Sym2T<double> A = {c * c, c * sn, sn * sn};
+  const Sym2T<double> B = {sn * sn, -c * sn, c * c};
+  const Sym2T<double> dA = {-2.0 * c * sn, c * c - sn * sn, 2.0 * c * sn};
+  const Sym2T<double> d2A = {-2.0 * (c * c - sn * sn), -4.0 * c * sn, 2.0 * (c * c - sn * sn)};
+  const double de2 = 2.0 * e2 * em, d2e2 = 2.0 * e2 * em * (2.0 - 3.0 * e);
+  g.S = {s2 * (A.a + e2 * B.a), s2 * (A.b + e2 * B.b), s2 * (A.c + e2 * B.c)};
+  g.d[0] = {s2 * de2 * B.a, s2 * de2 * B.b, s2 * de2 * B.c};
+  const double k1 = s2 * em * (1.0 + e);   // s2 (1 - e^2)
+  g.d[1] = {k1 * dA.a, k1 * dA.b, k1 * dA.c};
+  g.d[2] = {2.0 * g.S.a, 2.0 * g.S.b, 2.0 * g.S.c};
+  g.d2[0] = {s2 * d2e2 * B.a, s2 * d2e2 * B.b, s2 * d2e2 * B.c};
+  g.d2[1] = {-s2 * de2 * dA.a, -s2 * de2 * dA.b, -s2 * de2 * dA.c};
+  g.d2[2] = {2.0 * g.d[0].a, 2.0 * g.d[0].b, 2.0 * g.d[0].c};
+  g.d2[3] = {k1 * d2A.a, k1 * d2A.b, k1 * d2A.c};
+  g.d2[4] = {2.0 * g.d[1].a, 2.0 * g.d[1].b, 2.0 * g.d[1].c};
+  g.d2[5] = {4.0 * g.S.a, 4.0 * g.S.b, 4.0 * g.S.c};
+}
+
+__device__ inline Sym2T<double> inv2(const Sym2T<double>& S, double& logdet) {
+  const double det = S.a * S.c - S.b * S.b;
+  logdet = log(det);
+  const double r = 1.0 / det;
+  return {S.c * r, -S.b * r, S.a * r};
+}
+__device__ inline double gauss_weight(double w, const Sym2T<double>& S) {
+  return w / (6.283185307179586 * sqrt(S.a * S.c - S.b * S.b));
+}
+
+// One galaxy component's table entry, computed in T and stored as float: precision P of
+// Sigma = tau A Sigma_g A^T + S_k, weighted normaliser, and with `full` -1/2 dP, -1/2 d logdet and
+// their second derivatives over (axis, angle, scale).
+template <class T>
+__device__ inline void gal_entry(const GalShapeT<T>& gs, const T A[4], const Sym2T<T>& Sk, T w, T tau, bool full,
+                                 float* e) {
+  const Sym2T<T> Sp = congruence(A, gs.S);
+  const Sym2T<T> S = {tau * Sp.a + Sk.a, tau * Sp.b + Sk.b, tau * Sp.c + Sk.c};
+  T ld;
+  const Sym2T<T> Pm = inv2(S, ld);
+  e[GT_P + 0] = (float)Pm.a;
+  e[GT_P + 1] = (float)Pm.b;
+  e[GT_P + 2] = (float)Pm.c;
+  e[GT_W] = (float)gauss_weight(w, S);
+  if (!full) return;
+  Mat2T<T> PdS[3];
+  for (int a = 0; a < 3; ++a) {
+    const Sym2T<T> t = congruence(A, gs.d[a]);
+    PdS[a] = mul(Pm, Sym2T<T>{tau * t.a, tau * t.b, tau * t.c});
+    const Sym2T<T> dP = to_sym(mul(PdS[a], Pm));   // P dS P = -dP/da
+    e[GT_QA + 3 * a + 0] = (float)(T(0.5) * dP.a);
+    e[GT_QA + 3 * a + 1] = (float)(T(0.5) * dP.b);
+    e[GT_QA + 3 * a + 2] = (float)(T(0.5) * dP.c);
+    e[GT_LA + a] = (float)(T(-0.5) * trace(PdS[a]));
+  }
+  int q = 0;
+  for (int a = 0; a < 3; ++a)
+    for (int b = a; b < 3; ++b, ++q) {
+      const Sym2T<T> t = congruence(A, gs.d2[q]);
+      const Sym2T<T> d2S = {tau * t.a, tau * t.b, tau * t.c};
+      const Mat2T<T> X = mul(PdS[a], PdS[b]);
+      const Sym2T<T> two = sym_plus_t(mul(X, Pm));
+      const Mat2T<T> Pd2 = mul(Pm, d2S);
+      const Sym2T<T> third = to_sym(mul(Pd2, Pm));
+      e[GT_QAB + 3 * q + 0] = (float)(T(-0.5) * (two.a - third.a));
+      e[GT_QAB + 3 * q + 1] = (float)(T(-0.5) * (two.b - third.b));
+      e[GT_QAB + 3 * q + 2] = (float)(T(-0.5) * (two.c - third.c));
+      e[GT_LAB + q] = (float)(T(-0.5) * (trace(Pd2) - trace(X)));
+    }
+}
+
 // Brightness constants of every listed source for all five bands, in float64.  One warp per
 // source: lane 5t + b (t = type, b = band, lanes 0-9) evaluates the lognormal moments of l_b for
 // type t, lanes 0-4 then combine both types for band b.  Spreading the transcendental functions
@@ -130,40 +205,21 @@ __global__ void __launch_bounds__(64) table_kernel(ProblemDev P, const double* _
     galaxy_shape_f(th[3], th[4], th[5], gs);
     const float A[4] = {(float)im.A[0], (float)im.A[1], (float)im.A[2], (float)im.A[3]};
     const float tau = P.tau[j], nu = P.nu[j];
+    float* e = out + TB_GAL + tid * GT_STRIDE;
+    // A long, thin galaxy (axis ratio ~1e-4, radius ~1e3 px) gives Sigma entries ~1e6 whose
+    // determinant cancels to ~1e-6 of a c: float32 would leave P and its shape derivatives with a
+    // few correct bits.  Where a c exceeds 16 det such a component is built in float64.
     const Sym2 Sp = congruence(A, gs.S);
     const Sym2 S = {tau * Sp.a + pc.S.a, tau * Sp.b + pc.S.b, tau * Sp.c + pc.S.c};
-    float ld;
-    const Sym2 Pm = inv2(S, ld);
-    float* e = out + TB_GAL + tid * GT_STRIDE;
-    e[GT_P + 0] = Pm.a;
-    e[GT_P + 1] = Pm.b;
-    e[GT_P + 2] = Pm.c;
-    e[GT_W] = gauss_weight(pc.w * nu, S);
-    if (full) {
-      Mat2 PdS[3];
-      for (int a = 0; a < 3; ++a) {
-        const Sym2 t = congruence(A, gs.d[a]);
-        PdS[a] = mul(Pm, Sym2{tau * t.a, tau * t.b, tau * t.c});
-        const Sym2 dP = to_sym(mul(PdS[a], Pm));   // P dS P = -dP/da
-        e[GT_QA + 3 * a + 0] = 0.5f * dP.a;
-        e[GT_QA + 3 * a + 1] = 0.5f * dP.b;
-        e[GT_QA + 3 * a + 2] = 0.5f * dP.c;
-        e[GT_LA + a] = -0.5f * trace(PdS[a]);
-      }
-      int q = 0;
-      for (int a = 0; a < 3; ++a)
-        for (int b = a; b < 3; ++b, ++q) {
-          const Sym2 t = congruence(A, gs.d2[q]);
-          const Sym2 d2S = {tau * t.a, tau * t.b, tau * t.c};
-          const Mat2 X = mul(PdS[a], PdS[b]);
-          const Sym2 two = sym_plus_t(mul(X, Pm));
-          const Mat2 Pd2 = mul(Pm, d2S);
-          const Sym2 third = to_sym(mul(Pd2, Pm));
-          e[GT_QAB + 3 * q + 0] = -0.5f * (two.a - third.a);
-          e[GT_QAB + 3 * q + 1] = -0.5f * (two.b - third.b);
-          e[GT_QAB + 3 * q + 2] = -0.5f * (two.c - third.c);
-          e[GT_LAB + q] = -0.5f * (trace(Pd2) - trace(X));
-        }
+    const float bb = S.b * S.b;
+    const float det = fmaf(S.a, S.c, -bb) - fmaf(S.b, S.b, -bb);
+    if (S.a * S.c <= 16.f * det) {
+      gal_entry<float>(gs, A, pc.S, pc.w * nu, tau, full != 0, e);
+    } else {
+      GalShapeT<double> gd;
+      galaxy_shape_d(th[3], th[4], th[5], gd);
+      const double Ad[4] = {im.A[0], im.A[1], im.A[2], im.A[3]};
+      gal_entry<double>(gd, Ad, Sym2T<double>{pc.S.a, pc.S.b, pc.S.c}, (double)pc.w * nu, (double)tau, full != 0, e);
     }
   } else if (tid < NGAL + NSTAR) {
     const int k = tid - NGAL;

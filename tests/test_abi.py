@@ -116,9 +116,10 @@ def test_validation_rejects_bad_descriptors(pkg):
 def test_hessian_mode_validation(pkg):
     """The tensor-core SYRK modes exist for 128-pixel tiles only; unknown modes are refused."""
     sc = synth.tiny(seed=1, n_sources=2, n_images=2)
-    for mode in (pkg.HESS_FP32, pkg.HESS_TF32, pkg.HESS_BF16X3):
+    for mode in (pkg.HESS_FP32, pkg.HESS_TF32, pkg.HESS_BF16X3, pkg.HESS_BF16X6, pkg.HESS_TF32X3):
         assert pkg.HostProblem(sc, tile_pixels=128, hessian_mode=mode).counts()["sources"] == 2
-    for mode, tile in ((3, 128), (-1, 128), (pkg.HESS_TF32, 256), (pkg.HESS_BF16X3, 512)):
+    for mode, tile in ((5, 128), (-1, 128), (pkg.HESS_TF32, 256), (pkg.HESS_BF16X3, 512), (pkg.HESS_BF16X6, 256),
+                       (pkg.HESS_TF32X3, 1024)):
         with pytest.raises(pkg.CelesteError, match="invalid argument"):
             pkg.HostProblem(sc, tile_pixels=tile, hessian_mode=mode)
 

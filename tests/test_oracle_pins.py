@@ -439,3 +439,49 @@ def test_patches_and_neighbours_brute_force():
         for (n, *_r) in rects[s]:
             want = sorted(t for t in range(sc.n_sources) if t != s and (masks[(s, n)] & masks[(t, n)]).any())
             assert sorted(nbr[s][n]) == want
+
+
+def test_newton_stops_at_the_evaluation_floor():
+    """Trust-region Newton on a function whose values and gradients carry a rounding floor (value
+    noise 3e-8 relative, like a float32 sum; gradient noise 1e-3 absolute) with ftol = 1e-12, far
+    below that floor, so that neither the accepted-change test nor the Newton decrement can end
+    the solve: it must stop as converged once a rejected step had promised no more than ftol |f|,
+    near the true minimum, instead of shrinking the radius until it collapses.  The function is a
+    strictly convex quadratic plus a quartic in 6 dimensions whose minimiser is found
+    independently by scipy; without the floor the same solve converges by the other tests."""
+    rng = np.random.default_rng(4)
+    A = rng.standard_normal((6, 6))
+    B = A @ A.T + 6 * np.eye(6)
+    c = rng.standard_normal(6)
+    f0 = 1e4
+
+    def exact(x):
+        return f0 + 0.5 * x @ B @ x - c @ x + 0.25 * np.sum(x ** 4)
+
+    def grad(x):
+        return B @ x - c + x ** 3
+
+    def hess(x):
+        return B + np.diag(3 * x ** 2)
+
+    def h(x, salt):
+        # deterministic pseudo-noise in [-0.5, 0.5) from the bits of x
+        b = np.frombuffer(np.asarray(x, np.float64).tobytes(), np.uint64)
+        return ((int(b.sum() % 1000003) * (salt + 7919)) % 1000003) / 1000003.0 - 0.5
+
+    def noisy_value(x):
+        return exact(x) * (1.0 + 3e-8 * h(x, 0))
+
+    def noisy_vgh(x):
+        g = grad(x) + 1e-3 * np.array([h(x, k + 1) for k in range(6)])
+        return -noisy_value(x), -g, -hess(x)
+
+    xmin = optimize.minimize(exact, np.zeros(6), jac=grad, method="BFGS", tol=1e-12).x
+    fmin = exact(xmin)
+    r = O.trust_region_newton(lambda x: -noisy_value(x), noisy_vgh, np.full(6, 3.0), ftol=1e-12)
+    assert r["status"] == O.STATUS_CONVERGED and r["iters"] < 50
+    assert exact(r["theta"]) - fmin <= 1e-9 * f0
+    # without the floor the same solve converges by the accepted-change or decrement tests
+    r = O.trust_region_newton(lambda x: -exact(x), lambda x: (-exact(x), -grad(x), -hess(x)), np.full(6, 3.0))
+    assert r["status"] == O.STATUS_CONVERGED
+    assert exact(r["theta"]) - fmin <= 2e-8 * f0

@@ -175,6 +175,18 @@ def test_edge_patches_clipped_and_maximal(P):
     compare_all(P, sc, th, what="edges")
 
 
+@pytest.mark.parametrize("axis_logit,scale", [(-7.6, 1500.0), (-4.6, 50.0)])
+def test_thin_extended_galaxy(P, axis_logit, scale):
+    """A galaxy far thinner than a pixel and far longer than its patch (axis ratio 5e-4, half-light
+    radius 1500 px; and 1e-2, 50 px), the shape Newton reached on a faint mosaic source: its
+    components' covariances are ill-conditioned (a c / det up to ~1e5), where float32 tables lose
+    the precision matrix and its shape derivatives."""
+    sc = synth.single_source(seed=9, size=31, is_gal=True)
+    th = _spread(sc.theta0, np.random.default_rng(9))
+    th[0, 3], th[0, 5], th[0, 6] = axis_logit, math.log(scale), 4.7
+    compare_all(P, sc, th, what=f"thin galaxy axis_logit={axis_logit} scale={scale}")
+
+
 def test_newton_matches_oracle_optimum(P):
     """Batched GPU Newton reaches the oracle's optimum within 1e-4 per identified parameter."""
     sc = synth.single_source(seed=1611, size=41)
@@ -210,15 +222,20 @@ def compare_optimum(got, ref, tol=1e-4, slack=None):
     stop_slack) widens each bound by what the ELBO stopping tolerance leaves undetermined along
     weakly curved directions, mapped through the parameter's transform."""
     sig = lambda x: 1 / (1 + math.exp(-x))
-    dsig = lambda x: sig(x) * (1 - sig(x))
     sl = np.zeros(27) if slack is None else np.asarray(slack)
+
+    def image(f, x, w):
+        # how far f moves when its argument moves by up to w from x (the slack's image through the
+        # transform; a derivative at x understates it where f flattens, e.g. a sigmoid at 27)
+        return max(abs(f(x + w) - f(x)), abs(f(x - w) - f(x)))
+
     a_gal = sig(ref[6])
-    assert abs(sig(got[6]) - a_gal) <= tol + dsig(ref[6]) * sl[6]
+    assert abs(sig(got[6]) - a_gal) <= tol + image(sig, ref[6], sl[6])
     assert np.all(np.abs(got[0:2] - ref[0:2]) <= tol + sl[0:2])
     if a_gal > 1e-3:
-        assert abs(sig(got[2]) - sig(ref[2])) <= tol + dsig(ref[2]) * sl[2]
-        assert abs(sig(got[3]) - sig(ref[3])) <= tol + dsig(ref[3]) * sl[3]
-        assert abs(math.exp(got[5]) - math.exp(ref[5])) <= (tol + sl[5]) * math.exp(ref[5])
+        assert abs(sig(got[2]) - sig(ref[2])) <= tol + image(sig, ref[2], sl[2])
+        assert abs(sig(got[3]) - sig(ref[3])) <= tol + image(sig, ref[3], sl[3])
+        assert abs(math.exp(got[5]) - math.exp(ref[5])) <= tol * math.exp(ref[5]) + image(math.exp, ref[5], sl[5])
         if sig(ref[3]) < 1 - 1e-3:
             assert abs(math.remainder(got[4] - ref[4], math.pi)) <= tol + sl[4]
         idx = [9, 10] + list(range(19, 27))
