@@ -71,6 +71,9 @@ def parse(argv=None):
                     help="mosaic: 10x10 overlapping fields, 100,000 sources, 1-12 exposures each (the headline); "
                          "field: 2048x1489 px x 5 bands, --sources sources")
     ap.add_argument("--sources", type=int, default=1000, help="sources of the field workload")
+    ap.add_argument("--mosaic-fields", type=int, default=10,
+                    help="the mosaic's fields per side (1000 sources per field at the same density; 10 = the "
+                         "headline's 100,000 sources; smaller mosaics for profiler captures)")
     ap.add_argument("--tile", type=int, default=0, help="pixels per tile; 0 = autotune")
     ap.add_argument("--no-warm-start", dest="warm_start", action="store_false",
                     help="time only the plain form (Newton from the catalog, FP32 FMA Hessian)")
@@ -97,9 +100,10 @@ def parse(argv=None):
 def workload_config(args):
     """The workload (identical for both arms; how it is solved is in `method`)."""
     if args.workload == "mosaic":
-        return {"workload": "mosaic_10x10_fields_100000src", "fields": [10, 10], "field_px": [2048, 1489],
+        f = args.mosaic_fields
+        return {"workload": f"mosaic_{f}x{f}_fields_{1000 * f * f}src", "fields": [f, f], "field_px": [2048, 1489],
                 "field_overlap": 0.2, "bands_per_field": "1-3", "exposures_per_source": "1-12",
-                "sources_per_gpu": 100_000, "patch_radius": "8-64 (brightness, 4 sigma of the widest component)",
+                "sources_per_gpu": 1000 * f * f, "patch_radius": "8-64 (brightness, 4 sigma of the widest component)",
                 "galaxy_fraction": 0.6, "elbo_tol": 1e-8, "max_iter": 50,
                 "l2": "inputs larger than L2 (GBs of patch pixels) and a 256 MiB flush between timed steps",
                 "parallelism": "one independently seeded mosaic per GPU"}
@@ -281,7 +285,8 @@ def make_scene(args, rank, device):
     import synth
     if args.workload == "mosaic":
         from synth.mosaic import mosaic
-        return mosaic(seed=args.seed + rank, device=device)
+        f = args.mosaic_fields
+        return mosaic(seed=args.seed + rank, fields_x=f, fields_y=f, n_sources=1000 * f * f, device=device)
     return synth.field(seed=args.seed + rank, n_sources=args.sources)
 
 

@@ -287,22 +287,25 @@ __device__ __forceinline__ void syrk_mma(const float (*As)[SYRK_LD], const float
 
 // One galaxy mixture component's contribution at pixel offset d (squares s): value, 5 first and 15
 // second derivatives over v5 = (mu0, mu1, axis, angle, scale), accumulated into its family's sums.
+// Far from a narrow component its Gaussian underflows to exactly 0 (q > ~207): where that holds on
+// every lane of the warp (lanes without a pixel count as 0) the component adds exactly nothing, and
+// the warp skips its derivative terms (on the mosaic ~19 % of warp-component pairs).  All lanes of
+// the warp must be active.
 __device__ __forceinline__ void gal_component(const float* ep, float d0, float d1, float s0, float s1, float s2,
-                                              float& F, float (&Fv)[5], float (&Fvv)[15]) {
+                                              bool valid, float& F, float (&Fv)[5], float (&Fvv)[15]) {
   float e[GT_STRIDE];
-  {
-    const float4* e4 = reinterpret_cast<const float4*>(ep);
+  const float4* e4 = reinterpret_cast<const float4*>(ep);
 #pragma unroll
-    for (int w = 0; w < GT_STRIDE / 4; ++w) {
-      const float4 t4 = e4[w];
-      e[4 * w + 0] = t4.x;
-      e[4 * w + 1] = t4.y;
-      e[4 * w + 2] = t4.z;
-      e[4 * w + 3] = t4.w;
-    }
+  for (int w = 0; w < GT_STRIDE / 4; ++w) {
+    const float4 t4 = e4[w];
+    e[4 * w + 0] = t4.x;
+    e[4 * w + 1] = t4.y;
+    e[4 * w + 2] = t4.z;
+    e[4 * w + 3] = t4.w;
   }
   const float q = e[GT_P] * s0 + e[GT_P + 1] * s1 + e[GT_P + 2] * s2;
   const float N = e[GT_W] * exp2f(q * (-0.5f * LOG2E));
+  if (__all_sync(0xffffffffu, N == 0.f || !valid)) return;
   const float z0 = e[GT_P] * d0 + e[GT_P + 1] * d1, z1 = e[GT_P + 1] * d0 + e[GT_P + 2] * d1;
   float b[3], t0[3], t1[3];
 #pragma unroll
@@ -437,10 +440,10 @@ __global__ void __launch_bounds__(BLOCK) elbo_full_kernel(ProblemDev P) {
       // instruction cache, and each family's accumulators stay statically indexed
 #pragma unroll 1
       for (int j = 0; j < CELESTE_NEXP; ++j)
-        gal_component(&tab[TB_GAL + (k * NMIX + j) * GT_STRIDE], d0, d1, s0, s1, s2, F[0], Fv[0], Fvv[0]);
+        gal_component(&tab[TB_GAL + (k * NMIX + j) * GT_STRIDE], d0, d1, s0, s1, s2, valid, F[0], Fv[0], Fvv[0]);
 #pragma unroll 1
       for (int j = CELESTE_NEXP; j < NMIX; ++j)
-        gal_component(&tab[TB_GAL + (k * NMIX + j) * GT_STRIDE], d0, d1, s0, s1, s2, F[1], Fv[1], Fvv[1]);
+        gal_component(&tab[TB_GAL + (k * NMIX + j) * GT_STRIDE], d0, d1, s0, s1, s2, valid, F[1], Fv[1], Fvv[1]);
     }
 
     // ---- galaxy profile over G6 = (mu0, mu1, dev, axis, angle, scale);  v5 index -> G6 index:

@@ -221,7 +221,12 @@ def compare_optimum(got, ref, tol=1e-4, slack=None):
     is below 1 - 1e-3 (otherwise they are unidentified).  `slack` (free-parameter units, from
     stop_slack) widens each bound by what the ELBO stopping tolerance leaves undetermined along
     weakly curved directions, mapped through the parameter's transform."""
-    sig = lambda x: 1 / (1 + math.exp(-x))
+    def sig(x):
+        return 1.0 / (1.0 + math.exp(-x)) if x >= 0 else math.exp(x) / (1.0 + math.exp(x))
+
+    def exp(x):
+        return math.exp(x) if x < 700.0 else math.inf
+
     sl = np.zeros(27) if slack is None else np.asarray(slack)
 
     def image(f, x, w):
@@ -235,7 +240,7 @@ def compare_optimum(got, ref, tol=1e-4, slack=None):
     if a_gal > 1e-3:
         assert abs(sig(got[2]) - sig(ref[2])) <= tol + image(sig, ref[2], sl[2])
         assert abs(sig(got[3]) - sig(ref[3])) <= tol + image(sig, ref[3], sl[3])
-        assert abs(math.exp(got[5]) - math.exp(ref[5])) <= tol * math.exp(ref[5]) + image(math.exp, ref[5], sl[5])
+        assert abs(exp(got[5]) - exp(ref[5])) <= tol * exp(ref[5]) + image(exp, ref[5], sl[5])
         if sig(ref[3]) < 1 - 1e-3:
             assert abs(math.remainder(got[4] - ref[4], math.pi)) <= tol + sl[4]
         idx = [9, 10] + list(range(19, 27))
