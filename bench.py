@@ -510,7 +510,7 @@ def main():
 
     clocks = clk.summary()
     sm_mhz = clocks["sm_mhz"] or 1920.0
-    roofline, kernels = rooflines(prof, t_step, n_sm, sm_mhz, peaks, iters, args.steps)
+    roofline, kernels = rooflines(prof, t_step, n_sm, sm_mhz, peaks, iters, args.steps, kernel_variant(tile, hmode))
 
     e2e = end_to_end(args, P, prob, scene, step, theta, theta0, flush, stream, world, dev) if args.e2e_steps > 0 else None
 
@@ -547,9 +547,16 @@ def main():
         dist.destroy_process_group()
 
 
-def rooflines(prof, t_step, n_sm, sm_mhz, peaks, iters, steps):
+def kernel_variant(tile, hmode):
+    """Name of the pixel-kernel instantiation that a problem with this tile size and Hessian form runs."""
+    ppt = {128: 1, 256: 2, 512: 4}.get(tile, 8)
+    return f"elbo_full_kernel<{1 if hmode else ppt}, {hmode}>"
+
+
+def rooflines(prof, t_step, n_sm, sm_mhz, peaks, iters, steps, variant):
     """The pixel kernel (FP32 bound; also against the special-function unit and HBM) and the
-    trust-region step (FP64), each with its share of the timed steps."""
+    trust-region step (FP64), each with its share of the timed steps.  `traffic` comes from the
+    committed DRAM capture of the same kernel variant, if its source is unchanged since."""
     clk = sm_mhz * 1e6
     nominal_fp32 = n_sm * FP32_LANES_PER_SM * 2 * clk / 1e12
     nominal_mufu = n_sm * MUFU_PER_SM_CLK * clk / 1e12
@@ -564,9 +571,10 @@ def rooflines(prof, t_step, n_sm, sm_mhz, peaks, iters, steps):
     if os.path.exists(tfile) and prof["full_launches"]:
         with open(tfile) as f:
             tr = json.load(f)
-        if tr.get("kernel_source_hash") == _build_hash():
-            traffic = tr["dram_bytes_per_pixel"] * px / prof["full_launches"]
-    roof = {"bound": "alu", "kernel": "elbo_full_kernel", "achieved": achieved, "peak": nominal_fp32,
+        ent = tr.get("kernels", {}).get(variant)
+        if ent and tr.get("kernel_source_hash") == _build_hash():
+            traffic = ent["dram_bytes_per_pixel"] * px / prof["full_launches"]
+    roof = {"bound": "alu", "kernel": variant, "achieved": achieved, "peak": nominal_fp32,
             "unit": "TFLOP/s", "frac": achieved / nominal_fp32 if achieved else None, "traffic": traffic,
             "peak_basis": f"{n_sm} SMs (queried) x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_mhz:.0f} MHz (median SM "
                           f"clock sampled during the timed steps)",
