@@ -195,6 +195,19 @@ enum { CELESTE_NBR_FULL = 0, CELESTE_NBR_WINDOW = 1 };
  * Errors: CELESTE_ERR_INVALID_ARG when capacity is too small or n_pairs is NULL. */
 int celeste_joint_pairs(celeste_problem* p, int32_t* pairs, int64_t capacity, int64_t* n_pairs);
 
+/* Device memory of the joint calls (celeste_joint_cross_hessian, _newton, _value): the overlap
+ * lists and tiles, the cross-tile sums and the joint Newton state (about 12 KB per source plus
+ * 12 bytes per patch pixel).  celeste_joint_workspace_bytes: bytes needed (host only; builds the
+ * overlap lists on first use; 0 for a NULL problem).  celeste_joint_bind: bind a caller-owned
+ * device buffer of at least that size, 256-byte aligned, after celeste_problem_bind, and upload the
+ * lists into it (asynchronous on `stream`; the problem keeps the host copies).  The library
+ * allocates nothing for the joint calls; they return CELESTE_ERR_STATE until a workspace is bound.
+ * The buffer must outlive every later joint call on the problem.
+ * Errors: CELESTE_ERR_STATE before celeste_problem_bind; CELESTE_ERR_WORKSPACE when the buffer is
+ * missing, too small or misaligned. */
+size_t celeste_joint_workspace_bytes(celeste_problem* p);
+int celeste_joint_bind(celeste_problem* p, void* workspace, size_t bytes, celeste_stream_t stream);
+
 /* Cross-source Hessian blocks of J at theta, one per pair of celeste_joint_pairs:
  *   theta:  device float64 [S][27], the parameters of every source;
  *   blocks: device float64 [n_pairs][27][27]; block k row i, column j = d2J/dtheta_{s,i} dtheta_{t,j}
@@ -225,8 +238,7 @@ int celeste_joint_cross_hessian(celeste_problem* p, const double* theta, double*
  *   iters_out, status_out, J_out, cg_iters_out (may be NULL): host; outer iterations, one
  *           CELESTE_STATUS_* for the whole solve, J at the result, total CG iterations.
  * Synchronous (reads a few scalars back every iteration); leaves the background rendered in
- * window mode at the result.  Allocates its state (about 12 KB per source plus 12 bytes per patch
- * pixel) with cudaMalloc on first use, owned by the problem. */
+ * window mode at the result.  Its state lives in the joint workspace (celeste_joint_bind). */
 int celeste_joint_newton(celeste_problem* p, double* theta, const celeste_newton_opts* opts, int32_t max_cg,
                          int32_t* iters_out, int32_t* status_out, double* J_out, int32_t* cg_iters_out,
                          celeste_stream_t stream);

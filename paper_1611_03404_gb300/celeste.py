@@ -59,7 +59,7 @@ EXPORTED = ["celeste_problem_create", "celeste_problem_workspace_bytes", "celest
             "celeste_cnn_mse", "celeste_cnn_adamw", "celeste_extract_patches", "celeste_covariance_batch",
             "celeste_render_background_mode", "celeste_joint_pairs", "celeste_joint_cross_hessian",
             "celeste_joint_newton", "celeste_joint_value", "celeste_problem_check", "celeste_problem_set_wait_budget",
-            "celeste_measure_peak"]
+            "celeste_measure_peak", "celeste_joint_workspace_bytes", "celeste_joint_bind"]
 
 
 def load_library(path=None):
@@ -101,6 +101,8 @@ def load_library(path=None):
         "celeste_problem_set_wait_budget": (ctypes.c_int, [vp, ctypes.c_longlong]),
         "celeste_measure_peak": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                                 ctypes.POINTER(ctypes.c_double), vp]),
+        "celeste_joint_workspace_bytes": (ctypes.c_size_t, [vp]),
+        "celeste_joint_bind": (ctypes.c_int, [vp, vp, ctypes.c_size_t, vp]),
         "celeste_joint_newton": (ctypes.c_int, [vp, dp, ctypes.POINTER(NewtonOpts), ctypes.c_int32,
                                                 ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                                                 ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32), vp]),
@@ -202,11 +204,23 @@ class Problem:
         """[n_pairs, 2] int32 (host numpy): source pairs s < t whose windows overlap."""
         return _joint_pairs(self.handle)
 
+    def _joint_workspace(self, stream=None):
+        """Binds the joint calls' device workspace (torch memory) on first use."""
+        if getattr(self, "_joint_ws", None) is None:
+            L = lib()
+            nbytes = L.celeste_joint_workspace_bytes(self.handle)
+            buf = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+            off = (-buf.data_ptr()) % 256
+            _check(L.celeste_joint_bind(self.handle, ctypes.c_void_p(buf.data_ptr() + off), ctypes.c_size_t(nbytes),
+                                        _stream(stream)))
+            self._joint_ws = buf
+
     def joint_newton(self, theta, max_iter=50, ftol=1e-8, gtol=1e-10, delta_max=1e4, eta=0.1, delta_min=1e-12,
                      max_cg=100, stream=None):
         """Trust-region Newton on the joint objective over all sources (theta updated in place).
         Returns dict(iters, status, J, cg_iters)."""
         assert theta.dtype == torch.float64 and theta.is_contiguous() and theta.shape == (self.S, NPARAM)
+        self._joint_workspace(stream)
         o = NewtonOpts(max_iter=max_iter, ftol=ftol, gtol=gtol, delta0=1.0, delta_max=delta_max, eta=eta,
                        delta_min=delta_min, graph_iters=1)
         it, st, cg = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
@@ -219,6 +233,7 @@ class Problem:
     def joint_value(self, theta, stream=None):
         """The joint objective J at theta (every covered pixel counted once)."""
         assert theta.dtype == torch.float64 and theta.is_contiguous() and theta.shape == (self.S, NPARAM)
+        self._joint_workspace(stream)
         J = ctypes.c_double(0.0)
         _check(lib().celeste_joint_value(self.handle, _ptr(theta), ctypes.byref(J), _stream(stream)))
         return J.value
@@ -227,6 +242,7 @@ class Problem:
         """Cross-source Hessian blocks of the joint objective, [n_pairs, 27, 27] float64 on theta's
         device, in the order of joint_pairs(); the background must be rendered with NBR_WINDOW at theta."""
         assert theta.dtype == torch.float64 and theta.is_contiguous() and theta.shape == (self.S, NPARAM)
+        self._joint_workspace(stream)
         n = len(self.joint_pairs())
         out = torch.empty(max(n, 1), NPARAM, NPARAM, dtype=torch.float64, device=theta.device)
         _check(lib().celeste_joint_cross_hessian(self.handle, _ptr(theta), _ptr(out), _stream(stream)))

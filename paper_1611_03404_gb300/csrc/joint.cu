@@ -127,31 +127,11 @@ static void joint_host(celeste_problem* p) {
   p->joint_host_built = true;
 }
 
-// The host lists uploaded into one device allocation owned by the problem (first use).
+// The joint structures live in a caller-bound workspace (celeste_joint_bind): the overlap lists,
+// then the joint Newton state.
 static int joint_build(celeste_problem* p) {
   joint_host(p);
-  if (p->joint_built) return CELESTE_OK;
-  const int n_pairs = (int)p->joint_pairs.size() / 2;
-  const JointLayout L = joint_layout(p->joint_n_items, p->joint_n_tiles, n_pairs);
-  void* dev = nullptr;
-  cudaError_t e = cudaMalloc(&dev, L.total);
-  if (e != cudaSuccess) return cuda_fail(e, "joint buffers");
-  char* b = static_cast<char*>(dev);
-  if (p->joint_n_items)
-    e = cudaMemcpy(b + L.items, p->joint_items_h.data(), sizeof(int) * p->joint_items_h.size(), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess && p->joint_n_tiles)
-    e = cudaMemcpy(b + L.tiles, p->joint_tiles_h.data(), sizeof(int) * p->joint_tiles_h.size(), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess)
-    e = cudaMemcpy(b + L.pair_items, p->joint_pair_items_h.data(), sizeof(int) * p->joint_pair_items_h.size(),
-                   cudaMemcpyHostToDevice);
-  if (e == cudaSuccess && n_pairs)
-    e = cudaMemcpy(b + L.pairs, p->joint_pairs.data(), sizeof(int) * p->joint_pairs.size(), cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) {
-    cudaFree(dev);
-    return cuda_fail(e, "joint upload");
-  }
-  p->joint_dev = dev;
-  p->joint_built = true;
+  if (!p->joint_built) return fail(CELESTE_ERR_STATE, "bind the joint workspace first (celeste_joint_bind)");
   return CELESTE_OK;
 }
 
@@ -845,15 +825,14 @@ JNLayout jn_layout(int S, int n_pairs, long long n_pix) {
 }
 
 
-// Allocates the joint solver's state on first use (sources' coupling lists uploaded with it).
-int jn_state(celeste_problem* p, const JNLayout& L) {
-  if (p->jn_dev) return CELESTE_OK;
+// Each source's coupling entries (pair index * 2 + side), CSR over the sources: host lists kept on
+// the problem for the upload at bind.
+void jn_rows(celeste_problem* p) {
   const int S = p->S, n_pairs = (int)p->joint_pairs.size() / 2;
-  void* dev = nullptr;
-  cudaError_t e = cudaMalloc(&dev, L.total);
-  if (e != cudaSuccess) return cuda_fail(e, "joint Newton buffers");
-  // each source's coupling entries (pair index * 2 + side)
-  std::vector<int> row_ptr(S + 1, 0), row_ent(2 * std::max(n_pairs, 1), 0);
+  std::vector<int>& row_ptr = p->jn_row_ptr_h;
+  std::vector<int>& row_ent = p->jn_row_ent_h;
+  row_ptr.assign(S + 1, 0);
+  row_ent.assign(2 * std::max(n_pairs, 1), 0);
   for (int k = 0; k < n_pairs; ++k) {
     row_ptr[p->joint_pairs[2 * k] + 1] += 1;
     row_ptr[p->joint_pairs[2 * k + 1] + 1] += 1;
@@ -864,14 +843,10 @@ int jn_state(celeste_problem* p, const JNLayout& L) {
     row_ent[fill[p->joint_pairs[2 * k]]++] = 2 * k;
     row_ent[fill[p->joint_pairs[2 * k + 1]]++] = 2 * k + 1;
   }
-  char* b = static_cast<char*>(dev);
-  e = cudaMemcpy(b + L.row_ptr, row_ptr.data(), sizeof(int) * (S + 1), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(b + L.row_ent, row_ent.data(), sizeof(int) * row_ent.size(), cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) {
-    cudaFree(dev);
-    return cuda_fail(e, "joint Newton upload");
-  }
-  p->jn_dev = dev;
+}
+
+int jn_state(celeste_problem* p, const JNLayout&) {
+  if (!p->jn_dev) return fail(CELESTE_ERR_STATE, "bind the joint workspace first (celeste_joint_bind)");
   return CELESTE_OK;
 }
 
@@ -1114,4 +1089,41 @@ extern "C" int celeste_joint_value(celeste_problem* p, const double* theta, doub
   *J_out = h.dJ;
   prof_count(p, 8);
   return device_errors(Dj, st);
+}
+
+extern "C" size_t celeste_joint_workspace_bytes(celeste_problem* p) {
+  if (!p) return 0;
+  joint_host(p);
+  const int n_pairs = (int)p->joint_pairs.size() / 2;
+  return joint_layout(p->joint_n_items, p->joint_n_tiles, n_pairs).total + jn_layout(p->S, n_pairs, p->n_pix).total;
+}
+
+extern "C" int celeste_joint_bind(celeste_problem* p, void* workspace, size_t bytes, celeste_stream_t stream) {
+  if (!p) return fail(CELESTE_ERR_INVALID_ARG, "null problem");
+  if (!p->bound) return fail(CELESTE_ERR_STATE, "bind the problem first");
+  joint_host(p);
+  const int n_pairs = (int)p->joint_pairs.size() / 2;
+  const JointLayout L = joint_layout(p->joint_n_items, p->joint_n_tiles, n_pairs);
+  const JNLayout J = jn_layout(p->S, n_pairs, p->n_pix);
+  if (!workspace || bytes < L.total + J.total)
+    return fail(CELESTE_ERR_WORKSPACE, "joint workspace needs %zu bytes", L.total + J.total);
+  if (reinterpret_cast<uintptr_t>(workspace) % 256) return fail(CELESTE_ERR_WORKSPACE, "workspace must be 256-byte aligned");
+  cudaStream_t st = (cudaStream_t)stream;
+  char* b = static_cast<char*>(workspace);
+  jn_rows(p);
+  cudaError_t e = cudaSuccess;
+  auto up = [&](size_t off, const std::vector<int>& v) {
+    if (e == cudaSuccess && !v.empty()) e = cudaMemcpyAsync(b + off, v.data(), sizeof(int) * v.size(), cudaMemcpyHostToDevice, st);
+  };
+  up(L.items, p->joint_items_h);
+  up(L.tiles, p->joint_tiles_h);
+  up(L.pair_items, p->joint_pair_items_h);
+  up(L.pairs, p->joint_pairs);
+  up(L.total + J.row_ptr, p->jn_row_ptr_h);
+  up(L.total + J.row_ent, p->jn_row_ent_h);
+  if (e != cudaSuccess) return cuda_fail(e, "joint upload");
+  p->joint_dev = b;
+  p->jn_dev = b + L.total;
+  p->joint_built = true;
+  return CELESTE_OK;
 }

@@ -435,8 +435,6 @@ celeste_problem::~celeste_problem() {
   for (cudaEvent_t ev : iter_events) cudaEventDestroy(ev);
   if (newton_exec) cudaGraphExecDestroy(newton_exec);
   if (capture_stream) cudaStreamDestroy(capture_stream);
-  if (joint_dev) cudaFree(joint_dev);
-  if (jn_dev) cudaFree(jn_dev);
 }
 
 extern "C" void celeste_problem_destroy(celeste_problem* p) { delete p; }

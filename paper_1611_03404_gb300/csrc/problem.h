@@ -53,8 +53,9 @@ struct celeste_problem {
   std::vector<int> joint_pairs;                       // [n_pairs][2] sources s < t
   std::vector<int> joint_items_h, joint_tiles_h, joint_pair_items_h;   // flat int records
   int joint_n_items = 0, joint_n_tiles = 0;
-  void* joint_dev = nullptr;                          // items, tiles, pair CSR, tile partials
-  void* jn_dev = nullptr;                             // joint Newton state (built on first use)
+  void* joint_dev = nullptr;                          // items, tiles, pair CSR, tile partials (caller memory)
+  void* jn_dev = nullptr;                             // joint Newton state (caller memory, after the above)
+  std::vector<int> jn_row_ptr_h, jn_row_ent_h;        // each source's coupling entries, uploaded at joint bind
   // profiling (celeste_profile_start/stop)
   bool prof_on = false;
   std::vector<cudaEvent_t> prof_events;

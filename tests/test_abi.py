@@ -149,3 +149,17 @@ def test_joint_pairs_empty_when_no_window_overlaps(pkg):
     sc = synth.tiny(seed=11, n_sources=3, n_images=3)
     sc.radius = np.full_like(sc.radius, 1)
     assert len(pkg.HostProblem(sc, tile_pixels=128).joint_pairs()) == 0
+
+
+def test_joint_workspace_is_caller_bound(pkg):
+    """The joint calls' memory is a caller-bound workspace: its size is known on the host, and binding
+    needs a bound problem (no device memory is touched here)."""
+    import ctypes
+    sc = synth.tiny(seed=3, n_sources=5, n_images=2, H=40, W=44, radius=(6, 12))
+    hp = pkg.HostProblem(sc, tile_pixels=128)
+    L = pkg.lib()
+    n = L.celeste_joint_workspace_bytes(hp.handle)
+    assert n > 0 and n % 256 == 0
+    assert L.celeste_joint_workspace_bytes(None) == 0
+    rc = L.celeste_joint_bind(hp.handle, ctypes.c_void_p(256), ctypes.c_size_t(n), None)
+    assert rc == 5 and "bind the problem" in L.celeste_last_error_detail().decode()
