@@ -387,10 +387,28 @@ size_t celeste_cnn_workspace_bytes(int batch);
 int celeste_cnn_init(float* params, uint16_t* params_bf16, uint64_t seed, celeste_stream_t stream);
 
 /* y [batch][27] = network(x [batch][32][32][5]); with out_scale / out_shift (both or neither,
- * [27]) the output is y * scale + shift.  Keeps the activations in ws for celeste_cnn_backward. */
+ * [27]) the output is y * scale + shift.  Keeps the activations in ws for celeste_cnn_backward.
+ * Runs on the tcgen05 tensor cores (celeste_cnn_forward_ex with CELESTE_CNN_TCGEN05). */
 int celeste_cnn_forward(const float* params, const uint16_t* params_bf16, const uint16_t* x, int batch,
                         const float* out_scale, const float* out_shift, float* y, void* ws, size_t ws_bytes,
                         celeste_stream_t stream);
+
+/* The same forward pass on a chosen engine:
+ *   CELESTE_CNN_MMA_SYNC (0): one implicit-GEMM kernel per layer, warp-level mma.sync m16n8k16;
+ *   CELESTE_CNN_TCGEN05 (1): per layer a GEMM on the fifth-generation tensor cores, 128-row tiles,
+ *     operands gathered into 128-byte-swizzled shared memory, tcgen05.mma into a tensor-memory
+ *     accumulator, tcgen05.ld epilogue (bias, ReLU).  Waits are bounded: a product that does not
+ *     complete sets an error word that celeste_cnn_status reports.
+ * Both use BF16 operands and FP32 accumulation; their outputs differ only in summation order. */
+enum { CELESTE_CNN_MMA_SYNC = 0, CELESTE_CNN_TCGEN05 = 1 };
+int celeste_cnn_forward_ex(const float* params, const uint16_t* params_bf16, const uint16_t* x, int batch,
+                           const float* out_scale, const float* out_shift, float* y, void* ws, size_t ws_bytes,
+                           int engine, celeste_stream_t stream);
+
+/* CELESTE_ERR_TIMEOUT (and clears it) if a tensor-core product of the network's forward pass did not
+ * complete within its wait budget since the last call; CELESTE_OK otherwise.  Synchronous (reads a
+ * device word of the current device). */
+int celeste_cnn_status(void);
 
 /* grad [param_count] += d loss / d params given dy = d loss / d y [batch][27], after a forward
  * call on the same x, ws and parameters (without scale / shift). */

@@ -10,7 +10,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT, "libceleste.so")
 SOURCES = ["pixels.cu", "tables.cu", "background.cu", "assemble.cu", "newton.cu", "problem.cu", "api.cu", "no_alloc.cu",
-           "cnn.cu", "cov.cu", "joint.cu", "peaks.cu"]
+           "cnn.cu", "cnn_tc.cu", "cov.cu", "joint.cu", "peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

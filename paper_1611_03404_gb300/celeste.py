@@ -59,7 +59,8 @@ EXPORTED = ["celeste_problem_create", "celeste_problem_workspace_bytes", "celest
             "celeste_cnn_mse", "celeste_cnn_adamw", "celeste_extract_patches", "celeste_covariance_batch",
             "celeste_render_background_mode", "celeste_joint_pairs", "celeste_joint_cross_hessian",
             "celeste_joint_newton", "celeste_joint_value", "celeste_problem_check", "celeste_problem_set_wait_budget",
-            "celeste_measure_peak", "celeste_joint_workspace_bytes", "celeste_joint_bind"]
+            "celeste_measure_peak", "celeste_joint_workspace_bytes", "celeste_joint_bind", "celeste_cnn_forward_ex",
+            "celeste_cnn_status"]
 
 
 def load_library(path=None):
@@ -102,6 +103,9 @@ def load_library(path=None):
         "celeste_measure_peak": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                                 ctypes.POINTER(ctypes.c_double), vp]),
         "celeste_joint_workspace_bytes": (ctypes.c_size_t, [vp]),
+        "celeste_cnn_forward_ex": (ctypes.c_int, [dp, dp, dp, ctypes.c_int, dp, dp, dp, dp, ctypes.c_size_t,
+                                                  ctypes.c_int, vp]),
+        "celeste_cnn_status": (ctypes.c_int, []),
         "celeste_joint_bind": (ctypes.c_int, [vp, vp, ctypes.c_size_t, vp]),
         "celeste_joint_newton": (ctypes.c_int, [vp, dp, ctypes.POINTER(NewtonOpts), ctypes.c_int32,
                                                 ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),

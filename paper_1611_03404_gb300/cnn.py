@@ -20,6 +20,7 @@ from .celeste import NPARAM, _check, _ptr, _stream, lib
 
 PATCH = 32
 BANDS = 5
+ENGINE_MMA_SYNC, ENGINE_TCGEN05 = 0, 1
 # parameters taken from the network by default (indices in the 27-vector): the type logit (6)
 # and the log variances of the log fluxes (8, 10) and of the colours (15-18, 23-26), which the
 # catalog does not carry; position, shape, flux and colour means stay the catalog's
@@ -53,16 +54,29 @@ class WarmStartCNN:
             self._ws[batch] = _aligned(int(lib().celeste_cnn_workspace_bytes(batch)), self.device)
         return self._ws[batch]
 
-    def forward(self, x, standardised=True):
-        """x: int16 [B, 32, 32, 5] (BF16 bits) -> [B, 27] float32 (standardised, or parameter space)."""
+    def forward(self, x, standardised=True, engine=None):
+        """x: int16 [B, 32, 32, 5] (BF16 bits) -> [B, 27] float32 (standardised, or parameter space).
+        engine: None (the library's default), ENGINE_MMA_SYNC or ENGINE_TCGEN05."""
         assert x.dtype == torch.int16 and x.is_contiguous() and tuple(x.shape[1:]) == (PATCH, PATCH, BANDS)
         B = x.shape[0]
         y = torch.empty(B, NPARAM, dtype=torch.float32, device=self.device)
         _, ws, nb = self.workspace(B)
         sc, sh = (None, None) if standardised else (self.sd, self.mu)
-        _check(lib().celeste_cnn_forward(_ptr(self.params), _ptr(self.params_bf16), _ptr(x), B, _ptr(sc), _ptr(sh),
-                                         _ptr(y), ws, ctypes.c_size_t(nb), _stream(None)))
+        if engine is None:
+            _check(lib().celeste_cnn_forward(_ptr(self.params), _ptr(self.params_bf16), _ptr(x), B, _ptr(sc),
+                                             _ptr(sh), _ptr(y), ws, ctypes.c_size_t(nb), _stream(None)))
+        else:
+            _check(lib().celeste_cnn_forward_ex(_ptr(self.params), _ptr(self.params_bf16), _ptr(x), B, _ptr(sc),
+                                                _ptr(sh), _ptr(y), ws, ctypes.c_size_t(nb), ctypes.c_int(engine),
+                                                _stream(None)))
         return y
+
+    def activations(self, batch):
+        """The first hidden layer's activations kept in the workspace by the last forward call at this
+        batch size: int16 [batch, 32, 32, 32] (BF16 bits)."""
+        buf, ws, _ = self.workspace(batch)
+        off = ws.value - buf.data_ptr()
+        return buf[off:off + batch * 32 * 32 * 32 * 2].view(torch.int16).view(batch, 32, 32, 32)
 
     def backward(self, x, dy):
         assert x.dtype == torch.int16 and dy.dtype == torch.float32 and dy.is_contiguous()

@@ -20,6 +20,7 @@
 #include <cstdint>
 
 #include "celeste_internal.cuh"
+#include "cnn_tc.h"
 #include "problem.h"
 
 namespace celeste {
@@ -435,11 +436,33 @@ static int check_ws(int batch, const void* ws, size_t bytes) {
   return CELESTE_OK;
 }
 
+// Error word of the tensor-core forward path (a bounded wait that ran out).
+static __device__ int g_cnn_tc_err;
+
+extern "C" int celeste_cnn_status(void) {
+  int v = 0;
+  cudaError_t e = cudaMemcpyFromSymbol(&v, g_cnn_tc_err, sizeof(int));
+  if (e != cudaSuccess) return cuda_fail(e, "cnn status");
+  if (!v) return CELESTE_OK;
+  const int zero = 0;
+  cudaMemcpyToSymbol(g_cnn_tc_err, &zero, sizeof(int));
+  return fail(CELESTE_ERR_TIMEOUT, "a tensor-core product of the network did not complete in time");
+}
+
 extern "C" int celeste_cnn_forward(const float* params, const uint16_t* params_bf16, const uint16_t* x, int batch,
                                    const float* out_scale, const float* out_shift, float* y, void* ws,
                                    size_t ws_bytes, celeste_stream_t stream) {
+  return celeste_cnn_forward_ex(params, params_bf16, x, batch, out_scale, out_shift, y, ws, ws_bytes,
+                                CELESTE_CNN_TCGEN05, stream);
+}
+
+extern "C" int celeste_cnn_forward_ex(const float* params, const uint16_t* params_bf16, const uint16_t* x, int batch,
+                                      const float* out_scale, const float* out_shift, float* y, void* ws,
+                                      size_t ws_bytes, int engine, celeste_stream_t stream) {
   if (!params || !params_bf16 || !x || !y) return fail(CELESTE_ERR_INVALID_ARG, "null argument");
   if ((out_scale == nullptr) != (out_shift == nullptr)) return fail(CELESTE_ERR_INVALID_ARG, "scale and shift go together");
+  if (engine != CELESTE_CNN_MMA_SYNC && engine != CELESTE_CNN_TCGEN05)
+    return fail(CELESTE_ERR_INVALID_ARG, "engine must be CELESTE_CNN_MMA_SYNC or CELESTE_CNN_TCGEN05");
   int rc = check_ws(batch, ws, ws_bytes);
   if (rc != CELESTE_OK) return rc;
   cudaStream_t st = (cudaStream_t)stream;
@@ -451,6 +474,34 @@ extern "C" int celeste_cnn_forward(const float* params, const uint16_t* params_b
   cudaError_t e;
   ConvGeom g1{B, 32, 32, CIN, 32, 32, C1, 1}, g2{B, 32, 32, C1, 16, 16, C2, 2};
   ConvGeom g3{B, 16, 16, C2, 8, 8, C3, 2}, g4{B, 8, 8, C3, 4, 4, C4, 2};
+  if (engine == CELESTE_CNN_TCGEN05) {
+    int* err = nullptr;
+    if ((e = cudaGetSymbolAddress(reinterpret_cast<void**>(&err), g_cnn_tc_err)) != cudaSuccess)
+      return cuda_fail(e, "cnn error word");
+    auto conv = [&](const ConvGeom& g, const bf16* in, int64_t wo, int64_t bo, bf16* out) {
+      cnn_tc::Args a{};
+      a.M = g.B * g.OH * g.OW;
+      a.N = g.Cout;
+      a.K = 9 * g.Cin;
+      a.conv = 1;
+      a.B = g.B, a.H = g.H, a.W = g.W, a.Cin = g.Cin, a.OH = g.OH, a.OW = g.OW, a.stride = g.stride;
+      a.in = in, a.w = pb + wo, a.bias = params + bo, a.out = out, a.err = err;
+      return tc_gemm_forward(a, st);
+    };
+    auto fc = [&](int nin, int nout, const bf16* in, int64_t wo, int64_t bo, bf16* out, float* outf) {
+      cnn_tc::Args a{};
+      a.M = B, a.N = nout, a.K = nin, a.conv = 0;
+      a.in = in, a.w = pb + wo, a.bias = params + bo, a.out = out, a.out_f = outf, a.scale = out_scale,
+      a.shift = out_shift, a.err = err;
+      return tc_gemm_forward(a, st);
+    };
+    if ((e = conv(g1, xin, o.w1, o.b1, w.a1)) != cudaSuccess || (e = conv(g2, w.a1, o.w2, o.b2, w.a2)) != cudaSuccess ||
+        (e = conv(g3, w.a2, o.w3, o.b3, w.a3)) != cudaSuccess || (e = conv(g4, w.a3, o.w4, o.b4, w.a4)) != cudaSuccess ||
+        (e = fc(FLAT, F5, w.a4, o.w5, o.b5, w.a5, nullptr)) != cudaSuccess ||
+        (e = fc(F5, NOUT, w.a5, o.w6, o.b6, nullptr, y)) != cudaSuccess)
+      return cuda_fail(e, "cnn forward (tensor cores)");
+    return CELESTE_OK;
+  }
   if ((e = gemm(ConvFwd{g1, xin, pb + o.w1, params + o.b1, w.a1}, B * 1024, C1, 9 * CIN, 1, st)) != cudaSuccess ||
       (e = gemm(ConvFwd{g2, w.a1, pb + o.w2, params + o.b2, w.a2}, B * 256, C2, 9 * C1, 1, st)) != cudaSuccess ||
       (e = gemm(ConvFwd{g3, w.a2, pb + o.w3, params + o.b3, w.a3}, B * 64, C3, 9 * C2, 1, st)) != cudaSuccess ||

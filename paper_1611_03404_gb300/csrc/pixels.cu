@@ -67,13 +67,19 @@ __device__ __forceinline__ float warp_reduce_scatter32(float (&v)[32], int lane)
 // Thread 0: bulk copies of tile `tile`'s patch table and pixel records into (tab, spix),
 // completing on bar (one expect_tx for both).  The caller has synchronised the CTA since the
 // buffer was last read; the proxy fence orders those generic reads before the async writes.
-__device__ __forceinline__ void issue_tile(const ProblemDev& P, int tile, float* tab, float4* spix, uint64_t* bar) {
+// The tile's and its patch's records go to shared memory too (tm, pm), so that the other threads
+// read them there after the wait instead of two dependent global loads at the start of the tile.
+__device__ __forceinline__ void issue_tile(const ProblemDev& P, int tile, float* tab, float4* spix, uint64_t* bar,
+                                           TileDev* tm, PatchDev* pm) {
   const TileDev t = P.tiles[tile];
+  const PatchDev pt = P.patches[t.patch];
   fence_proxy_async_smem();
   const uint32_t tb = TB_FLOATS * 4u, pb = (uint32_t)t.count * 16u;
   mbar_expect_tx(bar, tb + pb);
   bulk_copy(tab, P.ptab + (size_t)t.patch * TB_FLOATS, tb, bar);
-  bulk_copy(spix, P.pix + P.patches[t.patch].pix_off + t.start, pb, bar);
+  bulk_copy(spix, P.pix + pt.pix_off + t.start, pb, bar);
+  *tm = t;
+  *pm = pt;
 }
 
 // All threads: wait (bounded by P.wait_budget) for a staged buffer.  On a timeout: error word, a
@@ -356,6 +362,8 @@ __global__ void __launch_bounds__(BLOCK) elbo_full_kernel(ProblemDev P) {
   __shared__ __align__(16) float tab_buf[NB][TB_FLOATS];
   __shared__ __align__(16) float4 spix_buf[NB][BLOCK * PPT];
   __shared__ __align__(8) uint64_t bar[NB];
+  __shared__ TileDev tmeta[NB];
+  __shared__ PatchDev pmeta[NB];
   __shared__ float red[BLOCK / 32][128];
   __shared__ __align__(16) float syrk[HM ? BLOCK / 32 : 1][2][16][SYRK_LD];
 
@@ -375,7 +383,7 @@ __global__ void __launch_bounds__(BLOCK) elbo_full_kernel(ProblemDev P) {
   // closing barrier.
   if (tid == 0) {
     slot = wl_take(P, WL_TILES);
-    if (slot >= 0) issue_tile(P, slot, tab_buf[0], spix_buf[0], &bar[0]);
+    if (slot >= 0) issue_tile(P, slot, tab_buf[0], spix_buf[0], &bar[0], &tmeta[0], &pmeta[0]);
   }
   __syncthreads();
   int tile = slot;
@@ -383,7 +391,7 @@ __global__ void __launch_bounds__(BLOCK) elbo_full_kernel(ProblemDev P) {
   const int b = NB == 2 ? (int)(it & 1u) : 0;
   if (NB == 2 && tid == 0) {
     slot = wl_take(P, WL_TILES);
-    if (slot >= 0) issue_tile(P, slot, tab_buf[b ^ 1], spix_buf[b ^ 1], &bar[b ^ 1]);
+    if (slot >= 0) issue_tile(P, slot, tab_buf[b ^ 1], spix_buf[b ^ 1], &bar[b ^ 1], &tmeta[b ^ 1], &pmeta[b ^ 1]);
   }
   if (!wait_tile(P, &bar[b], (it / NB) & 1u, &bar[b ^ (NB - 1)], ((it + 1) / NB) & 1u, NB == 2 && slot >= 0)) {
     if (tid < NACC) P.partials[(size_t)tile * NACC + tid] = __int_as_float(0x7fc00000);
@@ -391,8 +399,8 @@ __global__ void __launch_bounds__(BLOCK) elbo_full_kernel(ProblemDev P) {
   }
   const float* tab = tab_buf[b];
   const float4* spix = spix_buf[b];
-  const TileDev t = P.tiles[tile];
-  const PatchDev pt = P.patches[t.patch];
+  const TileDev t = tmeta[b];
+  const PatchDev pt = pmeta[b];
   if (tid == 0) atomicAdd(P.counters + 0, (unsigned long long)t.count);
   const SNConst c = *reinterpret_cast<const SNConst*>(&tab[TB_SNC]);
   float acc[4] = {0.f, 0.f, 0.f, 0.f};
@@ -591,7 +599,7 @@ __global__ void __launch_bounds__(BLOCK) elbo_full_kernel(ProblemDev P) {
   if constexpr (NB == 1) {
     if (tid == 0) {
       slot = wl_take(P, WL_TILES);
-      if (slot >= 0) issue_tile(P, slot, tab_buf[0], spix_buf[0], &bar[0]);
+      if (slot >= 0) issue_tile(P, slot, tab_buf[0], spix_buf[0], &bar[0], &tmeta[0], &pmeta[0]);
     }
     __syncthreads();
     tile = slot;
@@ -611,6 +619,8 @@ __global__ void __launch_bounds__(BLOCK) elbo_value_kernel(ProblemDev P, int dif
   __shared__ __align__(16) float tab_buf[2][TB_FLOATS];
   __shared__ __align__(16) float4 spix_buf[2][BLOCK * PPT];
   __shared__ __align__(8) uint64_t bar[2];
+  __shared__ TileDev tmeta[2];
+  __shared__ PatchDev pmeta[2];
   __shared__ float red[BLOCK / 32];
 
   __shared__ int slot;
@@ -621,7 +631,7 @@ __global__ void __launch_bounds__(BLOCK) elbo_value_kernel(ProblemDev P, int dif
   }
   if (tid == 0) {
     slot = wl_take(P, WL_TILES);
-    if (slot >= 0) issue_tile(P, slot, tab_buf[0], spix_buf[0], &bar[0]);
+    if (slot >= 0) issue_tile(P, slot, tab_buf[0], spix_buf[0], &bar[0], &tmeta[0], &pmeta[0]);
   }
   __syncthreads();
   int tile = slot;
@@ -629,7 +639,7 @@ __global__ void __launch_bounds__(BLOCK) elbo_value_kernel(ProblemDev P, int dif
   const int b = (int)(it & 1u);
   if (tid == 0) {
     slot = wl_take(P, WL_TILES);
-    if (slot >= 0) issue_tile(P, slot, tab_buf[b ^ 1], spix_buf[b ^ 1], &bar[b ^ 1]);
+    if (slot >= 0) issue_tile(P, slot, tab_buf[b ^ 1], spix_buf[b ^ 1], &bar[b ^ 1], &tmeta[b ^ 1], &pmeta[b ^ 1]);
   }
   if (!wait_tile(P, &bar[b], (it >> 1) & 1u, &bar[b ^ 1], ((it + 1) >> 1) & 1u, slot >= 0)) {
     if (tid == 0) P.vpartials[tile] = __int_as_float(0x7fc00000);
@@ -637,8 +647,8 @@ __global__ void __launch_bounds__(BLOCK) elbo_value_kernel(ProblemDev P, int dif
   }
   const float* tab = tab_buf[b];
   const float4* spix = spix_buf[b];
-  const TileDev t = P.tiles[tile];
-  const PatchDev pt = P.patches[t.patch];
+  const TileDev t = tmeta[b];
+  const PatchDev pt = pmeta[b];
   if (tid == 0) atomicAdd(P.counters + 1, (unsigned long long)t.count);
   const SNConst c = *reinterpret_cast<const SNConst*>(&tab[TB_SNC]);
   float sum = 0.f;
@@ -650,6 +660,17 @@ __global__ void __launch_bounds__(BLOCK) elbo_value_kernel(ProblemDev P, int dif
     const int row = idx / pt.w, col = idx - row * pt.w;
     const float fx = (float)col, fy = (float)row;
     const float4 pv = spix[i];
+    // the pixel's reference values, loaded ahead of the profiles so that their latency overlaps them
+    float2 ref = make_float2(0.f, 0.f);
+    float wpx = 1.f;
+    if (diff == 2) {
+      ref = P.refEV[pt.pix_off + idx];
+      wpx = P.pweight[pt.pix_off + idx];
+    } else if (diff) {
+      ref = P.srcmom[pt.pix_off + idx];
+    } else if (P.pweight) {
+      wpx = P.pweight[pt.pix_off + idx];
+    }
     float f0 = 0.f, fE = 0.f, fD = 0.f;
 #pragma unroll
     for (int k = 0; k < CELESTE_NPSF; ++k) {
@@ -677,21 +698,17 @@ __global__ void __launch_bounds__(BLOCK) elbo_value_kernel(ProblemDev P, int dif
     if (diff == 2) {
       // joint objective: every source may have moved; the change from the stored pixel rates at
       // the reference point, weighted by 1 / (windows holding the pixel)
-      const float2 ref = P.refEV[pt.pix_off + idx];
-      const float w = P.pweight[pt.pix_off + idx];
       const float dE = E - ref.x;
-      sum += w * (x > 0.f ? x * log1pf(dE / ref.x) - dE - 0.5f * x * (V / (E * E) - ref.y / (ref.x * ref.x)) : -dE);
+      sum += wpx * (x > 0.f ? x * log1pf(dE / ref.x) - dE - 0.5f * x * (V / (E * E) - ref.y / (ref.x * ref.x)) : -dE);
     } else if (diff) {
-      const float2 ref = P.srcmom[pt.pix_off + idx];
       const float dE = c.iota * (EG - ref.x);                  // E(theta) - E(theta_ref)
       const float Er = pv.y + c.iota * ref.x;
       const float Vr = pv.z + c.iota * c.iota * ref.y;
       sum += x > 0.f ? x * log1pf(dE / Er) - dE - 0.5f * x * (V / (E * E) - Vr / (Er * Er)) : -dE;
     } else {
       // pixel weight: 1 / (windows holding the pixel) for the joint objective, else 1
-      const float w = P.pweight ? P.pweight[pt.pix_off + idx] : 1.f;
       const float dEx = E - x;
-      sum += w * (x > 0.f ? pv.w + x * log1pf(dEx / x) - dEx - 0.5f * x * V / (E * E) : -E);
+      sum += wpx * (x > 0.f ? pv.w + x * log1pf(dEx / x) - dEx - 0.5f * x * V / (E * E) : -E);
     }
   }
 #pragma unroll

@@ -122,3 +122,43 @@ def test_patch_extraction_matches_oracle(P):
     for s in range(sc.n_sources):
         ref = C.extract_patch(sc, s, cen)
         assert np.all(np.abs(x[s] - ref) <= 2.0 ** -8 * np.abs(ref) + 1e-6), s
+
+
+@pytest.mark.parametrize("B", [300, 4096])
+def test_tcgen05_forward_matches_mma_sync_and_oracle(P, B):
+    """The forward pass on the tcgen05 tensor cores (tensor-memory accumulator, 128-row tiles) against
+    the warp-level mma.sync engine and the float64 oracle: the same BF16 operands and FP32
+    accumulation, so the two engines differ only in summation order (the first layer's BF16
+    activations within a few units in the last place, the outputs within 1e-2 of their scale), and
+    both stay within the oracle test's 3 % of the output scale.  B = 300 leaves partial last tiles in
+    the dense layers and the last convolution."""
+    pkg, cnn = P
+    dev = torch.device("cuda:0")
+    net = cnn.WarmStartCNN(dev, seed=13)
+    net.params += 0.05 * torch.randn(net.n, device=dev, dtype=torch.float32,
+                                     generator=torch.Generator(device=dev).manual_seed(4))
+    net.params_bf16.copy_(_bf16_bits(net.params))
+    x = _bf16_bits(torch.randn(B, 32, 32, 5, device=dev, dtype=torch.float32,
+                               generator=torch.Generator(device=dev).manual_seed(5)))
+    y_ref = net.forward(x, engine=cnn.ENGINE_MMA_SYNC)
+    a1_ref = net.activations(B).clone()
+    y_tc = net.forward(x, engine=cnn.ENGINE_TCGEN05)
+    torch.cuda.synchronize()
+    assert pkg.lib().celeste_cnn_status() == 0
+    a1_tc = net.activations(B).clone()
+    a_ref = a1_ref.view(torch.bfloat16).float()
+    a_tc = a1_tc.view(torch.bfloat16).float()
+    assert float((a_tc - a_ref).abs().max()) <= 2 ** -6 * float(a_ref.abs().max())
+    assert float((a_tc - a_ref).norm() / a_ref.norm()) <= 2e-3
+    scale = float(y_ref.double().pow(2).mean().sqrt())
+    assert float((y_tc.double() - y_ref.double()).abs().max()) <= 1e-2 * scale
+    # against the oracle on a sample of the batch
+    pw = _from_bits(net.params_bf16)
+    offs = np.cumsum([0] + [int(np.prod(s)) for _, s in C.SHAPES])
+    for k, (name, _) in enumerate(C.SHAPES):
+        if name.startswith("b"):
+            pw[offs[k]:offs[k + 1]] = net.params[offs[k]:offs[k + 1]].double().cpu()
+    idx = torch.arange(0, B, max(1, B // 64))
+    yr = C.forward(pw, _from_bits(x[idx.to(dev)]))
+    s_or = float(yr.pow(2).mean().sqrt())
+    assert float((y_tc[idx.to(dev)].double().cpu() - yr).abs().max()) <= 3e-2 * s_or
