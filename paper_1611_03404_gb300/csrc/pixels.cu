@@ -216,23 +216,28 @@ __device__ __forceinline__ void split_tf32(float x, uint32_t& big, uint32_t& sma
 }
 
 // D[nt] (16 x 8 tiles nt = 0, 1) += A' B' for this warp's staged 32 pixels.
+// Rows 11..15 of the 16-row fragments are the zero padding of the 11 x 11 block: they read `zrow`
+// (a zero row in shared memory) instead of staged rows.
 template <int HM>
-__device__ __forceinline__ void syrk_mma(const float (*As)[SYRK_LD], const float (*Bt)[SYRK_LD], float (&d)[2][4],
-                                         int lane) {
+__device__ __forceinline__ void syrk_mma(const float (*As)[SYRK_LD], const float (*Bt)[SYRK_LD], const float* zrow,
+                                         float (&d)[2][4], int lane) {
   const int g = lane >> 2, t = lane & 3;
+  const float* A0 = As[g];
+  const float* A1 = g + 8 < NRED ? As[g + 8] : zrow;
+  const float* Bn[2] = {Bt[g], g + 8 < NRED ? Bt[g + 8] : zrow};
   if constexpr (HM == 4) {
 #pragma unroll
     for (int k0 = 0; k0 < 64; k0 += 8) {
       uint32_t ab[4], as[4];
-      split_tf32(As[g][k0 + t], ab[0], as[0]);
-      split_tf32(As[g + 8][k0 + t], ab[1], as[1]);
-      split_tf32(As[g][k0 + t + 4], ab[2], as[2]);
-      split_tf32(As[g + 8][k0 + t + 4], ab[3], as[3]);
+      split_tf32(A0[k0 + t], ab[0], as[0]);
+      split_tf32(A1[k0 + t], ab[1], as[1]);
+      split_tf32(A0[k0 + t + 4], ab[2], as[2]);
+      split_tf32(A1[k0 + t + 4], ab[3], as[3]);
 #pragma unroll
       for (int nt = 0; nt < 2; ++nt) {
         uint32_t bb0, bs0, bb1, bs1;
-        split_tf32(Bt[8 * nt + g][k0 + t], bb0, bs0);
-        split_tf32(Bt[8 * nt + g][k0 + t + 4], bb1, bs1);
+        split_tf32(Bn[nt][k0 + t], bb0, bs0);
+        split_tf32(Bn[nt][k0 + t + 4], bb1, bs1);
         mma_tf32(d[nt], as[0], as[1], as[2], as[3], bb0, bb1);   // small terms first
         mma_tf32(d[nt], ab[0], ab[1], ab[2], ab[3], bs0, bs1);
         mma_tf32(d[nt], ab[0], ab[1], ab[2], ab[3], bb0, bb1);
@@ -242,15 +247,15 @@ __device__ __forceinline__ void syrk_mma(const float (*As)[SYRK_LD], const float
 #pragma unroll
     for (int k0 = 0; k0 < 64; k0 += 16) {
       uint32_t ah[4], am[4], al[4];
-      split3_bf16x2(&As[g][k0 + 2 * t], ah[0], am[0], al[0]);
-      split3_bf16x2(&As[g + 8][k0 + 2 * t], ah[1], am[1], al[1]);
-      split3_bf16x2(&As[g][k0 + 2 * t + 8], ah[2], am[2], al[2]);
-      split3_bf16x2(&As[g + 8][k0 + 2 * t + 8], ah[3], am[3], al[3]);
+      split3_bf16x2(&A0[k0 + 2 * t], ah[0], am[0], al[0]);
+      split3_bf16x2(&A1[k0 + 2 * t], ah[1], am[1], al[1]);
+      split3_bf16x2(&A0[k0 + 2 * t + 8], ah[2], am[2], al[2]);
+      split3_bf16x2(&A1[k0 + 2 * t + 8], ah[3], am[3], al[3]);
 #pragma unroll
       for (int nt = 0; nt < 2; ++nt) {
         uint32_t bh0, bm0, bl0, bh1, bm1, bl1;
-        split3_bf16x2(&Bt[8 * nt + g][k0 + 2 * t], bh0, bm0, bl0);
-        split3_bf16x2(&Bt[8 * nt + g][k0 + 2 * t + 8], bh1, bm1, bl1);
+        split3_bf16x2(&Bn[nt][k0 + 2 * t], bh0, bm0, bl0);
+        split3_bf16x2(&Bn[nt][k0 + 2 * t + 8], bh1, bm1, bl1);
         mma_bf16(d[nt], al[0], al[1], al[2], al[3], bh0, bh1);   // small terms first
         mma_bf16(d[nt], ah[0], ah[1], ah[2], ah[3], bl0, bl1);
         mma_bf16(d[nt], am[0], am[1], am[2], am[3], bm0, bm1);
@@ -262,11 +267,11 @@ __device__ __forceinline__ void syrk_mma(const float (*As)[SYRK_LD], const float
   } else if constexpr (HM == 1) {
 #pragma unroll
     for (int k0 = 0; k0 < 64; k0 += 8) {
-      const uint32_t a0 = to_tf32(As[g][k0 + t]), a1 = to_tf32(As[g + 8][k0 + t]);
-      const uint32_t a2 = to_tf32(As[g][k0 + t + 4]), a3 = to_tf32(As[g + 8][k0 + t + 4]);
+      const uint32_t a0 = to_tf32(A0[k0 + t]), a1 = to_tf32(A1[k0 + t]);
+      const uint32_t a2 = to_tf32(A0[k0 + t + 4]), a3 = to_tf32(A1[k0 + t + 4]);
 #pragma unroll
       for (int nt = 0; nt < 2; ++nt) {
-        const uint32_t b0 = to_tf32(Bt[8 * nt + g][k0 + t]), b1 = to_tf32(Bt[8 * nt + g][k0 + t + 4]);
+        const uint32_t b0 = to_tf32(Bn[nt][k0 + t]), b1 = to_tf32(Bn[nt][k0 + t + 4]);
         mma_tf32(d[nt], a0, a1, a2, a3, b0, b1);
       }
     }
@@ -274,15 +279,15 @@ __device__ __forceinline__ void syrk_mma(const float (*As)[SYRK_LD], const float
 #pragma unroll
     for (int k0 = 0; k0 < 64; k0 += 16) {
       uint32_t ah[4], al[4];
-      split_bf16x2(&As[g][k0 + 2 * t], ah[0], al[0]);
-      split_bf16x2(&As[g + 8][k0 + 2 * t], ah[1], al[1]);
-      split_bf16x2(&As[g][k0 + 2 * t + 8], ah[2], al[2]);
-      split_bf16x2(&As[g + 8][k0 + 2 * t + 8], ah[3], al[3]);
+      split_bf16x2(&A0[k0 + 2 * t], ah[0], al[0]);
+      split_bf16x2(&A1[k0 + 2 * t], ah[1], al[1]);
+      split_bf16x2(&A0[k0 + 2 * t + 8], ah[2], al[2]);
+      split_bf16x2(&A1[k0 + 2 * t + 8], ah[3], al[3]);
 #pragma unroll
       for (int nt = 0; nt < 2; ++nt) {
         uint32_t bh0, bl0, bh1, bl1;
-        split_bf16x2(&Bt[8 * nt + g][k0 + 2 * t], bh0, bl0);
-        split_bf16x2(&Bt[8 * nt + g][k0 + 2 * t + 8], bh1, bl1);
+        split_bf16x2(&Bn[nt][k0 + 2 * t], bh0, bl0);
+        split_bf16x2(&Bn[nt][k0 + 2 * t + 8], bh1, bl1);
         mma_bf16(d[nt], ah[0], ah[1], ah[2], ah[3], bh0, bh1);
         mma_bf16(d[nt], ah[0], ah[1], ah[2], ah[3], bl0, bl1);
         mma_bf16(d[nt], al[0], al[1], al[2], al[3], bh0, bh1);
@@ -353,29 +358,28 @@ __device__ __forceinline__ void gal_component(const float* ep, float d0, float d
 // ------------------------------------------------------------------------------ full kernel
 // HM: 0 all sums on the FP32 pipes; 1 / 2 the Jacobian cross-product on the tensor cores with
 // TF32 / BF16 hi+lo operands.
-// Tiles are double-buffered (HM = 0): the next tile's copies are issued before the current one
-// is evaluated.  The tensor-core variants keep one buffer (their staging area fills the rest of
-// the 48 KB of static shared memory).
+// Tiles are double-buffered: the next tile's copies are issued before the current one is
+// evaluated.  (The tensor-core variants' staging area holds the 11 rows of A' and B'^T per warp;
+// the fragments' padding rows read one shared zero row, which keeps both buffers within the 48 KB
+// of static shared memory.)
 template <int PPT, int HM>
 __global__ void __launch_bounds__(BLOCK) elbo_full_kernel(ProblemDev P) {
-  constexpr int NB = HM == 0 ? 2 : 1;
+  constexpr int NB = 2;
   __shared__ __align__(16) float tab_buf[NB][TB_FLOATS];
   __shared__ __align__(16) float4 spix_buf[NB][BLOCK * PPT];
   __shared__ __align__(8) uint64_t bar[NB];
   __shared__ TileDev tmeta[NB];
   __shared__ PatchDev pmeta[NB];
   __shared__ float red[BLOCK / 32][128];
-  __shared__ __align__(16) float syrk[HM ? BLOCK / 32 : 1][2][16][SYRK_LD];
+  __shared__ __align__(16) float syrk[HM ? BLOCK / 32 : 1][2][NRED][SYRK_LD];
+  __shared__ __align__(16) float zrow[HM ? SYRK_LD : 4];
 
   __shared__ int slot;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid == 0)
     for (int b = 0; b < NB; ++b) mbar_init(&bar[b], 1);
-  if constexpr (HM != 0) {   // padding rows 11..15 of A' and B'^T stay zero
-    for (int i = lane; i < 5 * SYRK_LD; i += 32) {
-      syrk[warp][0][11 + i / SYRK_LD][i % SYRK_LD] = 0.f;
-      syrk[warp][1][11 + i / SYRK_LD][i % SYRK_LD] = 0.f;
-    }
+  if constexpr (HM != 0) {   // the zero row standing for rows 11..15 of A' and B'^T
+    for (int i = tid; i < SYRK_LD; i += BLOCK) zrow[i] = 0.f;
   }
   // Iteration it uses buffer it % NB for its (it / NB + 1)-th time: the barrier's phase parity is
   // (it / NB) & 1.  Thread 0 takes the next tile from the queue and issues its copies; the wait's
@@ -566,7 +570,7 @@ __global__ void __launch_bounds__(BLOCK) elbo_full_kernel(ProblemDev P) {
         Bt[a][32 + lane] = cx.yV[a];
       }
       __syncwarp();
-      syrk_mma<HM>(As, Bt, dm, lane);
+      syrk_mma<HM>(As, Bt, zrow, dm, lane);
       __syncwarp();   // the staging area is rewritten for the next 32 pixels
     }
   }
