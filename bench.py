@@ -629,9 +629,9 @@ def catalog_agreement(th, th_ref, st, st_ref, prob, theta0):
 
 def end_to_end(args, P, prob, scene, step, theta, theta0, flush, stream, world, dev):
     """Through the public API at N GPUs: every step copies the images and the catalog from pinned host
-    memory, rebinds (re-gathers the patch pixels), runs the step and reads the converged catalog and
-    status back; L2 flushed before each step as in the timed loop; the first step warms the pinned
-    buffers and is not counted."""
+    memory, re-gathers the patch pixels from the new images (celeste_problem_refresh_pixels), runs the
+    step and reads the converged catalog and status back; L2 flushed before each step as in the timed
+    loop; the first step warms the pinned buffers and is not counted."""
     import torch
     host_pix = [torch.from_numpy(np.ascontiguousarray(im.pixels)).pin_memory() for im in scene.images]
     host_theta = torch.from_numpy(scene.theta0.copy()).pin_memory()
@@ -647,7 +647,7 @@ def end_to_end(args, P, prob, scene, step, theta, theta0, flush, stream, world, 
         for dp, hp in zip(prob.pixels, host_pix):
             dp.copy_(hp, non_blocking=True)
         theta0.copy_(host_theta, non_blocking=True)
-        prob.rebind()
+        prob.refresh_pixels()
         _, _, status_e, _ = step()
         out_theta.copy_(theta, non_blocking=True)
         out_status.copy_(status_e, non_blocking=True)

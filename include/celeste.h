@@ -160,6 +160,12 @@ int celeste_problem_counts(const celeste_problem* p, int64_t counts[5]);
  * every later call on this problem.  Asynchronous on `stream`. */
 int celeste_problem_bind(celeste_problem* p, void* workspace, size_t bytes, celeste_stream_t stream);
 
+/* New pixel values in the same images (the device buffers given at create, same layout and catalog
+ * positions): re-gathers every patch pixel's count and log-factorial term, as bind does, without
+ * re-uploading the layout; clears the error words.  The background must be rendered again before the
+ * next evaluation.  Asynchronous on `stream`. */
+int celeste_problem_refresh_pixels(celeste_problem* p, celeste_stream_t stream);
+
 /* Fixed part of every patch pixel's rate: gathers the counts and renders the neighbours'
  * expected brightness and variance (Sec. "Variational Inference": neighbours held fixed).
  *   nbr_theta: device float64 [S][27], the parameters the neighbours are fixed at.

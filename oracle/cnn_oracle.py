@@ -48,6 +48,18 @@ def forward(p, x):
     return F.linear(h, w["w6"], w["b6"])
 
 
+def layer_pre(p, k, x):
+    """Layer k's pre-activation (before ReLU) from its input x: k = 1..4 the convolutions (x NHWC
+    [B, H, W, C] -> NHWC), k = 5, 6 the dense layers (x [B, 1024] or [B, 256]; for k = 5 a 4 x 4 x 64
+    map is flattened in (h, w, c) order).  The same arithmetic as `forward`, one layer at a time."""
+    w = unpack(p)
+    if k <= 4:
+        stride = 1 if k == 1 else 2
+        h = F.conv2d(x.permute(0, 3, 1, 2), w[f"w{k}"].permute(0, 3, 1, 2), w[f"b{k}"], stride=stride, padding=1)
+        return h.permute(0, 2, 3, 1)
+    return F.linear(x.reshape(x.shape[0], -1), w[f"w{k}"], w[f"b{k}"])
+
+
 def mse(y, t, weight=None):
     """Mean over [B, 27] of weight_j (y - t)^2."""
     d = (y - t) ** 2

@@ -60,7 +60,7 @@ EXPORTED = ["celeste_problem_create", "celeste_problem_workspace_bytes", "celest
             "celeste_render_background_mode", "celeste_joint_pairs", "celeste_joint_cross_hessian",
             "celeste_joint_newton", "celeste_joint_value", "celeste_problem_check", "celeste_problem_set_wait_budget",
             "celeste_measure_peak", "celeste_joint_workspace_bytes", "celeste_joint_bind", "celeste_cnn_forward_ex",
-            "celeste_cnn_status"]
+            "celeste_cnn_status", "celeste_problem_refresh_pixels"]
 
 
 def load_library(path=None):
@@ -106,6 +106,7 @@ def load_library(path=None):
         "celeste_cnn_forward_ex": (ctypes.c_int, [dp, dp, dp, ctypes.c_int, dp, dp, dp, dp, ctypes.c_size_t,
                                                   ctypes.c_int, vp]),
         "celeste_cnn_status": (ctypes.c_int, []),
+        "celeste_problem_refresh_pixels": (ctypes.c_int, [vp, vp]),
         "celeste_joint_bind": (ctypes.c_int, [vp, vp, ctypes.c_size_t, vp]),
         "celeste_joint_newton": (ctypes.c_int, [vp, dp, ctypes.POINTER(NewtonOpts), ctypes.c_int32,
                                                 ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
@@ -303,6 +304,10 @@ class Problem:
         x = torch.empty(self.S, 32, 32, 5, dtype=torch.int16, device=self.device)
         _check(lib().celeste_extract_patches(self.handle, _ptr(x), _stream(stream)))
         return x
+
+    def refresh_pixels(self, stream=None):
+        """New counts in the same device images: re-gather the patch pixels (layout unchanged)."""
+        _check(lib().celeste_problem_refresh_pixels(self.handle, _stream(stream)))
 
     def rebind(self, stream=None):
         """Upload the layout again and re-gather the patch pixels from the device images."""

@@ -71,12 +71,21 @@ class WarmStartCNN:
                                                 _stream(None)))
         return y
 
-    def activations(self, batch):
-        """The first hidden layer's activations kept in the workspace by the last forward call at this
-        batch size: int16 [batch, 32, 32, 32] (BF16 bits)."""
+    def buffers(self, batch):
+        """The workspace's BF16 buffers (int16 bit patterns) at this batch size: a1..a5, the five hidden
+        layers' activations after ReLU kept by the last forward call, and d1..d5, the gradients w.r.t.
+        their pre-ReLU values left by the last backward call (the library's workspace layout: a_k then
+        d_k for k = 1..5, each 256-byte aligned)."""
         buf, ws, _ = self.workspace(batch)
         off = ws.value - buf.data_ptr()
-        return buf[off:off + batch * 32 * 32 * 32 * 2].view(torch.int16).view(batch, 32, 32, 32)
+        shapes = [(32, 32, 32), (16, 16, 64), (8, 8, 64), (4, 4, 64), (256,)]
+        out = {}
+        for k, shp in enumerate(shapes, 1):
+            n = batch * int(np.prod(shp))
+            for name in ("a", "d"):
+                out[f"{name}{k}"] = buf[off:off + 2 * n].view(torch.int16).view(batch, *shp)
+                off += (2 * n + 255) // 256 * 256
+        return out
 
     def backward(self, x, dy):
         assert x.dtype == torch.int16 and dy.dtype == torch.float32 and dy.is_contiguous()

@@ -430,6 +430,21 @@ extern "C" int celeste_problem_bind(celeste_problem* p, void* workspace, size_t 
   return CELESTE_OK;
 }
 
+extern "C" int celeste_problem_refresh_pixels(celeste_problem* p, celeste_stream_t stream) {
+  if (!p) return fail(CELESTE_ERR_INVALID_ARG, "null problem");
+  if (!p->bound) return fail(CELESTE_ERR_STATE, "problem is not bound to a workspace");
+  cudaStream_t st = (cudaStream_t)stream;
+  const ProblemDev& D = p->dev;
+  cudaError_t e = cudaMemsetAsync(D.err, 0, sizeof(int) * 4, st);
+  if (e != cudaSuccess) return cuda_fail(e, "clear err");
+  if (D.n_tiles > 0) {
+    gather_pixels_kernel<<<D.n_tiles, 256, 0, st>>>(D);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "gather_pixels_kernel");
+  }
+  p->background_ready = false;
+  return CELESTE_OK;
+}
+
 celeste_problem::~celeste_problem() {
   for (cudaEvent_t ev : prof_events) cudaEventDestroy(ev);
   for (cudaEvent_t ev : iter_events) cudaEventDestroy(ev);

@@ -141,11 +141,11 @@ def test_tcgen05_forward_matches_mma_sync_and_oracle(P, B):
     x = _bf16_bits(torch.randn(B, 32, 32, 5, device=dev, dtype=torch.float32,
                                generator=torch.Generator(device=dev).manual_seed(5)))
     y_ref = net.forward(x, engine=cnn.ENGINE_MMA_SYNC)
-    a1_ref = net.activations(B).clone()
+    a1_ref = net.buffers(B)["a1"].clone()
     y_tc = net.forward(x, engine=cnn.ENGINE_TCGEN05)
     torch.cuda.synchronize()
     assert pkg.lib().celeste_cnn_status() == 0
-    a1_tc = net.activations(B).clone()
+    a1_tc = net.buffers(B)["a1"].clone()
     a_ref = a1_ref.view(torch.bfloat16).float()
     a_tc = a1_tc.view(torch.bfloat16).float()
     assert float((a_tc - a_ref).abs().max()) <= 2 ** -6 * float(a_ref.abs().max())
@@ -162,3 +162,62 @@ def test_tcgen05_forward_matches_mma_sync_and_oracle(P, B):
     yr = C.forward(pw, _from_bits(x[idx.to(dev)]))
     s_or = float(yr.pow(2).mean().sqrt())
     assert float((y_tc[idx.to(dev)].double().cpu() - yr).abs().max()) <= 3e-2 * s_or
+
+
+def test_backward_layer_by_layer_matches_oracle(P):
+    """Each layer's weight and input gradient against the float64 oracle fed the GPU's own BF16
+    operands: the layer's input activation (the input patch for the first layer) and the gradient
+    w.r.t. its pre-ReLU output as the backward pass left them in the workspace.  What remains is the
+    FP32 summation order (weights: 1e-4 of the gradient's norm) and the BF16 rounding of each stored
+    input gradient (2^-8 of its scale), so each layer is checked at its own precision rather than
+    through the roundings of every layer above it."""
+    pkg, cnn = P
+    dev = torch.device("cuda:0")
+    net = cnn.WarmStartCNN(dev, seed=17)
+    net.params += 0.05 * torch.randn(net.n, device=dev, dtype=torch.float32,
+                                     generator=torch.Generator(device=dev).manual_seed(6))
+    net.params_bf16.copy_(_bf16_bits(net.params))
+    B = 96
+    x = _bf16_bits(torch.randn(B, 32, 32, 5, device=dev, dtype=torch.float32,
+                               generator=torch.Generator(device=dev).manual_seed(7)))
+    net.forward(x)
+    dy = torch.randn(B, 27, device=dev, dtype=torch.float32, generator=torch.Generator(device=dev).manual_seed(8))
+    net.grad.zero_()
+    net.backward(x, dy)
+    torch.cuda.synchronize()
+    buf = {k: _from_bits(v) for k, v in net.buffers(B).items()}
+    pw = _from_bits(net.params_bf16)
+    offs = np.cumsum([0] + [int(np.prod(s)) for _, s in C.SHAPES])
+    names = [n for n, _ in C.SHAPES]
+    for k, (name, _) in enumerate(C.SHAPES):
+        if name.startswith("b"):
+            pw[offs[k]:offs[k + 1]] = net.params[offs[k]:offs[k + 1]].double().cpu()
+    g = net.grad.double().cpu()
+    inputs = {1: _from_bits(x), 2: buf["a1"], 3: buf["a2"], 4: buf["a3"], 5: buf["a4"], 6: buf["a5"]}
+    out_grads = {k: buf[f"d{k}"] for k in range(1, 6)}
+    # the last layer's products take the FP32 output gradient rounded to BF16; its bias gradient sums
+    # it unrounded
+    out_grads[6] = _from_bits(_bf16_bits(dy))
+    report = {}
+    for k in range(1, 7):
+        p = pw.clone().requires_grad_(True)
+        xin = inputs[k].clone().requires_grad_(True)
+        z = C.layer_pre(p, k, xin)
+        (gp, gx) = torch.autograd.grad((z * out_grads[k].reshape(z.shape)).sum(), (p, xin))
+        if k == 6:
+            gp = gp.clone()
+            gp[offs[names.index("b6")]:offs[names.index("b6") + 1]] = dy.double().cpu().sum(0)
+        iw, ib = names.index(f"w{k}"), names.index(f"b{k}")
+        for idx in (iw, ib):
+            a, b = g[offs[idx]:offs[idx + 1]], gp[offs[idx]:offs[idx + 1]]
+            rel = float((a - b).norm() / b.norm())
+            report[names[idx]] = rel
+            assert rel <= 1e-4, (names[idx], rel)
+        if k >= 2:
+            # the gradient w.r.t. layer k-1's pre-ReLU value: this input gradient masked by the ReLU
+            ref = gx.reshape(out_grads[k - 1].shape) * (inputs[k].reshape(out_grads[k - 1].shape) > 0)
+            got = out_grads[k - 1]
+            err = float((got - ref).abs().max())
+            report[f"d{k - 1}"] = err / float(ref.abs().max())
+            assert err <= 2.0 ** -8 * float(ref.abs().max()), (k, err, float(ref.abs().max()))
+    print("CNN_LAYER_GRAD " + " ".join(f"{n}:{v:.2e}" for n, v in report.items()))

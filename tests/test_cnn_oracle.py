@@ -111,3 +111,19 @@ def test_patch_extraction_reads_the_image():
         bands = {sc.images[m].band for (m, _, _) in cen[s]}
         for b in set(range(5)) - bands:
             assert not x[:, :, b].any()
+
+
+def test_layer_pre_composes_to_forward():
+    """layer_pre, one layer at a time, composed with ReLU between layers, is the network's forward
+    (which the tests above pin against a direct loop over the convolution's definition and finite
+    differences), and each convolution layer's output has the stride's spatial size."""
+    rng = np.random.default_rng(12)
+    p = torch.as_tensor(rng.standard_normal(C.N_PARAMS) * 0.05)
+    x = torch.as_tensor(rng.standard_normal((3, 32, 32, 5)))
+    h = x
+    for k, side in zip(range(1, 5), (32, 16, 8, 4)):
+        h = torch.relu(C.layer_pre(p, k, h))
+        assert tuple(h.shape) == (3, side, side, 32 if k == 1 else 64)
+    h = torch.relu(C.layer_pre(p, 5, h))
+    y = C.layer_pre(p, 6, h)
+    np.testing.assert_allclose(y.numpy(), C.forward(p, x).numpy(), rtol=1e-12, atol=1e-12)

@@ -270,3 +270,30 @@ def test_newton_graph_matches_plain_launches(P):
         for x, y in zip(runs[a][1:], runs[b][1:]):
             np.testing.assert_array_equal(x, y)
     assert runs[3][3].max() <= 7
+
+
+def test_refresh_pixels_matches_a_fresh_bind(P):
+    """New counts written into the same device images: celeste_problem_refresh_pixels re-gathers the
+    patch pixels, and the evaluation equals that of a problem bound from scratch on the new images."""
+    sc = synth.tiny(seed=12, n_sources=4, n_images=3, H=34, W=38, radius=(6, 12))
+    dev = torch.device("cuda:0")
+    pix = [torch.as_tensor(np.ascontiguousarray(im.pixels, np.float32)).to(dev) for im in sc.images]
+    prob = P.Problem(sc, device=dev, tile_pixels=128, device_pixels=pix)
+    th = torch.as_tensor(sc.theta0, device=dev).contiguous()
+    prob.render_background(th)
+    before = [t.cpu().numpy() for t in prob.elbo_batch(th)]
+    rng = np.random.default_rng(3)
+    new = [np.asarray(rng.poisson(np.maximum(im.pixels, 0.0) + 5.0), np.float32) for im in sc.images]
+    for d, n in zip(pix, new):
+        d.copy_(torch.as_tensor(n))
+    prob.refresh_pixels()
+    prob.render_background(th)
+    after = [t.cpu().numpy() for t in prob.elbo_batch(th)]
+    for im, n in zip(sc.images, new):
+        im.pixels = n
+    fresh = P.Problem(sc, device=dev, tile_pixels=128)
+    fresh.render_background(th)
+    ref = [t.cpu().numpy() for t in fresh.elbo_batch(th)]
+    for a, r in zip(after, ref):
+        np.testing.assert_array_equal(a, r)
+    assert not np.array_equal(after[0], before[0])
