@@ -316,6 +316,14 @@ int celeste_covariance_batch(celeste_problem* p, const double* theta, double* co
 int celeste_tr_solve_batch(const double* B, const double* g, const double* delta, int n, double* p,
                            double* pred, int32_t* hard, celeste_stream_t stream);
 
+/* The float64 reciprocal the subproblem solver divides with (its recurrences divide once per row),
+ * applied elementwise, so that its error bound can be tested: r[i] ~ 1 / x[i] from the PTX
+ * approximate reciprocal refined by two Newton-Raphson steps (no counterpart in the paper; an
+ * implementation detail of the float64 solve).  x, r: device float64 [n] (r may alias x).  For
+ * normal x, |r - 1/x| is within 2 units in the last place of 1/x; x = 0 or |x| < 2^-1022 gives NaN,
+ * |x| > 2^1022 gives 0.  Returns CELESTE_ERR_INVALID_ARG for n < 0 or a null pointer with n > 0. */
+int celeste_tr_reciprocal(const double* x, double* r, int n, celeste_stream_t stream);
+
 /* Device-time accounting of the library's own kernels, for benchmarks.
  *   celeste_profile_start: reset and start recording.  While recording, every launch of the
  *     ELBO+gradient+Hessian pixel kernel, of the value-only pixel kernel and of the trust-region

@@ -54,7 +54,7 @@ class ProfileStats(ctypes.Structure):
 EXPORTED = ["celeste_problem_create", "celeste_problem_workspace_bytes", "celeste_problem_counts",
             "celeste_problem_bind", "celeste_render_background", "celeste_elbo_batch", "celeste_newton_batch",
             "celeste_problem_destroy", "celeste_strerror", "celeste_last_error_detail", "celeste_profile_start",
-            "celeste_profile_stop", "celeste_tr_solve_batch", "celeste_elbo_batch_noalloc", "celeste_cnn_param_count",
+            "celeste_profile_stop", "celeste_tr_solve_batch", "celeste_tr_reciprocal", "celeste_elbo_batch_noalloc", "celeste_cnn_param_count",
             "celeste_cnn_workspace_bytes", "celeste_cnn_init", "celeste_cnn_forward", "celeste_cnn_backward",
             "celeste_cnn_mse", "celeste_cnn_adamw", "celeste_extract_patches", "celeste_covariance_batch",
             "celeste_render_background_mode", "celeste_joint_pairs", "celeste_joint_cross_hessian",
@@ -83,6 +83,7 @@ def load_library(path=None):
         "celeste_profile_start": (ctypes.c_int, [vp]),
         "celeste_profile_stop": (ctypes.c_int, [vp, ctypes.POINTER(ProfileStats)]),
         "celeste_tr_solve_batch": (ctypes.c_int, [dp, dp, dp, ctypes.c_int, dp, dp, dp, vp]),
+        "celeste_tr_reciprocal": (ctypes.c_int, [dp, dp, ctypes.c_int, vp]),
         "celeste_elbo_batch_noalloc": (ctypes.c_int, [vp, dp, dp, dp, dp, vp]),
         "celeste_cnn_param_count": (ctypes.c_int64, []),
         "celeste_cnn_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int]),
@@ -345,6 +346,14 @@ def tr_solve_batch(B, g, delta, stream=None):
     _check(lib().celeste_tr_solve_batch(_ptr(B), _ptr(g), _ptr(delta), ctypes.c_int(n), _ptr(p), _ptr(pred), _ptr(hard),
                                         _stream(stream)))
     return p, pred, hard
+
+
+def tr_reciprocal(x, stream=None):
+    """The subproblem solver's float64 reciprocal applied to a float64 CUDA tensor (for its error test)."""
+    assert x.dtype == torch.float64 and x.is_contiguous() and x.is_cuda
+    r = torch.empty_like(x)
+    _check(lib().celeste_tr_reciprocal(_ptr(x), _ptr(r), ctypes.c_int(x.numel()), _stream(stream)))
+    return r
 
 
 def measure_peak(kind, stream=None):

@@ -34,6 +34,7 @@ struct NewtonDev {
   double* pred;         // [S] predicted reduction of f = -ELBO
   double* Ltrial;       // [S] ELBO change from theta to the trial point
   double* tcache;       // [S][TR_CACHE] tridiagonal form of the last Householder-reduced B
+  double* lam;          // [S] multiplier of the last subproblem (negative: none)
   int* state;           // [S][ST_STRIDE]
   int* count;           // [0]: active sources after the update
   int S;
@@ -61,6 +62,7 @@ __global__ void newton_init_kernel(NewtonDev N, int* flags) {
   N.state[ST_STRIDE * s + ST_SAME] = 0;
   N.state[ST_STRIDE * s + ST_CACHED] = 0;
   if (!(N.delta[s] > 0.0)) N.delta[s] = N.delta0;
+  N.lam[s] = -1.0;
   flags[s] = FLAG_FULL;
 }
 
@@ -112,9 +114,13 @@ __global__ void __launch_bounds__(32 * TR_WARPS) tr_step_kernel(NewtonDev N, int
   const bool use_cache = same && st[ST_CACHED];
   const bool try_newton = !same && st[ST_ITERS] > 0 && !st[ST_BOUNDARY];
   double* cache = N.tcache + (size_t)s * TR_CACHE;
-  const bool reduced = tr_solve_warp(S, HL, -1.0, gk, delta, try_newton, use_cache ? cache : nullptr, cache, pk,
-                                     pred, hard);
-  if (lane == 0) st[ST_CACHED] = use_cache || reduced;
+  double lam;
+  const bool reduced = tr_solve_warp(S, HL, -1.0, gk, delta, try_newton, use_cache ? cache : nullptr, cache,
+                                     N.lam[s], lam, pk, pred, hard);
+  if (lane == 0) {
+    st[ST_CACHED] = use_cache || reduced;
+    N.lam[s] = lam;
+  }
   const double pnorm = sqrt(warp_sum(lane < NP ? pk * pk : 0.0));
   if (lane < NP) N.trial[(size_t)s * NP + lane] = N.theta[(size_t)s * NP + lane] + pk;
   if (lane == 0) {
@@ -143,14 +149,20 @@ __global__ void __launch_bounds__(32 * TR_WARPS) tr_solve_batch_kernel(const dou
   if (q >= n) return;
   TrSmem& S = sm[warp];
   const double gk = lane < NP ? g[(size_t)q * NP + lane] : 0.0;
-  double pk, pr;
+  double pk, pr, lam;
   int hc;
-  tr_solve_warp(S, B + (size_t)q * NP * NP, 1.0, gk, delta[q], true, nullptr, nullptr, pk, pr, hc);
+  tr_solve_warp(S, B + (size_t)q * NP * NP, 1.0, gk, delta[q], true, nullptr, nullptr, -1.0, lam, pk, pr, hc);
   if (lane < NP) p[(size_t)q * NP + lane] = pk;
   if (lane == 0) {
     if (pred) pred[q] = pr;
     if (hard) hard[q] = hc;
   }
+}
+
+// The solver's float64 reciprocal applied elementwise (for its error-bound test).
+__global__ void tr_reciprocal_kernel(const double* __restrict__ x, double* __restrict__ r, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) r[i] = tr_rcp(x[i]);
 }
 
 // Accept or reject the trial point and update the radius (Nocedal & Wright Alg. 4.1).
@@ -281,6 +293,7 @@ extern "C" int celeste_newton_batch(celeste_problem* p, double* theta, const cel
   N.state = reinterpret_cast<int*>(p->base + L.nt_state);
   N.tcache = reinterpret_cast<double*>(p->base + L.nt_tcache);
   N.count = reinterpret_cast<int*>(p->base + L.nt_count);
+  N.lam = reinterpret_cast<double*>(p->base + L.nt_lam);
   N.S = p->S;
   N.ftol = o.ftol > 0 ? o.ftol : 1e-8;
   N.gtol = o.gtol > 0 ? o.gtol : 1e-10;
@@ -414,5 +427,14 @@ extern "C" int celeste_tr_solve_batch(const double* B, const double* g, const do
                                                                                                  pred, hard);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "tr_solve_batch_kernel");
+  return CELESTE_OK;
+}
+
+extern "C" int celeste_tr_reciprocal(const double* x, double* r, int n, celeste_stream_t stream) {
+  if (n < 0 || (n > 0 && (!x || !r))) return fail(CELESTE_ERR_INVALID_ARG, "null argument");
+  if (n == 0) return CELESTE_OK;
+  tr_reciprocal_kernel<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(x, r, n);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "tr_reciprocal_kernel");
   return CELESTE_OK;
 }

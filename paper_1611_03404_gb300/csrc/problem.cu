@@ -326,6 +326,7 @@ void build_layout(celeste_problem* p) {
   L.nt_state = take(sizeof(int) * 8 * S);
   L.nt_tcache = take(sizeof(double) * TR_CACHE * S);
   L.nt_count = take(sizeof(int) * 4);
+  L.nt_lam = take(sizeof(double) * S);
   L.total = o;
 }
 

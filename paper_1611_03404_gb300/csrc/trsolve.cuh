@@ -53,6 +53,22 @@ struct TrSmem {
   double PL[TR_N][32], PR[TR_N][32], PY[TR_N][32];
 };
 
+// 1/a in float64 with few float64-pipe instructions (a float64 division issues a dozen, and the
+// solver's recurrences divide once per row): the approximate reciprocal of the PTX ISA
+// (rcp.approx.ftz.f64, special-function unit) refined by two Newton-Raphson steps for f(r) = 1/r - a,
+// r <- r + r (1 - a r) (Ypma, "Historical development of the Newton-Raphson method", SIAM Review
+// 1995), each squaring the relative error: a seed good to 2^-14 ends within an ulp or two of 1/a.
+// Normal a only: |a| < 2^-1022 or a = 0 gives NaN (the solver masks those rows as not positive
+// definite), |a| > 2^1022 gives 0.
+__device__ __forceinline__ double tr_rcp(double a) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(a));
+  double e = fma(-a, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-a, r, 1.0);
+  return fma(r, e, r);
+}
+
 __device__ inline double tr_warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -63,13 +79,13 @@ __device__ inline double tr_warp_sum(double v) {
 __device__ inline bool tr_ldl(TrSmem& S, double lambda) {
   double Dp = S.d[0] + lambda;
   bool pd = Dp > 0.0;
-  double r = 1.0 / Dp;
+  double r = tr_rcp(Dp);
   S.D[0] = r;
   for (int i = 1; i < TR_N; ++i) {
     S.L[i] = S.off[i] * r;                 // off the pivot chain
     Dp = fma(-S.o2[i], r, S.d[i] + lambda);
     pd = pd && Dp > 0.0;
-    r = 1.0 / Dp;
+    r = tr_rcp(Dp);
     S.D[i] = r;
   }
   return pd;
@@ -118,7 +134,7 @@ __device__ inline int tr_sturm_f(const TrSmem& S, float x) {
 __device__ inline bool tr_eval_lane(TrSmem& S, int lane, double lam, double& pn, double& qn2) {
   double Dp = S.d[0] + lam;
   bool pd = Dp > 0.0;
-  double r = 1.0 / Dp;
+  double r = tr_rcp(Dp);
   double w = -S.gh[0];
   S.PR[0][lane] = r;
   S.PY[0][lane] = w;
@@ -126,7 +142,7 @@ __device__ inline bool tr_eval_lane(TrSmem& S, int lane, double lam, double& pn,
     const double l = S.off[i] * r;
     Dp = fma(-S.o2[i], r, S.d[i] + lam);
     pd = pd && Dp > 0.0;
-    r = 1.0 / Dp;
+    r = tr_rcp(Dp);
     w = fma(-l, w, -S.gh[i]);
     S.PL[i][lane] = l;
     S.PR[i][lane] = r;
@@ -175,28 +191,54 @@ __device__ inline void tr_take_y(TrSmem& S, int lane, int src) {
 // largest evaluated multiplier on the left (phi < 0; phi is concave and increasing, so Newton
 // from the left stays left).  Non-positive-definite points lie left of -lambda_min <= lambda*.
 // spec bounds |eigenvalues of T| (Gershgorin): the bracket counts as closed once it is narrower
-// than 4 ulps of max(|lambda|, spec).  On return S.y holds the step in the T basis; returns 1 for
-// the hard case (the bracket closes on the pole with phi > 0 to its right), in which S.y is not set.
+// than 4 ulps of max(|lambda|, spec).  hint (> 0, or negative for none): the multiplier of this
+// source's previous subproblem; the root moves little from one Newton iteration to the next, so
+// the first pass puts its points on a geometric grid around the hint (factors 2^-7.75 .. 2^7.75)
+// instead of across the whole bracket.  On return S.y holds the step in the T basis and lam_out
+// its multiplier; returns 1 for the hard case (the bracket closes on the pole with phi > 0 to its
+// right), in which S.y is not set.
 __device__ inline int tr_lambda_parallel(TrSmem& S, int lane, double lo, double hi, double delta, bool try_zero,
-                                         double spec) {
+                                         double spec, double hint, double& lam_out) {
   constexpr double TOL = 1e-10;
   double L = lo, H = hi;            // L <= lambda* <= H
   bool have_h = false;              // S.y holds the point H (phi(H) >= 0)
   double lamN = -1.0;               // Newton point from the best left evaluation (< 0: none)
+  double lamS = -1.0;               // secant point through the best left point and H (< 0: none)
+  double lamL = -INFINITY, phiL = 0.0, dphiL = 1.0;   // largest left multiplier with phi < 0: phi, phi'
+  double phiH = 0.0;                // phi at H, once evaluated
   // Lane offsets.  Without a Newton point: lanes 1-15 geometric from L (2^-45 .. 2^-3 of the
   // bracket, for a root or pole just above L), lanes 16-31 uniform (1/17 .. 16/17, so the bracket
-  // shrinks at least 17-fold).  With one: lane 0 at it, lanes 1-15 above and 16-31 below at
-  // 2^-3 .. 2^-48 of the distance to the bracket's ends.
+  // shrinks at least 17-fold).  With one but no secant point: lane 0 at it, lanes 1-15 above and
+  // 16-31 below at 2^-3 .. 2^-48 of the distance to the bracket's ends.  With both: phi concave,
+  // so the Newton point from the left lies below the root and the secant point through a left
+  // point and a right one above it; lanes 0 and 1 at the two, lanes 2-23 evenly between them
+  // (the bracket shrinks at least 23-fold), lanes 24-27 above the secant point and 28-31 below
+  // the Newton point at 2^-4 .. 2^-16 of the distance to the bracket's ends (in case rounding
+  // has moved either across the root).
   const double gfac = lane < 16 ? ldexp(1.0, -3 * (16 - lane)) : (double)(lane - 15) / 17.0;
   const double nfac = ldexp(1.0, -3 * ((lane & 15) + 1));
+  const double ufac = (double)(lane - 1) / 23.0;
+  const double afac = ldexp(1.0, -4 * ((lane & 3) + 1));
+  const double hfac = exp2(0.5 * (double)(lane - 16) + 0.25);   // 2^-7.75 .. 2^7.75 around the hint
+  double lamH = H;                  // multiplier of the point H
   for (int pass = 0; pass < 16; ++pass) {
     // ---- this lane's multiplier
     double lam;
     const double span = H - L;
-    if (pass > 0 && lamN > L && lamN < H)
+    if (pass > 0 && lamN > L && lamN < H && lamS > lamN && lamS <= H)
+      lam = lane == 0   ? lamN
+            : lane == 1 ? lamS
+            : lane < 24 ? lamN + (lamS - lamN) * ufac
+            : lane < 28 ? lamS + (H - lamS) * afac
+                        : lamN - (lamN - L) * afac;
+    else if (pass > 0 && lamN > L && lamN < H)
       lam = lane == 0 ? lamN : (lane < 16 ? lamN + (H - lamN) * nfac : lamN - (lamN - L) * nfac);
     else
       lam = lane == 0 ? ((pass == 0 && try_zero) ? 0.0 : L + 0.5 * span) : L + span * gfac;
+    if (pass == 0 && hint > L && hint < H && lane > 0) {
+      const double lh = hint * hfac;
+      if (lh > L && lh < H) lam = lh;   // else the lane keeps its bracket point
+    }
     __syncwarp();   // (lane choices are selects; the evaluation below must issue once, converged)
     double pn = 0.0, qn2 = 0.0;
     const bool pd = tr_eval_lane(S, lane, lam, pn, qn2);
@@ -205,6 +247,7 @@ __device__ inline int tr_lambda_parallel(TrSmem& S, int lane, double lo, double 
       const bool interior = __shfl_sync(0xffffffffu, (int)(pd && pn <= delta), 0) != 0;
       if (interior) {
         tr_take_y(S, lane, 0);
+        lam_out = 0.0;
         return 0;
       }
     }
@@ -214,6 +257,7 @@ __device__ inline int tr_lambda_parallel(TrSmem& S, int lane, double lo, double 
     if (best <= TOL * delta) {
       const unsigned m = __ballot_sync(0xffffffffu, err == best);
       tr_take_y(S, lane, __ffs(m) - 1);
+      lam_out = __shfl_sync(0xffffffffu, lam, __ffs(m) - 1);
       return 0;
     }
     // ---- new bracket
@@ -224,20 +268,25 @@ __device__ inline int tr_lambda_parallel(TrSmem& S, int lane, double lo, double 
       const unsigned m = __ballot_sync(0xffffffffu, right && lam == newH);
       tr_take_y(S, lane, __ffs(m) - 1);
       H = newH;
+      lamH = newH;
+      phiH = tr_rcp(__shfl_sync(0xffffffffu, pn, __ffs(m) - 1)) - tr_rcp(delta);
       have_h = true;
     }
     L = fmax(L, newL);
-    // ---- Newton point from the largest left evaluation with phi < 0
+    // ---- Newton point from the largest left evaluation with phi < 0 (phi' = q^2 / |p|^3)
     const bool lft = pd && pn > delta;
     const double lbest = tr_warp_max(lft ? lam : -INFINITY);
-    lamN = -1.0;
-    if (lbest > -INFINITY) {
+    if (lbest > lamL) {
       const unsigned m = __ballot_sync(0xffffffffu, lft && lam == lbest);
       const int src = __ffs(m) - 1;
       const double pnb = __shfl_sync(0xffffffffu, pn, src), qb = __shfl_sync(0xffffffffu, qn2, src);
-      const double phi = 1.0 / pnb - 1.0 / delta;
-      lamN = lbest - phi / (qb / (pnb * pnb * pnb));
+      lamL = lbest;
+      phiL = tr_rcp(pnb) - tr_rcp(delta);
+      dphiL = qb * tr_rcp(pnb * pnb * pnb);
     }
+    lamN = lamL > -INFINITY ? lamL - phiL * tr_rcp(dphiL) : -1.0;
+    // ---- secant point through (lamL, phiL < 0) and (H, phiH >= 0)
+    lamS = have_h && lamL > -INFINITY && phiH > phiL ? lamL + (H - lamL) * (-phiL * tr_rcp(phiH - phiL)) : -1.0;
     // ---- bracket closed: no multiplier left between L and H that T + lambda I could tell apart
     //      (its entries carry rounding of a few ulps of the spectrum's scale `spec`, so a bracket
     //      that narrow around a root next to the pole is resolved as far as float64 allows)
@@ -246,9 +295,11 @@ __device__ inline int tr_lambda_parallel(TrSmem& S, int lane, double lo, double 
       // phi(H) >= 0 with H next to L: the root, unless |y| jumps across delta within the last
       // ulps of lambda -- the pole, where g's component along the eigenvector of lambda_min is
       // too small to resolve (the hard case, numerically)
+      lam_out = lamH;
       return tr_norm(S.y) < delta * (1.0 - 1e-6) ? 1 : 0;
     }
   }
+  lam_out = lamH;
   return have_h ? 0 : 1;
 }
 
@@ -268,7 +319,7 @@ __device__ inline bool tr_newton_step(TrSmem& S, double gi, double& p_i) {
   for (int k = 0; k < TR_N; ++k) {
     const double dk = S.A[k * TR_LD + k];
     if (!(dk > 0.0)) return false;   // same value in every lane
-    const double r = 1.0 / dk;
+    const double r = tr_rcp(dk);
     const bool act = row && lane > k;
     const double li = act ? ar[k] * r : 0.0;
     __syncwarp();
@@ -298,11 +349,13 @@ __device__ inline bool tr_newton_step(TrSmem& S, double gi, double& p_i) {
 // lane i (0 for lanes >= 27).  On return lane i < 27 holds p_i; pred = -(g.p + p.B.p/2); hard =
 // hard case taken.  try_newton: attempt the Newton step first.  cache_in (or null): the
 // tridiagonal form of this same B and g, stored by an earlier call, replaces the reduction;
-// cache_out (or null): where to store the reduction when one is made.  Returns true when the
-// reduction was made and stored.
+// cache_out (or null): where to store the reduction when one is made.  lam_hint: the multiplier
+// of this source's previous subproblem (negative: none); lam_out: this one's (0 for an interior
+// step, negative after the hard case).  Returns true when the reduction was made and stored.
 __device__ inline bool tr_solve_warp(TrSmem& S, const double* __restrict__ Bsrc, double bsign, double gi,
                                      double delta, bool try_newton, const double* __restrict__ cache_in,
-                                     double* __restrict__ cache_out, double& p_i, double& pred, int& hard) {
+                                     double* __restrict__ cache_out, double lam_hint, double& lam_out,
+                                     double& p_i, double& pred, int& hard) {
   const int lane = threadIdx.x & 31;
   const int n = TR_N;
   const bool row = lane < n;
@@ -329,6 +382,7 @@ __device__ inline bool tr_solve_warp(TrSmem& S, const double* __restrict__ Bsrc,
         p_i = pn;
         pred = -0.5 * tr_warp_sum(gi * pn);   // -(g.p + p.B.p/2) with B p = -g
         hard = 0;
+        lam_out = 0.0;
         return false;
       }
     }
@@ -351,7 +405,7 @@ __device__ inline bool tr_solve_warp(TrSmem& S, const double* __restrict__ Bsrc,
     }
     const double alpha = -copysign(sqrt(s2), x0);
     const double vi = lane == k + 1 ? x0 - alpha : xi;
-    const double beta = 1.0 / (s2 - alpha * x0);   // 2 / v.v with v.v = 2 (s2 - alpha x0)
+    const double beta = tr_rcp(s2 - alpha * x0);   // 2 / v.v with v.v = 2 (s2 - alpha x0)
     S.v[lane] = vi;
     __syncwarp();
     double u[4] = {0.0, 0.0, 0.0, 0.0};
@@ -429,7 +483,9 @@ __device__ inline bool tr_solve_warp(TrSmem& S, const double* __restrict__ Bsrc,
   const double hi = fmax(lo, gnorm / delta - a) * (1.0 + 1e-12) + 1e-300;
   if (lane == 0) S.flag[2] = 0;
   __syncwarp();
-  if (tr_lambda_parallel(S, lane, lo, hi, delta, lo == 0.0, spec)) {
+  lam_out = -1.0;
+  if (tr_lambda_parallel(S, lane, lo, hi, delta, lo == 0.0, spec, lam_hint, lam_out)) {
+    lam_out = -1.0;
     // hard case: g has (almost) no component along the eigenvector z of lambda_min.  lambda_min
     // from a float32 Sturm bracket refined by inverse iteration (lane 0), then
     // p = y(-lambda_min) + tau z with |p| = delta.
@@ -449,7 +505,7 @@ __device__ inline bool tr_solve_warp(TrSmem& S, const double* __restrict__ Bsrc,
       for (int i = 0; i < n; ++i) S.z[i] = 1.0;
       for (int r = 0; r < 4; ++r) {
         tr_ldl_solve(S, S.z, S.z);
-        const double rz = 1.0 / tr_norm(S.z);
+        const double rz = tr_rcp(tr_norm(S.z));
         for (int i = 0; i < n; ++i) S.z[i] *= rz;
       }
       double lmin = 0.0, zg = 0.0;

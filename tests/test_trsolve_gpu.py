@@ -104,3 +104,28 @@ def test_subproblem_hard_case(P):
     np.testing.assert_allclose((B + 2.0 * np.eye(27)) @ p, -g, atol=1e-7)
     pr, _, hr = O.tr_subproblem(g, B, delta)
     assert hr and abs(pr @ B @ pr / 2 + g @ pr - (p @ B @ p / 2 + g @ p)) <= 1e-9 * (1 + abs(g @ pr))
+
+
+def test_reciprocal_error_bound(P):
+    """The solver's reciprocal (approximate seed + two Newton-Raphson steps) against the correctly
+    rounded float64 quotient: within 2 ulps over the normal range, both signs, including powers of
+    two, their neighbours and the ends of the documented range."""
+    rng = np.random.default_rng(7)
+    x = np.concatenate([
+        np.exp(rng.uniform(-700, 700, 200000)) * rng.choice([-1.0, 1.0], 200000),
+        1.0 + rng.uniform(0, 1, 100000),
+        np.ldexp(1.0, np.arange(-1021, 1022)),
+        np.nextafter(np.ldexp(1.0, np.arange(-1021, 1022)), 0.0),
+        np.nextafter(np.ldexp(1.0, np.arange(-1021, 1022)), np.inf),
+        [1.0, -1.0, 3.0, 1.0 / 3.0, 0.1, 1e-300, 1e300, 2.0 ** -1022, 2.0 ** 1021],
+    ])
+    r = P.tr_reciprocal(torch.as_tensor(x, device="cuda")).cpu().numpy()
+    exact = 1.0 / x
+    ulp = np.spacing(np.abs(exact))
+    err = np.abs(r - exact) / ulp
+    assert np.all(np.isfinite(r)), x[~np.isfinite(r)][:5]
+    assert err.max() <= 2.0, (err.max(), x[np.argmax(err)])
+    # the documented ends: zero and subnormal inputs give NaN, |x| > 2^1022 gives 0
+    edge = P.tr_reciprocal(torch.tensor([0.0, 5e-324, 2.0 ** 1023, -(2.0 ** 1023)], dtype=torch.float64,
+                                        device="cuda")).cpu().numpy()
+    assert np.isnan(edge[0]) and np.isnan(edge[1]) and edge[2] == 0.0 and edge[3] == 0.0
