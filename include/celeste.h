@@ -140,6 +140,10 @@ typedef struct {
                           host checks of the active count; 1: plain launches, one check per
                           iteration.  Iterations after the last source stops launch kernels
                           that find empty worklists and change nothing. */
+  int32_t cta_sources; /* 0: twice the SM count.  An iteration that starts with at most this many
+                          active sources solves each subproblem on four warps (one CTA, the SM's
+                          four float64 pipes) instead of one; negative: always one warp.  Both
+                          solve the same subproblem; their roundings differ. */
 } celeste_newton_opts;
 
 /* Validate the description and build the host-side layout (patches, neighbours, work
@@ -315,6 +319,20 @@ int celeste_covariance_batch(celeste_problem* p, const double* theta, double* co
  *   Sturm multisection for the smallest eigenvalue, safeguarded Newton on 1/|p| - 1/delta). */
 int celeste_tr_solve_batch(const double* B, const double* g, const double* delta, int n, double* p,
                            double* pred, int32_t* hard, celeste_stream_t stream);
+
+/* celeste_tr_solve_batch with the solver's two layouts and its multiplier hint exposed, for tests:
+ *   warps:    1 (one warp per problem, the layout of iterations with many active sources) or 4 (one
+ *             CTA of four warps per problem, the layout celeste_newton_batch uses when few are left);
+ *   lam_hint: device float64 [n] or NULL; a multiplier near the solution's (negative: none), used
+ *             to place the first pass of the multiplier search (the Newton iteration passes each
+ *             source's previous multiplier); the solution does not depend on it beyond rounding;
+ *   lam:      device float64 [n] out or NULL: the multiplier found (0 for an interior step,
+ *             negative after the hard case).
+ * The other arguments are celeste_tr_solve_batch's.  Errors: CELESTE_ERR_INVALID_ARG for warps
+ * other than 1 or 4, n < 0, or a required pointer NULL with n > 0. */
+int celeste_tr_solve_batch_ex(const double* B, const double* g, const double* delta, int n, int warps,
+                              const double* lam_hint, double* p, double* pred, int32_t* hard, double* lam,
+                              celeste_stream_t stream);
 
 /* The float64 reciprocal the subproblem solver divides with (its recurrences divide once per row),
  * applied elementwise, so that its error bound can be tested: r[i] ~ 1 / x[i] from the PTX

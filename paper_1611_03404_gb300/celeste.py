@@ -41,7 +41,7 @@ class ProblemDesc(ctypes.Structure):
 class NewtonOpts(ctypes.Structure):
     _fields_ = [("max_iter", ctypes.c_int32), ("ftol", ctypes.c_double), ("gtol", ctypes.c_double),
                 ("delta0", ctypes.c_double), ("delta_max", ctypes.c_double), ("eta", ctypes.c_double),
-                ("delta_min", ctypes.c_double), ("graph_iters", ctypes.c_int32)]
+                ("delta_min", ctypes.c_double), ("graph_iters", ctypes.c_int32), ("cta_sources", ctypes.c_int32)]
 
 
 class ProfileStats(ctypes.Structure):
@@ -54,7 +54,7 @@ class ProfileStats(ctypes.Structure):
 EXPORTED = ["celeste_problem_create", "celeste_problem_workspace_bytes", "celeste_problem_counts",
             "celeste_problem_bind", "celeste_render_background", "celeste_elbo_batch", "celeste_newton_batch",
             "celeste_problem_destroy", "celeste_strerror", "celeste_last_error_detail", "celeste_profile_start",
-            "celeste_profile_stop", "celeste_tr_solve_batch", "celeste_tr_reciprocal", "celeste_elbo_batch_noalloc", "celeste_cnn_param_count",
+            "celeste_profile_stop", "celeste_tr_solve_batch", "celeste_tr_solve_batch_ex", "celeste_tr_reciprocal", "celeste_elbo_batch_noalloc", "celeste_cnn_param_count",
             "celeste_cnn_workspace_bytes", "celeste_cnn_init", "celeste_cnn_forward", "celeste_cnn_backward",
             "celeste_cnn_mse", "celeste_cnn_adamw", "celeste_extract_patches", "celeste_covariance_batch",
             "celeste_render_background_mode", "celeste_joint_pairs", "celeste_joint_cross_hessian",
@@ -84,6 +84,7 @@ def load_library(path=None):
         "celeste_profile_stop": (ctypes.c_int, [vp, ctypes.POINTER(ProfileStats)]),
         "celeste_tr_solve_batch": (ctypes.c_int, [dp, dp, dp, ctypes.c_int, dp, dp, dp, vp]),
         "celeste_tr_reciprocal": (ctypes.c_int, [dp, dp, ctypes.c_int, vp]),
+        "celeste_tr_solve_batch_ex": (ctypes.c_int, [dp, dp, dp, ctypes.c_int, ctypes.c_int, dp, dp, dp, dp, dp, vp]),
         "celeste_elbo_batch_noalloc": (ctypes.c_int, [vp, dp, dp, dp, dp, vp]),
         "celeste_cnn_param_count": (ctypes.c_int64, []),
         "celeste_cnn_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int]),
@@ -278,8 +279,10 @@ class Problem:
         _check(lib().celeste_problem_set_wait_budget(self.handle, ctypes.c_longlong(int(cycles))))
 
     def newton_batch(self, theta, delta=None, max_iter=50, ftol=1e-8, gtol=1e-10, delta0=1.0, delta_max=1e4,
-                     eta=0.1, delta_min=1e-12, graph_iters=4, stream=None):
-        """Runs trust-region Newton in place on `theta`; returns (delta, iters, status, elbo)."""
+                     eta=0.1, delta_min=1e-12, graph_iters=4, cta_sources=0, stream=None):
+        """Runs trust-region Newton in place on `theta`; returns (delta, iters, status, elbo).  cta_sources:
+        iterations starting with at most this many active sources solve each subproblem on four warps
+        (0: twice the SM count; negative: never)."""
         assert theta.dtype == torch.float64 and theta.is_contiguous() and theta.shape == (self.S, NPARAM)
         dev = theta.device
         if delta is None:
@@ -287,7 +290,7 @@ class Problem:
         iters = torch.zeros(self.S, dtype=torch.int32, device=dev)
         status = torch.zeros(self.S, dtype=torch.int32, device=dev)
         elbo = torch.empty(self.S, dtype=torch.float64, device=dev)
-        opts = NewtonOpts(max_iter, ftol, gtol, delta0, delta_max, eta, delta_min, graph_iters)
+        opts = NewtonOpts(max_iter, ftol, gtol, delta0, delta_max, eta, delta_min, graph_iters, cta_sources)
         _check(lib().celeste_newton_batch(self.handle, _ptr(theta), ctypes.byref(opts), _ptr(delta), _ptr(iters),
                                           _ptr(status), _ptr(elbo), _stream(stream)))
         return delta, iters, status, elbo
@@ -334,18 +337,26 @@ class Problem:
             pass
 
 
-def tr_solve_batch(B, g, delta, stream=None):
-    """Trust-region subproblems on the device: B [n,27,27], g [n,27], delta [n] float64 CUDA tensors.
-    Returns (p [n,27], pred [n], hard [n] int32)."""
+def tr_solve_batch(B, g, delta, warps=1, lam_hint=None, return_lambda=False, stream=None):
+    """Trust-region subproblems on the device: B [n,27,27], g [n,27], delta [n] float64 CUDA tensors, solved
+    on one warp or one four-warp CTA per problem (warps 1 or 4), the multiplier search optionally placed
+    around lam_hint [n].  Returns (p [n,27], pred [n], hard [n] int32) and, with return_lambda, the
+    multipliers [n]."""
     n = g.shape[0]
-    for t in (B, g, delta):
+    for t in (B, g, delta) + ((lam_hint,) if lam_hint is not None else ()):
         assert t.dtype == torch.float64 and t.is_contiguous() and t.is_cuda
     p = torch.empty(n, NPARAM, dtype=torch.float64, device=g.device)
     pred = torch.empty(n, dtype=torch.float64, device=g.device)
     hard = torch.empty(n, dtype=torch.int32, device=g.device)
-    _check(lib().celeste_tr_solve_batch(_ptr(B), _ptr(g), _ptr(delta), ctypes.c_int(n), _ptr(p), _ptr(pred), _ptr(hard),
-                                        _stream(stream)))
-    return p, pred, hard
+    lam = torch.empty(n, dtype=torch.float64, device=g.device)
+    if warps == 1 and lam_hint is None and not return_lambda:
+        _check(lib().celeste_tr_solve_batch(_ptr(B), _ptr(g), _ptr(delta), ctypes.c_int(n), _ptr(p), _ptr(pred),
+                                            _ptr(hard), _stream(stream)))
+    else:
+        _check(lib().celeste_tr_solve_batch_ex(_ptr(B), _ptr(g), _ptr(delta), ctypes.c_int(n), ctypes.c_int(warps),
+                                               _ptr(lam_hint) if lam_hint is not None else None, _ptr(p), _ptr(pred),
+                                               _ptr(hard), _ptr(lam), _stream(stream)))
+    return (p, pred, hard, lam) if return_lambda else (p, pred, hard)
 
 
 def tr_reciprocal(x, stream=None):

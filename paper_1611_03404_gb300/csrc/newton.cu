@@ -14,6 +14,7 @@
 #include "kernels.h"
 #include "problem.h"
 #include "trsolve.cuh"
+#include "trsolve_cta.cuh"
 
 namespace celeste {
 
@@ -37,6 +38,8 @@ struct NewtonDev {
   double* lam;          // [S] multiplier of the last subproblem (negative: none)
   int* state;           // [S][ST_STRIDE]
   int* count;           // [0]: active sources after the update
+  int* list;            // [S]: the active sources after the update (count[0] of them, any order)
+  int cta_max;          // at most this many active sources: four warps per subproblem
   int S;
   double ftol, gtol, delta0, delta_max, eta, delta_min;
 };
@@ -63,6 +66,8 @@ __global__ void newton_init_kernel(NewtonDev N, int* flags) {
   N.state[ST_STRIDE * s + ST_CACHED] = 0;
   if (!(N.delta[s] > 0.0)) N.delta[s] = N.delta0;
   N.lam[s] = -1.0;
+  N.list[s] = s;                  // every source active, listed in order
+  if (s == 0) N.count[0] = N.S;
   flags[s] = FLAG_FULL;
 }
 
@@ -77,6 +82,7 @@ __global__ void __launch_bounds__(32 * TR_WARPS) tr_step_kernel(NewtonDev N, int
     if (lane == 0) flags[s] = 0;
     return;
   }
+  if (*N.count <= N.cta_max) return;   // few sources left: tr_step_cta_kernel takes them
   TrSmem& S = sm[warp];
   const double* HL = N.HL + (size_t)s * NP * NP;
   const double* gL = N.gL + (size_t)s * NP;
@@ -138,11 +144,80 @@ __global__ void __launch_bounds__(32 * TR_WARPS) tr_step_kernel(NewtonDev N, int
   }
 }
 
+// The same step on four warps per source (trsolve_cta.cuh), for iterations that start with at most
+// N.cta_max active sources: one CTA per listed source.  The float64 pipes of all four SM
+// sub-partitions then work on one subproblem, where the one-warp kernel would leave three idle.
+__global__ void __launch_bounds__(128, 2) tr_step_cta_kernel(NewtonDev N, int* flags) {
+  extern __shared__ __align__(16) unsigned char tr_cta_smem[];
+  TrSmemQ& S = *reinterpret_cast<TrSmemQ*>(tr_cta_smem);
+  const int count = *N.count;
+  if (count > N.cta_max) return;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  for (int q = blockIdx.x; q < count; q += gridDim.x) {
+    const int s = N.list[q];
+    int* st = N.state + ST_STRIDE * s;
+    const double* HL = N.HL + (size_t)s * NP * NP;
+    const double* gL = N.gL + (size_t)s * NP;
+    const double gk = lane < NP ? -gL[lane] : 0.0;
+    bool finite = isfinite(N.L[s]) & isfinite(gk);
+#pragma unroll
+    for (int i = lane; i < NP * NP; i += 32) finite &= isfinite(HL[i]);
+    finite = __all_sync(0xffffffffu, finite);   // (every warp reads the same data: same decision)
+    if (!finite) {
+      if (tid == 0) {
+        st[ST_ACTIVE] = 0;
+        st[ST_STATUS] = CELESTE_STATUS_NONFINITE;
+        flags[s] = 0;
+      }
+      continue;
+    }
+    if (warp_max(fabs(gk)) <= N.gtol) {
+      if (tid == 0) {
+        st[ST_ACTIVE] = 0;
+        st[ST_STATUS] = CELESTE_STATUS_CONVERGED;
+        flags[s] = 0;
+      }
+      continue;
+    }
+    const double delta = N.delta[s];
+    const bool same = st[ST_SAME] != 0;
+    const bool use_cache = same && st[ST_CACHED];
+    const bool try_newton = !same && st[ST_ITERS] > 0 && !st[ST_BOUNDARY];
+    double* cache = N.tcache + (size_t)s * TR_CACHE;
+    double pk = 0.0, pred = 0.0, lam = -1.0;
+    int hard = 0;
+    // (every thread has read the source's state before the solver's first barrier; warp 0
+    // writes it back below)
+    const bool reduced = tr_solve_q(S, HL, -1.0, gk, delta, try_newton, use_cache ? cache : nullptr, cache,
+                                    N.lam[s], lam, pk, pred, hard);
+    if (w == 0) {
+      const double pnorm = sqrt(warp_sum(lane < NP ? pk * pk : 0.0));
+      if (lane < NP) N.trial[(size_t)s * NP + lane] = N.theta[(size_t)s * NP + lane] + pk;
+      if (lane == 0) {
+        st[ST_CACHED] = use_cache || reduced;
+        N.lam[s] = lam;
+        N.pred[s] = pred;
+        st[ST_ITERS] += 1;
+        st[ST_BOUNDARY] = pnorm >= (1.0 - 1e-9) * delta;
+        if (!st[ST_BOUNDARY] && pred <= N.ftol * fabs(N.L[s])) {
+          st[ST_ACTIVE] = 0;
+          st[ST_STATUS] = CELESTE_STATUS_CONVERGED;
+          flags[s] = 0;
+        } else {
+          flags[s] = FLAG_VALUE;
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // Batched subproblem solve for testing and standalone use: one warp per problem.
 __global__ void __launch_bounds__(32 * TR_WARPS) tr_solve_batch_kernel(const double* __restrict__ B,
                                                                        const double* __restrict__ g,
                                                                        const double* __restrict__ delta, int n,
-                                                                       double* p, double* pred, int* hard) {
+                                                                       const double* __restrict__ hint, double* p,
+                                                                       double* pred, int* hard, double* lam_out) {
   __shared__ TrSmem sm[TR_WARPS];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int q = blockIdx.x * TR_WARPS + warp;
@@ -151,11 +226,40 @@ __global__ void __launch_bounds__(32 * TR_WARPS) tr_solve_batch_kernel(const dou
   const double gk = lane < NP ? g[(size_t)q * NP + lane] : 0.0;
   double pk, pr, lam;
   int hc;
-  tr_solve_warp(S, B + (size_t)q * NP * NP, 1.0, gk, delta[q], true, nullptr, nullptr, -1.0, lam, pk, pr, hc);
+  tr_solve_warp(S, B + (size_t)q * NP * NP, 1.0, gk, delta[q], true, nullptr, nullptr, hint ? hint[q] : -1.0, lam,
+                pk, pr, hc);
   if (lane < NP) p[(size_t)q * NP + lane] = pk;
   if (lane == 0) {
     if (pred) pred[q] = pr;
     if (hard) hard[q] = hc;
+    if (lam_out) lam_out[q] = lam;
+  }
+}
+
+// The same on four warps per problem (one CTA each).
+__global__ void __launch_bounds__(128, 2) tr_solve_batch_cta_kernel(const double* __restrict__ B,
+                                                                   const double* __restrict__ g,
+                                                                   const double* __restrict__ delta, int n,
+                                                                   const double* __restrict__ hint, double* p,
+                                                                   double* pred, int* hard, double* lam_out) {
+  extern __shared__ __align__(16) unsigned char tr_cta_smem[];
+  TrSmemQ& S = *reinterpret_cast<TrSmemQ*>(tr_cta_smem);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int q = blockIdx.x; q < n; q += gridDim.x) {
+    const double gk = lane < NP ? g[(size_t)q * NP + lane] : 0.0;
+    double pk = 0.0, pr = 0.0, lam = -1.0;
+    int hc = 0;
+    tr_solve_q(S, B + (size_t)q * NP * NP, 1.0, gk, delta[q], true, nullptr, nullptr, hint ? hint[q] : -1.0, lam, pk,
+               pr, hc);
+    if (w == 0) {
+      if (lane < NP) p[(size_t)q * NP + lane] = pk;
+      if (lane == 0) {
+        if (pred) pred[q] = pr;
+        if (hard) hard[q] = hc;
+        if (lam_out) lam_out[q] = lam;
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -215,9 +319,13 @@ __global__ void tr_update_kernel(NewtonDev N, int* flags) {
     }
     active = st[ST_ACTIVE];
   }
-  // count active sources (one atomic per warp)
+  // count and list the active sources (one atomic per warp)
   const unsigned m = __ballot_sync(0xffffffffu, active);
-  if ((threadIdx.x & 31) == 0 && m) atomicAdd(N.count, __popc(m));
+  const int lane = threadIdx.x & 31;
+  int base = 0;
+  if (lane == 0 && m) base = atomicAdd(N.count, __popc(m));
+  base = __shfl_sync(0xffffffffu, base, 0);
+  if (active) N.list[base + __popc(m & ((1u << lane) - 1u))] = s;
 }
 
 __global__ void newton_finish_kernel(NewtonDev N, int32_t* iters, int32_t* status, double* elbo) {
@@ -230,7 +338,7 @@ __global__ void newton_finish_kernel(NewtonDev N, int32_t* iters, int32_t* statu
 
 // Kernels launched by one Newton iteration (newton_iteration below), and profiling events recorded
 // by it: value kernel (0, 1), full kernel (2, 3), subproblem step (4, 5).
-constexpr int NEWTON_KERNELS_PER_ITER = 12;
+constexpr int NEWTON_KERNELS_PER_ITER = 13;
 constexpr int EV_PER_ITER = 6;
 
 // The launches of one Newton iteration: subproblem step, value at the trial point, accept/reject,
@@ -247,6 +355,8 @@ static cudaError_t newton_iteration(const ProblemDev& D, const NewtonDev& N, cud
   cudaError_t e;
   if ((e = mark(4)) != cudaSuccess) return e;
   tr_step_kernel<<<(S + TR_WARPS - 1) / TR_WARPS, 32 * TR_WARPS, 0, st>>>(N, D.flags);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  tr_step_cta_kernel<<<std::max(1, std::min(N.cta_max, 2 * D.n_sm)), 128, sizeof(TrSmemQ), st>>>(N, D.flags);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = mark(5)) != cudaSuccess) return e;
   if ((e = launch_worklists(D, FLAG_VALUE, st)) != cudaSuccess) return e;
@@ -294,6 +404,8 @@ extern "C" int celeste_newton_batch(celeste_problem* p, double* theta, const cel
   N.tcache = reinterpret_cast<double*>(p->base + L.nt_tcache);
   N.count = reinterpret_cast<int*>(p->base + L.nt_count);
   N.lam = reinterpret_cast<double*>(p->base + L.nt_lam);
+  N.list = reinterpret_cast<int*>(p->base + L.nt_list);
+  N.cta_max = o.cta_sources > 0 ? o.cta_sources : (o.cta_sources == 0 ? 2 * p->dev.n_sm : -1);
   N.S = p->S;
   N.ftol = o.ftol > 0 ? o.ftol : 1e-8;
   N.gtol = o.gtol > 0 ? o.gtol : 1e-10;
@@ -307,6 +419,17 @@ extern "C" int celeste_newton_batch(celeste_problem* p, double* theta, const cel
   const int K = std::max(1, std::min(o.graph_iters > 0 ? o.graph_iters : 4, max_iter));
   const bool prof = p->prof_on;
   cudaError_t e;
+  {
+    static bool attr_set[64] = {};
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return cuda_fail(e, "device");
+    if (dev < 64 && !attr_set[dev]) {
+      if ((e = cudaFuncSetAttribute(tr_step_cta_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)sizeof(TrSmemQ))) != cudaSuccess)
+        return cuda_fail(e, "tr_step_cta_kernel shared memory");
+      attr_set[dev] = true;
+    }
+  }
   // events bracketing each iteration's value and full evaluation (profiling only)
   while (prof && p->iter_events.size() < (size_t)(EV_PER_ITER * K)) {
     cudaEvent_t ev;
@@ -421,12 +544,37 @@ extern "C" int celeste_newton_batch(celeste_problem* p, double* theta, const cel
 
 extern "C" int celeste_tr_solve_batch(const double* B, const double* g, const double* delta, int n, double* p,
                                       double* pred, int32_t* hard, celeste_stream_t stream) {
+  return celeste_tr_solve_batch_ex(B, g, delta, n, 1, nullptr, p, pred, hard, nullptr, stream);
+}
+
+extern "C" int celeste_tr_solve_batch_ex(const double* B, const double* g, const double* delta, int n, int warps,
+                                         const double* lam_hint, double* p, double* pred, int32_t* hard, double* lam,
+                                         celeste_stream_t stream) {
   if (n < 0 || (n > 0 && (!B || !g || !delta || !p))) return fail(CELESTE_ERR_INVALID_ARG, "null argument");
+  if (warps != 1 && warps != 4) return fail(CELESTE_ERR_INVALID_ARG, "warps must be 1 or 4");
   if (n == 0) return CELESTE_OK;
-  tr_solve_batch_kernel<<<(n + TR_WARPS - 1) / TR_WARPS, 32 * TR_WARPS, 0, (cudaStream_t)stream>>>(B, g, delta, n, p,
-                                                                                                 pred, hard);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return cuda_fail(e, "tr_solve_batch_kernel");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e;
+  if (warps == 1) {
+    tr_solve_batch_kernel<<<(n + TR_WARPS - 1) / TR_WARPS, 32 * TR_WARPS, 0, st>>>(B, g, delta, n, lam_hint, p, pred,
+                                                                                   hard, lam);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "tr_solve_batch_kernel");
+    return CELESTE_OK;
+  }
+  static bool attr_set[64] = {};
+  int dev = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return cuda_fail(e, "device");
+  if (dev < 64 && !attr_set[dev]) {
+    if ((e = cudaFuncSetAttribute(tr_solve_batch_cta_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)sizeof(TrSmemQ))) != cudaSuccess)
+      return cuda_fail(e, "tr_solve_batch_cta_kernel shared memory");
+    attr_set[dev] = true;
+  }
+  tr_solve_batch_cta_kernel<<<std::min(n, 1024), 128, sizeof(TrSmemQ), st>>>(B, g, delta, n, lam_hint, p, pred, hard,
+                                                                              lam);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "tr_solve_batch_cta_kernel");
   return CELESTE_OK;
 }
 

@@ -327,6 +327,7 @@ void build_layout(celeste_problem* p) {
   L.nt_tcache = take(sizeof(double) * TR_CACHE * S);
   L.nt_count = take(sizeof(int) * 4);
   L.nt_lam = take(sizeof(double) * S);
+  L.nt_list = take(sizeof(int) * S);
   L.total = o;
 }
 

@@ -11,7 +11,7 @@ namespace celeste {
 struct WsLayout {
   size_t images, patches, tiles, src_patch, nbr, u0, psf_coef, psf, pix, srcmom, ptab, partials, vpartials, flags, err, counters;
   size_t wl, wl_count, snc;
-  size_t nt_f, nt_g, nt_H, nt_trial, nt_pred, nt_ftrial, nt_state, nt_count, nt_tcache, nt_lam;
+  size_t nt_f, nt_g, nt_H, nt_trial, nt_pred, nt_ftrial, nt_state, nt_count, nt_tcache, nt_lam, nt_list;
   size_t total;
 };
 

@@ -76,7 +76,10 @@ __device__ inline double tr_warp_sum(double v) {
 }
 
 // LDL^T of T + lambda I into S.D (reciprocal pivots), S.L; returns false if a pivot is not positive.
-__device__ inline bool tr_ldl(TrSmem& S, double lambda) {
+// (The helpers below take any shared-memory layout with the members they use: the one-warp
+// solver's TrSmem and the four-warp solver's.)
+template <class SM>
+__device__ inline bool tr_ldl(SM& S, double lambda) {
   double Dp = S.d[0] + lambda;
   bool pd = Dp > 0.0;
   double r = tr_rcp(Dp);
@@ -92,7 +95,8 @@ __device__ inline bool tr_ldl(TrSmem& S, double lambda) {
 }
 
 // Solve (L D L^T) x = b (b may alias x).
-__device__ inline void tr_ldl_solve(const TrSmem& S, const double* b, double* x) {
+template <class SM>
+__device__ inline void tr_ldl_solve(const SM& S, const double* b, double* x) {
   x[0] = b[0];
   for (int i = 1; i < TR_N; ++i) x[i] = b[i] - S.L[i] * x[i - 1];
   for (int i = 0; i < TR_N; ++i) x[i] *= S.D[i];
@@ -114,7 +118,8 @@ __device__ inline double tr_norm(const double* x) {
 }
 
 // Float32 Sturm count (only used to bracket lambda_min; the bracket is widened afterwards).
-__device__ inline int tr_sturm_f(const TrSmem& S, float x) {
+template <class SM>
+__device__ inline int tr_sturm_f(const SM& S, float x) {
   float q = (float)S.d[0] - x;
   int c = q < 0.f;
   for (int i = 1; i < TR_N; ++i) {
@@ -127,40 +132,43 @@ __device__ inline int tr_sturm_f(const TrSmem& S, float x) {
 }
 
 // Lane-private evaluation at the lane's own multiplier lam: L D L^T = T + lam I (reciprocal
-// pivots in PR), y = -(T + lam I)^-1 gh in PY; returns false if a pivot is not positive.
+// pivots in PR), y = -(T + lam I)^-1 gh in PY (PL, PR, PY: the warp's [TR_N][32] scratch); returns
+// false if a pivot is not positive.
 // Otherwise pn = |y| and qn2 = y^T (T + lam I)^-1 y (phi'(lam) = qn2 / pn^3 for
 // phi = 1/|y| - 1/delta).  All lanes run the same instruction stream on their own lam, so a pass
 // costs one evaluation's float64 instructions for 32 multipliers.
-__device__ inline bool tr_eval_lane(TrSmem& S, int lane, double lam, double& pn, double& qn2) {
+template <class SM>
+__device__ inline bool tr_eval_lane(const SM& S, double (*PL)[32], double (*PR)[32], double (*PY)[32], int lane,
+                                    double lam, double& pn, double& qn2) {
   double Dp = S.d[0] + lam;
   bool pd = Dp > 0.0;
   double r = tr_rcp(Dp);
   double w = -S.gh[0];
-  S.PR[0][lane] = r;
-  S.PY[0][lane] = w;
+  PR[0][lane] = r;
+  PY[0][lane] = w;
   for (int i = 1; i < TR_N; ++i) {
     const double l = S.off[i] * r;
     Dp = fma(-S.o2[i], r, S.d[i] + lam);
     pd = pd && Dp > 0.0;
     r = tr_rcp(Dp);
     w = fma(-l, w, -S.gh[i]);
-    S.PL[i][lane] = l;
-    S.PR[i][lane] = r;
-    S.PY[i][lane] = w;
+    PL[i][lane] = l;
+    PR[i][lane] = r;
+    PY[i][lane] = w;
   }
   // (finished whatever the pivots' signs, so the warp stays converged; the caller masks by pd)
-  double y = S.PY[TR_N - 1][lane] * S.PR[TR_N - 1][lane];
-  S.PY[TR_N - 1][lane] = y;
+  double y = PY[TR_N - 1][lane] * PR[TR_N - 1][lane];
+  PY[TR_N - 1][lane] = y;
   double p2 = y * y;
   for (int i = TR_N - 2; i >= 0; --i) {
-    y = fma(-S.PL[i + 1][lane], y, S.PY[i][lane] * S.PR[i][lane]);
-    S.PY[i][lane] = y;
+    y = fma(-PL[i + 1][lane], y, PY[i][lane] * PR[i][lane]);
+    PY[i][lane] = y;
     p2 = fma(y, y, p2);
   }
-  double z = S.PY[0][lane], q2 = z * z * S.PR[0][lane];
+  double z = PY[0][lane], q2 = z * z * PR[0][lane];
   for (int i = 1; i < TR_N; ++i) {
-    z = fma(-S.PL[i][lane], z, S.PY[i][lane]);
-    q2 = fma(z * z, S.PR[i][lane], q2);
+    z = fma(-PL[i][lane], z, PY[i][lane]);
+    q2 = fma(z * z, PR[i][lane], q2);
   }
   pn = sqrt(p2);
   qn2 = q2;
@@ -241,7 +249,7 @@ __device__ inline int tr_lambda_parallel(TrSmem& S, int lane, double lo, double 
     }
     __syncwarp();   // (lane choices are selects; the evaluation below must issue once, converged)
     double pn = 0.0, qn2 = 0.0;
-    const bool pd = tr_eval_lane(S, lane, lam, pn, qn2);
+    const bool pd = tr_eval_lane(S, S.PL, S.PR, S.PY, lane, lam, pn, qn2);
     // ---- interior solution
     if (pass == 0 && try_zero) {
       const bool interior = __shfl_sync(0xffffffffu, (int)(pd && pn <= delta), 0) != 0;

@@ -187,14 +187,16 @@ def test_thin_extended_galaxy(P, axis_logit, scale):
     compare_all(P, sc, th, what=f"thin galaxy axis_logit={axis_logit} scale={scale}")
 
 
-def test_newton_matches_oracle_optimum(P):
-    """Batched GPU Newton reaches the oracle's optimum within 1e-4 per identified parameter."""
+@pytest.mark.parametrize("cta_sources", [0, -1], ids=["four_warps", "one_warp"])
+def test_newton_matches_oracle_optimum(P, cta_sources):
+    """Batched GPU Newton reaches the oracle's optimum within 1e-4 per identified parameter, with the
+    subproblems on four warps (few active sources: the default here) and on one warp."""
     sc = synth.single_source(seed=1611, size=41)
     dev = torch.device("cuda:0")
     prob = P.Problem(sc, device=dev)
     th = torch.as_tensor(sc.theta0, device=dev).contiguous()
     prob.render_background(th.clone())
-    delta, iters, status, elbo = prob.newton_batch(th)
+    delta, iters, status, elbo = prob.newton_batch(th, cta_sources=cta_sources)
     torch.cuda.synchronize()
     ref = O.Oracle(sc).newton(0, sc.theta0[0], sc.theta0)
     assert int(status[0]) == P.STATUS_CONVERGED and int(iters[0]) <= 50
@@ -260,16 +262,22 @@ def test_newton_graph_matches_plain_launches(P):
     start = torch.as_tensor(sc.theta0, device=dev).contiguous()
     prob.render_background(start.clone())
     runs = []
-    for graph_iters, max_iter in ((1, 50), (4, 50), (4, 50), (3, 7), (1, 7)):
+    # (cta_sources 6: one warp per subproblem until at most 6 of the 12 sources are left, then four)
+    for graph_iters, max_iter, cta in ((1, 50, 0), (4, 50, 0), (4, 50, 0), (3, 7, 0), (1, 7, 0), (1, 50, 6),
+                                       (4, 50, 6)):
         th = start.clone()
-        delta, iters, status, elbo = prob.newton_batch(th, max_iter=max_iter, graph_iters=graph_iters)
+        delta, iters, status, elbo = prob.newton_batch(th, max_iter=max_iter, graph_iters=graph_iters,
+                                                       cta_sources=cta)
         torch.cuda.synchronize()
         runs.append((max_iter, th.cpu().numpy(), delta.cpu().numpy(), iters.cpu().numpy(), status.cpu().numpy(),
                      elbo.cpu().numpy()))
-    for a, b in ((0, 1), (0, 2), (3, 4)):
+    for a, b in ((0, 1), (0, 2), (3, 4), (5, 6)):
         for x, y in zip(runs[a][1:], runs[b][1:]):
             np.testing.assert_array_equal(x, y)
     assert runs[3][3].max() <= 7
+    # the switch between the layouts changes rounding only
+    assert np.all(runs[5][4] == runs[0][4])
+    np.testing.assert_allclose(runs[5][5], runs[0][5], rtol=1e-7)
 
 
 def test_refresh_pixels_matches_a_fresh_bind(P):

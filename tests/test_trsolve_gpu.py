@@ -61,11 +61,7 @@ def _lambda_rounding(B, g, delta, pr, mo):
     return worst
 
 
-def test_subproblem_matches_oracle(P):
-    B, g, d = _problems(0, 400)
-    dev = torch.device("cuda:0")
-    p, pred, hard = P.tr_solve_batch(*(torch.as_tensor(a, device=dev).contiguous() for a in (B, g, d)))
-    p, pred = p.cpu().numpy(), pred.cpu().numpy()
+def _check_against_oracle(B, g, d, p, pred):
     for i in range(len(d)):
         pr, predr, _ = O.tr_subproblem(g[i], B[i], d[i])
         assert np.linalg.norm(p[i]) <= d[i] * (1 + 1e-9)
@@ -87,7 +83,56 @@ def test_subproblem_matches_oracle(P):
             assert np.abs(p[i] - pr).max() <= 1e-6 * max(np.abs(pr).max(), 1e-300), i
 
 
-def test_subproblem_hard_case(P):
+@pytest.mark.parametrize("warps", [1, 4])
+def test_subproblem_matches_oracle(P, warps):
+    """One warp per problem (iterations with many active sources) and one four-warp CTA per problem
+    (the few-source iterations), each against the oracle's eigendecomposition solution."""
+    B, g, d = _problems(0, 400)
+    dev = torch.device("cuda:0")
+    p, pred, hard = P.tr_solve_batch(*(torch.as_tensor(a, device=dev).contiguous() for a in (B, g, d)), warps=warps)
+    _check_against_oracle(B, g, d, p.cpu().numpy(), pred.cpu().numpy())
+
+
+@pytest.mark.parametrize("warps", [1, 4])
+def test_subproblem_multiplier_hint_changes_only_rounding(P, warps):
+    """The Newton iteration passes each source's previous multiplier to place the first pass of the
+    multiplier search; exact, close, far and absent hints must reach the same solution: the
+    multiplier to the search's tolerance and the model value to 1e-8 plus what float64 leaves
+    undetermined next to the pole (the unhinted solve is held to the oracle by
+    test_subproblem_matches_oracle)."""
+    B, g, d = _problems(1, 240)
+    dev = torch.device("cuda:0")
+    t = lambda a: torch.as_tensor(a, device=dev).contiguous()
+    model = lambda p: np.einsum("ij,ij->i", g, p) + 0.5 * np.einsum("ij,ijk,ik->i", p, B, p)
+    p0, pred0, _, lam0 = P.tr_solve_batch(t(B), t(g), t(d), warps=warps, return_lambda=True)
+    p0, lam0 = p0.cpu().numpy(), lam0.cpu().numpy()
+    m0 = model(p0)
+    assert np.any(lam0 > 0)
+    eig = np.array([np.linalg.eigvalsh(b) for b in B])
+    scale, lmin = np.abs(eig).max(axis=1), eig[:, 0]
+    # what float64 leaves undetermined: the reduction's backward error (tens of ulps of |B|) moves
+    # the pole -lambda_min, and |p(lambda)| ~ 1/(lambda + lambda_min) next to it, so |p| is fixed
+    # to about 64 eps |B| / (lambda + lambda_min) relative; along the boundary path the model moves
+    # by lambda delta^2 times that
+    lam_ref = np.where(lam0 > 0, lam0, 0.0)
+    res = np.where(lam_ref > 0, np.minimum(1.0, 64 * np.finfo(float).eps * scale /
+                                           np.maximum(lam_ref + lmin, 1e-300)), 0.0)
+    slack = lam_ref * d ** 2 * res + 1e-8 * np.abs(m0) + 1e-300
+    for f in (1.0, 1.0 + 1e-7, 0.3, 4.0, 1e3, 1e-3):
+        hint = np.where(lam0 > 0, lam0 * f, -1.0)
+        p, pred, _, lam = P.tr_solve_batch(t(B), t(g), t(d), warps=warps, lam_hint=t(hint), return_lambda=True)
+        p, lam = p.cpu().numpy(), lam.cpu().numpy()
+        assert np.all(np.linalg.norm(p, axis=1) <= d * (1 + 1e-9)), f
+        m = model(p)
+        bad = np.abs(m - m0) > slack
+        assert not bad.any(), (f, np.nonzero(bad)[0][:5], m[bad][:3], m0[bad][:3])
+        both = (lam0 > 0) & (lam > 0)
+        # |p(lambda)| = delta to 1e-10 relative: lambda is fixed to about that times its scale
+        assert np.all(np.abs(lam[both] - lam0[both]) <= 1e-6 * (lam0[both] + scale[both])), f
+
+
+@pytest.mark.parametrize("warps", [1, 4])
+def test_subproblem_hard_case(P, warps):
     rng = np.random.default_rng(4)
     Q, _ = np.linalg.qr(rng.normal(size=(27, 27)))
     lam = np.linspace(-2.0, 5.0, 27)
@@ -96,7 +141,7 @@ def test_subproblem_hard_case(P):
     delta = 5.0
     dev = torch.device("cuda:0")
     t = lambda a: torch.as_tensor(a, device=dev).contiguous()
-    p, pred, hard = P.tr_solve_batch(t(B[None]), t(g[None]), t(np.array([delta])))
+    p, pred, hard = P.tr_solve_batch(t(B[None]), t(g[None]), t(np.array([delta])), warps=warps)
     p = p.cpu().numpy()[0]
     assert int(hard[0]) == 1
     assert abs(np.linalg.norm(p) - delta) <= 1e-9 * delta
