@@ -5,7 +5,8 @@ Default workload: a seeded 10 x 10 mosaic of overlapping 2048 x 1489 fields, 100
 1-12 single-band exposures each, patch radius 8-64 px.  One step = one block-coordinate pass over
 every source: render the neighbours' fixed background, run the learned warm-start network on every
 source's patch, then run trust-region Newton (ELBO + exact gradient + dense Hessian per iteration,
-Hessian cross-product on the tensor cores) on every source from that start until all have stopped.
+in the Hessian form and tile size the autotuner picks among those that meet the precision bar:
+FP32 FMAs or a split tensor-core form) on every source from that start until all have stopped.
 The network is trained before the timed region on pairs from two freshly seeded mosaics.  The plain
 form (Newton from the catalog, Hessian on FP32 FMAs, no network) is timed on the same workload at the
 same ELBO tolerance and reported as "plain_fp32".  `--workload field` runs one 2048 x 1489 x 5-band
@@ -56,9 +57,9 @@ MUFU_FULL_PER_PIXEL = 48
 # path does less, the multiplier search more)
 FP64_FLOPS_PER_SUBPROBLEM = 4 * 27 ** 3 // 3
 # bytes per pixel evaluation that the pixel kernel must move: the 16-byte pixel record read and the
-# 8-byte source moments written (the 6880-byte patch table per patch comes on top)
+# 8-byte source moments written (the 7552-byte patch table per patch comes on top)
 BYTES_FULL_PER_PIXEL = 24
-TABLE_BYTES = 6880
+TABLE_BYTES = 7552
 
 
 def parse(argv=None):

@@ -18,7 +18,6 @@ import torch
 from .celeste import HESS_BF16X6, HESS_FP32, HESS_TF32X3, Problem
 
 PRECISE_MODES = (HESS_FP32, HESS_BF16X6, HESS_TF32X3)
-MIXED_MODES = (HESS_BF16X6, HESS_TF32X3)
 
 
 def _subset(scene, idx):
@@ -46,10 +45,10 @@ def _time(sub, dev, tile, mode, theta, reps, device_pixels):
 
 def tune(scene, device="cuda", modes=None, tiles=None, sample=4000, reps=5, seed=0, device_pixels=None):
     """Returns ((tile_pixels, hessian_mode), {"tile/mode": microseconds per 1000 pixels}) for `scene`,
-    timed on a seeded sample of `sample` sources.  modes: candidate Hessian forms (default: the
-    tensor-core forms that meet the precision bar); tiles: candidate tile sizes for the FP32 form
-    (the tensor-core forms use 128)."""
-    modes = MIXED_MODES if modes is None else tuple(modes)
+    timed on a seeded sample of `sample` sources.  modes: candidate Hessian forms (default: every form
+    that meets the precision bar); tiles: candidate tile sizes for the FP32 form (the tensor-core
+    forms use 128)."""
+    modes = PRECISE_MODES if modes is None else tuple(modes)
     tiles = (128, 256, 512) if tiles is None else tuple(tiles)
     S = scene.n_sources
     rng = np.random.default_rng(seed)

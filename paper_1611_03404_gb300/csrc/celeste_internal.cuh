@@ -38,15 +38,29 @@ constexpr int NRED = 11;
 constexpr int TB_MU = 0;      // 3 x (x, y) mean of PSF component k, + 2 pad
 constexpr int TB_STAR = 8;    // 3 x (W, P00, P01, P11)
 constexpr int TB_GAL = 20;    // NGAL x GT_STRIDE, component g = k * NMIX + j
+// A galaxy component's entry is laid out for the pixel kernel's two-wide float32 arithmetic: the
+// numbers combined in one packed operation sit side by side at an even offset (a few are stored
+// twice).  Q_a = -1/2 dP/da (entries 00, 01, 11; a = axis, angle, scale), l_a = -1/2 d logdet/da,
+// Q_ab and l_ab their second derivatives for the pairs ab = 00 01 02 11 12 22 (index pq 0-5).
 constexpr int GT_P = 0;       // 3: precision matrix (00, 01, 11)
 constexpr int GT_W = 3;       // weight * Gaussian normaliser, w_k nu_j / (2 pi sqrt(det)) (fracDev mixing applied later)
-constexpr int GT_QA = 4;      // 3 x 3: -1/2 dP/da, a = axis, angle, scale
-constexpr int GT_LA = 13;     // 3: -1/2 d logdet / da
-constexpr int GT_QAB = 16;    // 6 x 3: -1/2 d2P/dadb, pairs (00 01 02 11 12 22)
-constexpr int GT_LAB = 34;    // 6: -1/2 d2 logdet / dadb
-constexpr int GT_STRIDE = 40;
+constexpr int GT_PZ = 4;      // (P01, P11): with (P00, P01) the rows of P
+constexpr int GT_LA01 = 6;    // (l_0, l_1)
+constexpr int GT_Q01 = 8;     // (Q_0[i], Q_1[i]) for i = 00, 01, 11
+constexpr int GT_Q2 = 14;     // (Q_2[00], Q_2[01]), (Q_2[01], Q_2[11])
+constexpr int GT_LA2 = 18;    // l_2 (19: pad)
+constexpr int GT_CAB = 20;    // 3 groups of two pairs pq = (0, 1), (2, 3), (4, 5), 8 floats each:
+                              // (l_p, l_q), then (Q_p[i], Q_q[i]) for i = 00, 01, 11
+constexpr int GT_STRIDE = 44;
+// Offsets of the single numbers (the first of a number stored twice).
+__host__ __device__ constexpr int gt_qa(int a, int i) {
+  return a < 2 ? GT_Q01 + 2 * i + a : GT_Q2 + (i == 0 ? 0 : (i == 1 ? 1 : 3));
+}
+__host__ __device__ constexpr int gt_la(int a) { return a < 2 ? GT_LA01 + a : GT_LA2; }
+__host__ __device__ constexpr int gt_qab(int pq, int i) { return GT_CAB + 8 * (pq / 2) + 2 * (i + 1) + (pq % 2); }
+__host__ __device__ constexpr int gt_lab(int pq) { return GT_CAB + 8 * (pq / 2) + (pq % 2); }
 constexpr int TB_SNC = TB_GAL + NGAL * GT_STRIDE;   // SNConst
-constexpr int TB_FLOATS = TB_SNC + 20;              // 1720 floats = 6880 bytes (multiple of 16)
+constexpr int TB_FLOATS = TB_SNC + 20;              // 1888 floats = 7552 bytes (multiple of 16)
 
 // Per-(source, image) scalar constants used by the pixel kernels.
 struct SNConst {

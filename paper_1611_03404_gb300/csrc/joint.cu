@@ -167,10 +167,8 @@ __device__ inline void jac_rows(const float* tab, float fx, float fy, JacRows& r
       const int fam = j < CELESTE_NEXP ? 0 : 1;
       float b[3];
 #pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        const float* Q = e + GT_QA + 3 * a;
-        b[a] = e[GT_LA + a] + Q[0] * s0 + Q[1] * s1 + Q[2] * s2;
-      }
+      for (int a = 0; a < 3; ++a)
+        b[a] = e[gt_la(a)] + e[gt_qa(a, 0)] * s0 + e[gt_qa(a, 1)] * s1 + e[gt_qa(a, 2)] * s2;
       const float z0 = e[GT_P] * d0 + e[GT_P + 1] * d1, z1 = e[GT_P + 1] * d0 + e[GT_P + 2] * d1;
       const float v[6] = {N, N * z0, N * z1, N * b[0], N * b[1], N * b[2]};
       // (statically indexed accumulators: one branch per family)

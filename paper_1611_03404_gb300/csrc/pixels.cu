@@ -296,14 +296,65 @@ __device__ __forceinline__ void syrk_mma(const float (*As)[SYRK_LD], const float
   }
 }
 
-// One galaxy mixture component's contribution at pixel offset d (squares s): value, 5 first and 15
-// second derivatives over v5 = (mu0, mu1, axis, angle, scale), accumulated into its family's sums.
+// Two-wide float32 arithmetic (one packed instruction for two independent multiply-adds: half
+// the issue slots of the scalar form, which bounds this kernel).
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+
+// One galaxy family's sums over its components at a pixel: value F, first derivatives over
+// v5 = (mu0, mu1, axis, angle, scale) and second derivatives, the latter kept in the pairs that the
+// packed updates below form.
+struct GalAcc {
+  float F;
+  float2 v01, v23;              // d/dv (0, 1), (2, 3)
+  float v4;
+  float2 vv00_01;               // d2/dv dv: (0,0), (0,1)
+  float vv11;                   // (1,1)
+  float2 vv02_03, vv12_13;      // (0,2), (0,3); (1,2), (1,3)
+  float2 vv04_14;               // (0,4), (1,4)
+  float2 vv22_23, vv24_33, vv34_44;
+  __device__ __forceinline__ void zero() {
+    F = v4 = vv11 = 0.f;
+    v01 = v23 = vv00_01 = vv02_03 = vv12_13 = vv04_14 = vv22_23 = vv24_33 = vv34_44 = f2(0.f, 0.f);
+  }
+  __device__ __forceinline__ float v(int a) const {
+    return a == 0 ? v01.x : a == 1 ? v01.y : a == 2 ? v23.x : a == 3 ? v23.y : v4;
+  }
+  // (a, b) with a <= b
+  __device__ __forceinline__ float vv(int a, int b) const {
+    switch (a * 5 + b) {
+      case 0: return vv00_01.x;
+      case 1: return vv00_01.y;
+      case 2: return vv02_03.x;
+      case 3: return vv02_03.y;
+      case 4: return vv04_14.x;
+      case 6: return vv11;
+      case 7: return vv12_13.x;
+      case 8: return vv12_13.y;
+      case 9: return vv04_14.y;
+      case 12: return vv22_23.x;
+      case 13: return vv22_23.y;
+      case 14: return vv24_33.x;
+      case 18: return vv24_33.y;
+      case 19: return vv34_44.x;
+      default: return vv34_44.y;   // 24: (4, 4)
+    }
+  }
+};
+
+// One galaxy mixture component's contribution at pixel offset d (squares s; D0, D1, S0-S2 the
+// same numbers in both halves of a pair): value, 5 first and 15 second derivatives over v5,
+// accumulated into its family's sums.  z = P d, q = d.P.d = z.d; b_a = l_a + Q_a.s and
+// t_a = (Q_a d) for a = axis, angle, scale; the second derivatives N (z z^T - P),
+// N (z_i b_a - 2 t_a,i), N (b_a b_b + c_ab) with c_ab = l_ab + Q_ab.s.
 // Far from a narrow component its Gaussian underflows to exactly 0 (q > ~207): where that holds on
 // every lane of the warp (lanes without a pixel count as 0) the component adds exactly nothing, and
 // the warp skips its derivative terms (on the mosaic ~19 % of warp-component pairs).  All lanes of
 // the warp must be active.
-__device__ __forceinline__ void gal_component(const float* ep, float d0, float d1, float s0, float s1, float s2,
-                                              bool valid, float& F, float (&Fv)[5], float (&Fvv)[15]) {
+__device__ __forceinline__ void gal_component(const float* ep, float2 D0, float2 D1, float2 S0, float2 S1, float2 S2,
+                                              bool valid, GalAcc& A) {
   float e[GT_STRIDE];
   const float4* e4 = reinterpret_cast<const float4*>(ep);
 #pragma unroll
@@ -314,45 +365,43 @@ __device__ __forceinline__ void gal_component(const float* ep, float d0, float d
     e[4 * w + 2] = t4.z;
     e[4 * w + 3] = t4.w;
   }
-  const float q = e[GT_P] * s0 + e[GT_P + 1] * s1 + e[GT_P + 2] * s2;
+  // (q as in the value kernels, which difference-mode trial values are compared against)
+  const float q = e[GT_P] * S0.x + e[GT_P + 1] * S1.x + e[GT_P + 2] * S2.x;
   const float N = e[GT_W] * exp2f(q * (-0.5f * LOG2E));
   if (__all_sync(0xffffffffu, N == 0.f || !valid)) return;
-  const float z0 = e[GT_P] * d0 + e[GT_P + 1] * d1, z1 = e[GT_P + 1] * d0 + e[GT_P + 2] * d1;
-  float b[3], t0[3], t1[3];
+  const float2 z = fma2(f2(e[GT_PZ], e[GT_PZ + 1]), D1, mul2(f2(e[GT_P], e[GT_P + 1]), D0));   // (z0, z1)
+  // axis and angle together, scale alone
+  const float2 Q0 = f2(e[GT_Q01], e[GT_Q01 + 1]), Q1 = f2(e[GT_Q01 + 2], e[GT_Q01 + 3]),
+               Q2 = f2(e[GT_Q01 + 4], e[GT_Q01 + 5]);                       // (Q_0[i], Q_1[i])
+  const float2 b01 = fma2(Q2, S2, fma2(Q1, S1, fma2(Q0, S0, f2(e[GT_LA01], e[GT_LA01 + 1]))));
+  const float2 t0 = fma2(Q1, D1, mul2(Q0, D0));     // (t_0[0], t_1[0])
+  const float2 t1 = fma2(Q2, D1, mul2(Q1, D0));     // (t_0[1], t_1[1])
+  const float b2 = fmaf(e[GT_Q2 + 3], S2.x, fmaf(e[GT_Q2 + 1], S1.x, fmaf(e[GT_Q2], S0.x, e[GT_LA2])));
+  const float2 t2 = fma2(f2(e[GT_Q2 + 2], e[GT_Q2 + 3]), D1, mul2(f2(e[GT_Q2], e[GT_Q2 + 1]), D0));   // t_2
+  const float2 NN = f2(N, N);
+  const float2 Nz = mul2(NN, z);
+  const float2 Nm2 = f2(-2.f * N, -2.f * N);
+  const float2 Nb01 = mul2(NN, b01);
+  const float Nb2 = N * b2;
+  A.F += N;
+  A.v01 = add2(A.v01, Nz);
+  A.v23 = add2(A.v23, Nb01);
+  A.v4 += Nb2;
+  A.vv00_01 = fma2(f2(-N, -N), f2(e[GT_P], e[GT_P + 1]), fma2(f2(Nz.x, Nz.x), z, A.vv00_01));
+  A.vv11 = fmaf(-N, e[GT_P + 2], fmaf(Nz.y, z.y, A.vv11));
+  A.vv02_03 = fma2(Nm2, t0, fma2(f2(Nz.x, Nz.x), b01, A.vv02_03));
+  A.vv12_13 = fma2(Nm2, t1, fma2(f2(Nz.y, Nz.y), b01, A.vv12_13));
+  A.vv04_14 = fma2(Nm2, t2, fma2(Nz, f2(b2, b2), A.vv04_14));
+  // c_ab for the pairs (00, 01), (02, 11), (12, 22)
+  float2 c[3];
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    const float* Q = e + GT_QA + 3 * a;
-    b[a] = e[GT_LA + a] + Q[0] * s0 + Q[1] * s1 + Q[2] * s2;
-    t0[a] = Q[0] * d0 + Q[1] * d1;   // (Q_a d); (dP/da) d = -2 Q_a d
-    t1[a] = Q[1] * d0 + Q[2] * d1;
+  for (int g = 0; g < 3; ++g) {
+    const float* G = e + GT_CAB + 8 * g;
+    c[g] = fma2(f2(G[6], G[7]), S2, fma2(f2(G[4], G[5]), S1, fma2(f2(G[2], G[3]), S0, f2(G[0], G[1]))));
   }
-  const float Nz0 = N * z0, Nz1 = N * z1, Nm2 = -2.f * N;
-  F += N;
-  Fv[0] += Nz0;
-  Fv[1] += Nz1;
-  float Nb[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    Nb[a] = N * b[a];
-    Fv[2 + a] += Nb[a];
-  }
-  Fvv[tri5(0, 0)] += Nz0 * z0 - N * e[GT_P];
-  Fvv[tri5(0, 1)] += Nz0 * z1 - N * e[GT_P + 1];
-  Fvv[tri5(1, 1)] += Nz1 * z1 - N * e[GT_P + 2];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    Fvv[tri5(0, 2 + a)] += Nz0 * b[a] + Nm2 * t0[a];
-    Fvv[tri5(1, 2 + a)] += Nz1 * b[a] + Nm2 * t1[a];
-  }
-  int pq = 0;
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int bb = a; bb < 3; ++bb, ++pq) {
-      const float* Q = e + GT_QAB + 3 * pq;
-      const float cab = e[GT_LAB + pq] + Q[0] * s0 + Q[1] * s1 + Q[2] * s2;
-      Fvv[tri5(2 + a, 2 + bb)] += Nb[a] * b[bb] + N * cab;
-    }
+  A.vv22_23 = fma2(NN, c[0], fma2(f2(Nb01.x, Nb01.x), b01, A.vv22_23));
+  A.vv24_33 = fma2(NN, c[1], fma2(Nb01, f2(b2, b01.y), A.vv24_33));
+  A.vv34_44 = fma2(NN, c[2], fma2(f2(Nb01.y, Nb2), f2(b2, b2), A.vv34_44));
 }
 
 // ------------------------------------------------------------------------------ full kernel
@@ -364,7 +413,7 @@ __device__ __forceinline__ void gal_component(const float* ep, float d0, float d
 // of static shared memory.)
 template <int PPT, int HM>
 __global__ void __launch_bounds__(BLOCK) elbo_full_kernel(ProblemDev P) {
-  constexpr int NB = 2;
+  constexpr int NB = PPT >= 8 ? 1 : 2;   // (1024-pixel tiles: two pixel buffers would pass 48 KB)
   __shared__ __align__(16) float tab_buf[NB][TB_FLOATS];
   __shared__ __align__(16) float4 spix_buf[NB][BLOCK * PPT];
   __shared__ __align__(8) uint64_t bar[NB];
@@ -423,19 +472,14 @@ __global__ void __launch_bounds__(BLOCK) elbo_full_kernel(ProblemDev P) {
     // ---- profiles: star (value, d/dmu, d2/dmu2); galaxy families exp/deV over
     //      v5 = (mu0, mu1, axis, angle, scale): value, 5 first, 15 second derivatives
     float f0 = 0.f, f0m[2] = {0.f, 0.f}, f0mm[3] = {0.f, 0.f, 0.f};
-    float F[2], Fv[2][5], Fvv[2][15];
-#pragma unroll
-    for (int fam = 0; fam < 2; ++fam) {
-      F[fam] = 0.f;
-#pragma unroll
-      for (int a = 0; a < 5; ++a) Fv[fam][a] = 0.f;
-#pragma unroll
-      for (int a = 0; a < 15; ++a) Fvv[fam][a] = 0.f;
-    }
+    GalAcc G[2];
+    G[0].zero();
+    G[1].zero();
 #pragma unroll 1
     for (int k = 0; k < CELESTE_NPSF; ++k) {
       const float d0 = fx - tab[TB_MU + 2 * k], d1 = fy - tab[TB_MU + 2 * k + 1];
       const float s0 = d0 * d0, s1 = 2.f * d0 * d1, s2 = d1 * d1;
+      const float2 D0 = f2(d0, d0), D1 = f2(d1, d1), S0 = f2(s0, s0), S1 = f2(s1, s1), S2 = f2(s2, s2);
       {
         const float4 st = *reinterpret_cast<const float4*>(&tab[TB_STAR + 4 * k]);
         const float q = st.y * s0 + st.z * s1 + st.w * s2;
@@ -452,10 +496,10 @@ __global__ void __launch_bounds__(BLOCK) elbo_full_kernel(ProblemDev P) {
       // instruction cache, and each family's accumulators stay statically indexed
 #pragma unroll 1
       for (int j = 0; j < CELESTE_NEXP; ++j)
-        gal_component(&tab[TB_GAL + (k * NMIX + j) * GT_STRIDE], d0, d1, s0, s1, s2, valid, F[0], Fv[0], Fvv[0]);
+        gal_component(&tab[TB_GAL + (k * NMIX + j) * GT_STRIDE], D0, D1, S0, S1, S2, valid, G[0]);
 #pragma unroll 1
       for (int j = CELESTE_NEXP; j < NMIX; ++j)
-        gal_component(&tab[TB_GAL + (k * NMIX + j) * GT_STRIDE], d0, d1, s0, s1, s2, valid, F[1], Fv[1], Fvv[1]);
+        gal_component(&tab[TB_GAL + (k * NMIX + j) * GT_STRIDE], D0, D1, S0, S1, S2, valid, G[1]);
     }
 
     // ---- galaxy profile over G6 = (mu0, mu1, dev, axis, angle, scale);  v5 index -> G6 index:
@@ -467,19 +511,19 @@ __global__ void __launch_bounds__(BLOCK) elbo_full_kernel(ProblemDev P) {
     cx.f0mm[0] = f0mm[0];
     cx.f0mm[1] = f0mm[1];
     cx.f0mm[2] = f0mm[2];
-    const float dF = F[1] - F[0];
-    cx.f1 = F[0] + c.e * dF;
+    const float dF = G[1].F - G[0].F;
+    cx.f1 = G[0].F + c.e * dF;
     cx.f1g[2] = c.e1 * dF;
     cx.f1gg[tri6(2, 2)] = c.e2 * dF;
 #pragma unroll
     for (int a = 0; a < 5; ++a) {
       const int ga = a < 2 ? a : a + 1;
-      cx.f1g[ga] = Fv[0][a] + c.e * (Fv[1][a] - Fv[0][a]);
-      cx.f1gg[ga < 2 ? tri6(ga, 2) : tri6(2, ga)] = c.e1 * (Fv[1][a] - Fv[0][a]);
+      cx.f1g[ga] = G[0].v(a) + c.e * (G[1].v(a) - G[0].v(a));
+      cx.f1gg[ga < 2 ? tri6(ga, 2) : tri6(2, ga)] = c.e1 * (G[1].v(a) - G[0].v(a));
 #pragma unroll
       for (int bb = a; bb < 5; ++bb) {
         const int gb = bb < 2 ? bb : bb + 1;
-        cx.f1gg[tri6(ga, gb)] = Fvv[0][tri5(a, bb)] + c.e * (Fvv[1][tri5(a, bb)] - Fvv[0][tri5(a, bb)]);
+        cx.f1gg[tri6(ga, gb)] = G[0].vv(a, bb) + c.e * (G[1].vv(a, bb) - G[0].vv(a, bb));
       }
     }
     const float f1 = cx.f1;

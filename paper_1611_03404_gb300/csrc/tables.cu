@@ -94,15 +94,19 @@ __device__ inline void gal_entry(const GalShapeT<T>& gs, const T A[4], const Sym
   e[GT_P + 2] = (float)Pm.c;
   e[GT_W] = (float)gauss_weight(w, S);
   if (!full) return;
+  e[GT_PZ + 0] = (float)Pm.b;
+  e[GT_PZ + 1] = (float)Pm.c;
+  e[GT_LA2 + 1] = 0.f;
   Mat2T<T> PdS[3];
   for (int a = 0; a < 3; ++a) {
     const Sym2T<T> t = congruence(A, gs.d[a]);
     PdS[a] = mul(Pm, Sym2T<T>{tau * t.a, tau * t.b, tau * t.c});
     const Sym2T<T> dP = to_sym(mul(PdS[a], Pm));   // P dS P = -dP/da
-    e[GT_QA + 3 * a + 0] = (float)(T(0.5) * dP.a);
-    e[GT_QA + 3 * a + 1] = (float)(T(0.5) * dP.b);
-    e[GT_QA + 3 * a + 2] = (float)(T(0.5) * dP.c);
-    e[GT_LA + a] = (float)(T(-0.5) * trace(PdS[a]));
+    e[gt_qa(a, 0)] = (float)(T(0.5) * dP.a);
+    e[gt_qa(a, 1)] = (float)(T(0.5) * dP.b);
+    e[gt_qa(a, 2)] = (float)(T(0.5) * dP.c);
+    if (a == 2) e[GT_Q2 + 2] = (float)(T(0.5) * dP.b);   // Q_2[01], second copy
+    e[gt_la(a)] = (float)(T(-0.5) * trace(PdS[a]));
   }
   int q = 0;
   for (int a = 0; a < 3; ++a)
@@ -113,10 +117,10 @@ __device__ inline void gal_entry(const GalShapeT<T>& gs, const T A[4], const Sym
       const Sym2T<T> two = sym_plus_t(mul(X, Pm));
       const Mat2T<T> Pd2 = mul(Pm, d2S);
       const Sym2T<T> third = to_sym(mul(Pd2, Pm));
-      e[GT_QAB + 3 * q + 0] = (float)(T(-0.5) * (two.a - third.a));
-      e[GT_QAB + 3 * q + 1] = (float)(T(-0.5) * (two.b - third.b));
-      e[GT_QAB + 3 * q + 2] = (float)(T(-0.5) * (two.c - third.c));
-      e[GT_LAB + q] = (float)(T(-0.5) * (trace(Pd2) - trace(X)));
+      e[gt_qab(q, 0)] = (float)(T(-0.5) * (two.a - third.a));
+      e[gt_qab(q, 1)] = (float)(T(-0.5) * (two.b - third.b));
+      e[gt_qab(q, 2)] = (float)(T(-0.5) * (two.c - third.c));
+      e[gt_lab(q)] = (float)(T(-0.5) * (trace(Pd2) - trace(X)));
     }
 }
 
