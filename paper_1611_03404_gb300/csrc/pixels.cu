@@ -64,6 +64,28 @@ __device__ __forceinline__ float warp_reduce_scatter32(float (&v)[32], int lane)
   return v[0];
 }
 
+// The same through shared memory (T: the warp's 32 x XP_LD scratch): lane l writes its 32 values as
+// row l (eight 16-byte stores; rows XP_LD = 36 floats apart, so each quarter-warp phase of 16-byte
+// stores covers all 32 banks), then sums column l (conflict-free: consecutive lanes, consecutive
+// words), pairwise in packed adds.  About half the instructions of the shuffle form, which needs two
+// selects, a shuffle and an add per value and level.
+constexpr int XP_LD = 36;
+__device__ __forceinline__ float warp_reduce_scatter32_smem(const float (&v)[32], float* T, int lane) {
+  float4* row = reinterpret_cast<float4*>(T + lane * XP_LD);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) row[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+  __syncwarp();
+  float2 p[16];
+#pragma unroll
+  for (int r = 0; r < 16; ++r) p[r] = make_float2(T[(2 * r) * XP_LD + lane], T[(2 * r + 1) * XP_LD + lane]);
+  __syncwarp();   // the scratch is rewritten by the next call
+#pragma unroll
+  for (int w = 8; w >= 1; w >>= 1)
+#pragma unroll
+    for (int r = 0; r < w; ++r) p[r] = __fadd2_rn(p[r], p[r + w]);
+  return p[0].x + p[0].y;
+}
+
 // Thread 0: bulk copies of tile `tile`'s patch table and pixel records into (tab, spix),
 // completing on bar (one expect_tx for both).  The caller has synchronised the CTA since the
 // buffer was last read; the proxy fence orders those generic reads before the async writes.
@@ -420,7 +442,12 @@ __global__ void __launch_bounds__(BLOCK) elbo_full_kernel(ProblemDev P) {
   __shared__ TileDev tmeta[NB];
   __shared__ PatchDev pmeta[NB];
   __shared__ float red[BLOCK / 32][128];
-  __shared__ __align__(16) float syrk[HM ? BLOCK / 32 : 1][2][NRED][SYRK_LD];
+  // per-warp scratch: the tensor-core forms' staging of A' and B'^T, or the FP32 form's transposes
+  // for the reduce-scatter with 128-pixel tiles (with larger tiles the 18 KB cost a CTA per SM,
+  // more than the transposes save)
+  constexpr bool XP = HM == 0 && PPT == 1;
+  constexpr int WB = HM ? 2 * NRED * SYRK_LD : (XP ? 32 * XP_LD : 4);
+  __shared__ __align__(16) float wbuf[BLOCK / 32][WB];
   __shared__ __align__(16) float zrow[HM ? SYRK_LD : 4];
 
   __shared__ int slot;
@@ -587,7 +614,18 @@ __global__ void __launch_bounds__(BLOCK) elbo_full_kernel(ProblemDev P) {
     cx.A0w1 = cx.w1 * c.A0;
     cx.B0w2x2 = 2.f * cx.w2 * c.B0;
 
-    if constexpr (HM == 0) {
+    if constexpr (HM == 0 && XP) {
+      float v[32];
+      float* T = wbuf[warp];
+      fill_chunk<0>(v, cx, std::make_integer_sequence<int, 32>{});
+      acc[0] += warp_reduce_scatter32_smem(v, T, lane);
+      fill_chunk<1>(v, cx, std::make_integer_sequence<int, 32>{});
+      acc[1] += warp_reduce_scatter32_smem(v, T, lane);
+      fill_chunk<2>(v, cx, std::make_integer_sequence<int, 32>{});
+      acc[2] += warp_reduce_scatter32_smem(v, T, lane);
+      fill_chunk<3>(v, cx, std::make_integer_sequence<int, 32>{});
+      acc[3] += warp_reduce_scatter32_smem(v, T, lane);
+    } else if constexpr (HM == 0) {
       float v[32];
       fill_chunk<0>(v, cx, std::make_integer_sequence<int, 32>{});
       acc[0] += warp_reduce_scatter32(v, lane);
@@ -604,8 +642,8 @@ __global__ void __launch_bounds__(BLOCK) elbo_full_kernel(ProblemDev P) {
       acc[0] += warp_reduce_scatter32(v, lane);
       fill_chunk<1, true>(v, cx, std::make_integer_sequence<int, 32>{});
       acc[1] += warp_reduce_scatter32(v, lane);
-      float (*As)[SYRK_LD] = syrk[warp][0];
-      float (*Bt)[SYRK_LD] = syrk[warp][1];
+      float (*As)[SYRK_LD] = reinterpret_cast<float (*)[SYRK_LD]>(wbuf[warp]);
+      float (*Bt)[SYRK_LD] = reinterpret_cast<float (*)[SYRK_LD]>(wbuf[warp] + NRED * SYRK_LD);
 #pragma unroll
       for (int a = 0; a < NRED; ++a) {
         As[a][lane] = cx.ta[a];
