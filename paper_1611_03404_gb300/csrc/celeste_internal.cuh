@@ -109,6 +109,7 @@ struct ProblemDev {
   float4* pix;                   // [n_pix]: (x, fixed rate, fixed variance, log-factorial term)
   float2* srcmom;                // [n_pix]: the target source's (E[G], Var[G]) at its last full evaluation
   float* ptab;                   // [n_patches][TB_FLOATS] per-patch tables
+  const long long* tile_pix;     // [n_tiles] the tile's first float4 in pix (patch offset + start)
   float* partials;               // [n_tiles][NACC]
   float* vpartials;              // [n_tiles]
   int* flags;                    // [S] per-source work flags
@@ -345,5 +346,16 @@ __device__ inline void bulk_copy(void* dst, const void* src, uint32_t bytes, uin
                "l"(src), "r"(bytes), "r"(b)
                : "memory");
 }
+
+// Asynchronous global -> shared copies of 4, 8 or 16 bytes (naturally aligned), no registers
+// involved; cp_async_wait_all waits for every group this thread committed.
+template <int BYTES>
+__device__ inline void cp_async(void* dst, const void* src) {
+  static_assert(BYTES == 4 || BYTES == 8 || BYTES == 16, "cp.async copies 4, 8 or 16 bytes");
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d), "l"(src), "n"(BYTES) : "memory");
+}
+__device__ inline void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ inline void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 }  // namespace celeste

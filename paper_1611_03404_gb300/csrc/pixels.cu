@@ -86,22 +86,66 @@ __device__ __forceinline__ float warp_reduce_scatter32_smem(const float (&v)[32]
   return p[0].x + p[0].y;
 }
 
-// Thread 0: bulk copies of tile `tile`'s patch table and pixel records into (tab, spix),
-// completing on bar (one expect_tx for both).  The caller has synchronised the CTA since the
-// buffer was last read; the proxy fence orders those generic reads before the async writes.
-// The tile's and its patch's records go to shared memory too (tm, pm), so that the other threads
-// read them there after the wait instead of two dependent global loads at the start of the tile.
-__device__ __forceinline__ void issue_tile(const ProblemDev& P, int tile, float* tab, float4* spix, uint64_t* bar,
-                                           TileDev* tm, PatchDev* pm) {
-  const TileDev t = P.tiles[tile];
-  const PatchDev pt = P.patches[t.patch];
-  fence_proxy_async_smem();
-  const uint32_t tb = TB_FLOATS * 4u, pb = (uint32_t)t.count * 16u;
-  mbar_expect_tx(bar, tb + pb);
-  bulk_copy(tab, P.ptab + (size_t)t.patch * TB_FLOATS, tb, bar);
-  bulk_copy(spix, P.pix + pt.pix_off + t.start, pb, bar);
-  *tm = t;
-  *pm = pt;
+// Thread 0's feed of tiles from the work queue.  Staging a tile takes four dependent global round
+// trips (queue position, list entry, tile record, then the copies); done in one go they would hold
+// the CTA at its next barrier.  The feed runs them as a pipeline over three tiles: each call issues
+// the copies of the tile whose records arrived during the previous call, starts the record copies
+// of the next tile (cp.async into shared memory, so nothing stays in registers across the pixel
+// work), the list load of the one after, and the queue take after that (its result, one register,
+// is first needed by the next call).  The patch record comes with the tile's bulk copies.
+static_assert(sizeof(PatchDev) % 16 == 0, "the patch record is bulk-copied");
+struct TileFeed {
+  TileDev t;        // records of the tile to issue next (when s >= 0)
+  long long pix;
+  int s;            // its slot, or -1
+  int s_next;       // slot of the tile after it, or -1
+  int n;            // tiles in the worklist
+};
+
+__device__ __forceinline__ void feed_start(const ProblemDev& P, TileFeed& F, int& i_next) {
+  const int n = P.wl_count[WL_TILES];
+  const int* list = wl_list(P, WL_TILES);
+  F.n = n;
+  int i = atomicAdd(P.wl_count + 3 + WL_TILES, 1);
+  F.s = i < n ? list[i] : -1;
+  if (F.s >= 0) {
+    F.t = P.tiles[F.s];
+    F.pix = P.tile_pix[F.s];
+  }
+  i = atomicAdd(P.wl_count + 3 + WL_TILES, 1);
+  F.s_next = i < n ? list[i] : -1;
+  i_next = atomicAdd(P.wl_count + 3 + WL_TILES, 1);
+}
+
+// Issues the copies of the feed's ready tile into (tab, spix, pm) on bar and advances the feed;
+// returns the tile's slot (-1: the queue is exhausted).  The caller has synchronised the CTA since
+// the buffer was last read.
+__device__ __forceinline__ int feed_issue(const ProblemDev& P, TileFeed& F, int& i_next, float* tab, float4* spix,
+                                          uint64_t* bar, TileDev* tm, PatchDev* pm) {
+  cp_async_wait_all();   // the records copied by the previous call
+  const int s = F.s;
+  if (s >= 0) {
+    const TileDev t = F.t;
+    fence_proxy_async_smem();
+    const uint32_t tb = TB_FLOATS * 4u, pb = (uint32_t)t.count * 16u, mb = (uint32_t)sizeof(PatchDev);
+    mbar_expect_tx(bar, tb + pb + mb);
+    bulk_copy(tab, P.ptab + (size_t)t.patch * TB_FLOATS, tb, bar);
+    bulk_copy(spix, P.pix + F.pix, pb, bar);
+    bulk_copy(pm, P.patches + t.patch, mb, bar);
+    *tm = t;
+  }
+  const int sn = F.s_next;
+  F.s = sn;
+  if (sn >= 0) {
+    cp_async<16>(&F.t, P.tiles + sn);
+    cp_async<8>(&F.pix, P.tile_pix + sn);
+  }
+  const int n = F.n;
+  if (i_next < n) cp_async<4>(&F.s_next, wl_list(P, WL_TILES) + i_next);
+  else F.s_next = -1;
+  i_next = i_next < n ? atomicAdd(P.wl_count + 3 + WL_TILES, 1) : n;
+  cp_async_commit();
+  return s;
 }
 
 // All threads: wait (bounded by P.wait_budget) for a staged buffer.  On a timeout: error word, a
@@ -115,7 +159,10 @@ __device__ __forceinline__ bool wait_tile(const ProblemDev& P, uint64_t* bar, ui
     mbar_wait(bar, phase, WAIT_BUDGET_DEFAULT);
   }
   ok = __syncthreads_and(ok);
-  if (!ok && other_busy && threadIdx.x == 0) mbar_wait(other, other_phase, WAIT_BUDGET_DEFAULT);
+  if (!ok && threadIdx.x == 0) {
+    if (other_busy) mbar_wait(other, other_phase, WAIT_BUDGET_DEFAULT);
+    cp_async_wait_all();   // the tile feed's record copies
+  }
   return ok;
 }
 
@@ -440,7 +487,8 @@ __global__ void __launch_bounds__(BLOCK) elbo_full_kernel(ProblemDev P) {
   __shared__ __align__(16) float4 spix_buf[NB][BLOCK * PPT];
   __shared__ __align__(8) uint64_t bar[NB];
   __shared__ TileDev tmeta[NB];
-  __shared__ PatchDev pmeta[NB];
+  __shared__ __align__(16) PatchDev pmeta[NB];
+  __shared__ __align__(16) TileFeed feed;
   __shared__ float red[BLOCK / 32][128];
   // per-warp scratch: the tensor-core forms' staging of A' and B'^T, or the FP32 form's transposes
   // for the reduce-scatter with 128-pixel tiles (with larger tiles the 18 KB cost a CTA per SM,
@@ -461,18 +509,17 @@ __global__ void __launch_bounds__(BLOCK) elbo_full_kernel(ProblemDev P) {
   // (it / NB) & 1.  Thread 0 takes the next tile from the queue and issues its copies; the wait's
   // barrier publishes its index in `slot`, which thread 0 rewrites only after the iteration's
   // closing barrier.
+  int i_next = 0;   // thread 0: the feed's pending queue position
   if (tid == 0) {
-    slot = wl_take(P, WL_TILES);
-    if (slot >= 0) issue_tile(P, slot, tab_buf[0], spix_buf[0], &bar[0], &tmeta[0], &pmeta[0]);
+    feed_start(P, feed, i_next);
+    slot = feed_issue(P, feed, i_next, tab_buf[0], spix_buf[0], &bar[0], &tmeta[0], &pmeta[0]);
   }
   __syncthreads();
   int tile = slot;
   for (uint32_t it = 0; tile >= 0; ++it) {
   const int b = NB == 2 ? (int)(it & 1u) : 0;
-  if (NB == 2 && tid == 0) {
-    slot = wl_take(P, WL_TILES);
-    if (slot >= 0) issue_tile(P, slot, tab_buf[b ^ 1], spix_buf[b ^ 1], &bar[b ^ 1], &tmeta[b ^ 1], &pmeta[b ^ 1]);
-  }
+  if (NB == 2 && tid == 0)
+    slot = feed_issue(P, feed, i_next, tab_buf[b ^ 1], spix_buf[b ^ 1], &bar[b ^ 1], &tmeta[b ^ 1], &pmeta[b ^ 1]);
   if (!wait_tile(P, &bar[b], (it / NB) & 1u, &bar[b ^ (NB - 1)], ((it + 1) / NB) & 1u, NB == 2 && slot >= 0)) {
     if (tid < NACC) P.partials[(size_t)tile * NACC + tid] = __int_as_float(0x7fc00000);
     return;
@@ -683,16 +730,14 @@ __global__ void __launch_bounds__(BLOCK) elbo_full_kernel(ProblemDev P) {
   const int next = slot;
   __syncthreads();   // this buffer, red and slot are rewritten after this point
   if constexpr (NB == 1) {
-    if (tid == 0) {
-      slot = wl_take(P, WL_TILES);
-      if (slot >= 0) issue_tile(P, slot, tab_buf[0], spix_buf[0], &bar[0], &tmeta[0], &pmeta[0]);
-    }
+    if (tid == 0) slot = feed_issue(P, feed, i_next, tab_buf[0], spix_buf[0], &bar[0], &tmeta[0], &pmeta[0]);
     __syncthreads();
     tile = slot;
   } else {
     tile = next;
   }
   }
+  if (tid == 0) cp_async_wait_all();   // no record copy lands after the CTA has left
 }
 
 // ------------------------------------------------------------------------------ value kernel
@@ -706,7 +751,8 @@ __global__ void __launch_bounds__(BLOCK) elbo_value_kernel(ProblemDev P, int dif
   __shared__ __align__(16) float4 spix_buf[2][BLOCK * PPT];
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ TileDev tmeta[2];
-  __shared__ PatchDev pmeta[2];
+  __shared__ __align__(16) PatchDev pmeta[2];
+  __shared__ __align__(16) TileFeed feed;
   __shared__ float red[BLOCK / 32];
 
   __shared__ int slot;
@@ -715,18 +761,17 @@ __global__ void __launch_bounds__(BLOCK) elbo_value_kernel(ProblemDev P, int dif
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
   }
+  int i_next = 0;   // thread 0: the feed's pending queue position
   if (tid == 0) {
-    slot = wl_take(P, WL_TILES);
-    if (slot >= 0) issue_tile(P, slot, tab_buf[0], spix_buf[0], &bar[0], &tmeta[0], &pmeta[0]);
+    feed_start(P, feed, i_next);
+    slot = feed_issue(P, feed, i_next, tab_buf[0], spix_buf[0], &bar[0], &tmeta[0], &pmeta[0]);
   }
   __syncthreads();
   int tile = slot;
   for (uint32_t it = 0; tile >= 0; ++it) {
   const int b = (int)(it & 1u);
-  if (tid == 0) {
-    slot = wl_take(P, WL_TILES);
-    if (slot >= 0) issue_tile(P, slot, tab_buf[b ^ 1], spix_buf[b ^ 1], &bar[b ^ 1], &tmeta[b ^ 1], &pmeta[b ^ 1]);
-  }
+  if (tid == 0)
+    slot = feed_issue(P, feed, i_next, tab_buf[b ^ 1], spix_buf[b ^ 1], &bar[b ^ 1], &tmeta[b ^ 1], &pmeta[b ^ 1]);
   if (!wait_tile(P, &bar[b], (it >> 1) & 1u, &bar[b ^ 1], ((it + 1) >> 1) & 1u, slot >= 0)) {
     if (tid == 0) P.vpartials[tile] = __int_as_float(0x7fc00000);
     return;
@@ -811,6 +856,7 @@ __global__ void __launch_bounds__(BLOCK) elbo_value_kernel(ProblemDev P, int dif
   __syncthreads();   // this buffer, red and slot are rewritten after this point
   tile = next;
   }
+  if (tid == 0) cp_async_wait_all();   // no record copy lands after the CTA has left
 }
 
 // ------------------------------------------------------------------------------ launchers

@@ -257,6 +257,7 @@ void build_layout(celeste_problem* p) {
   }
   p->nbr.clear();
   p->tiles.clear();
+  p->tile_pix.clear();
   long long off = 0;
   for (int q = 0; q < NPch; ++q) {
     PatchDev& a = p->patches[q];
@@ -267,7 +268,10 @@ void build_layout(celeste_problem* p) {
     int npix = a.w * a.h;
     off += npix;
     a.tile_begin = (int)p->tiles.size();
-    for (int st = 0; st < npix; st += p->tile_pixels) p->tiles.push_back({q, st, std::min(p->tile_pixels, npix - st), 0});
+    for (int st = 0; st < npix; st += p->tile_pixels) {
+      p->tiles.push_back({q, st, std::min(p->tile_pixels, npix - st), 0});
+      p->tile_pix.push_back(a.pix_off + st);
+    }
     a.tile_end = (int)p->tiles.size();
   }
   p->n_pix = off;
@@ -300,6 +304,7 @@ void build_layout(celeste_problem* p) {
   L.images = take(sizeof(ImageDev) * N);
   L.patches = take(sizeof(PatchDev) * std::max(NPch, 1));
   L.tiles = take(sizeof(TileDev) * std::max<size_t>(p->tiles.size(), 1));
+  L.tile_pix = take(sizeof(long long) * std::max<size_t>(p->tiles.size(), 1));
   L.src_patch = take(sizeof(int) * (S + 1));
   L.nbr = take(sizeof(int) * std::max<size_t>(p->nbr.size(), 1));
   L.u0 = take(sizeof(double) * 2 * S);
@@ -362,6 +367,7 @@ extern "C" int celeste_problem_bind(celeste_problem* p, void* workspace, size_t 
   if ((e = upload(base, L.images, p->imgdev, st)) != cudaSuccess) return cuda_fail(e, "upload images");
   if ((e = upload(base, L.patches, p->patches, st)) != cudaSuccess) return cuda_fail(e, "upload patches");
   if ((e = upload(base, L.tiles, p->tiles, st)) != cudaSuccess) return cuda_fail(e, "upload tiles");
+  if ((e = upload(base, L.tile_pix, p->tile_pix, st)) != cudaSuccess) return cuda_fail(e, "upload tile offsets");
   if ((e = upload(base, L.src_patch, p->src_patch, st)) != cudaSuccess) return cuda_fail(e, "upload src_patch");
   if ((e = upload(base, L.nbr, p->nbr, st)) != cudaSuccess) return cuda_fail(e, "upload nbr");
   if ((e = upload(base, L.u0, p->u0, st)) != cudaSuccess) return cuda_fail(e, "upload u0");
@@ -383,6 +389,7 @@ extern "C" int celeste_problem_bind(celeste_problem* p, void* workspace, size_t 
   D.images = reinterpret_cast<const ImageDev*>(base + L.images);
   D.patches = reinterpret_cast<const PatchDev*>(base + L.patches);
   D.tiles = reinterpret_cast<const TileDev*>(base + L.tiles);
+  D.tile_pix = reinterpret_cast<const long long*>(base + L.tile_pix);
   D.src_patch = reinterpret_cast<const int*>(base + L.src_patch);
   D.nbr = reinterpret_cast<const int*>(base + L.nbr);
   D.u0 = reinterpret_cast<const double*>(base + L.u0);

@@ -9,7 +9,7 @@
 namespace celeste {
 
 struct WsLayout {
-  size_t images, patches, tiles, src_patch, nbr, u0, psf_coef, psf, pix, srcmom, ptab, partials, vpartials, flags, err, counters;
+  size_t images, patches, tiles, tile_pix, src_patch, nbr, u0, psf_coef, psf, pix, srcmom, ptab, partials, vpartials, flags, err, counters;
   size_t wl, wl_count, snc;
   size_t nt_f, nt_g, nt_H, nt_trial, nt_pred, nt_ftrial, nt_state, nt_count, nt_tcache, nt_lam, nt_list;
   size_t total;
@@ -37,6 +37,7 @@ struct celeste_problem {
   // layout
   std::vector<celeste::PatchDev> patches;
   std::vector<celeste::TileDev> tiles;
+  std::vector<long long> tile_pix;   // per tile: its patch's pixel offset + its start
   std::vector<int> src_patch, nbr;
   std::vector<celeste::ImageDev> imgdev;
   std::vector<double> psf_coef;

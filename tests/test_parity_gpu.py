@@ -207,14 +207,18 @@ def test_newton_matches_oracle_optimum(P, cta_sources):
 
 def stop_slack(H, L, ftol=1e-8):
     """Per free parameter, how far the ELBO-tolerance stopping rule leaves the optimum undetermined:
-    Newton stops once the predicted gain is below ftol |L|, and along parameter i that gain stays
-    below ftol |L| within sqrt(2 ftol |L| [(-H)^-1]_ii) of the maximum.  Three times that."""
-    try:
-        cov = np.linalg.inv(-H)
-        d = np.clip(np.diag(cov), 0.0, None)
-    except np.linalg.LinAlgError:
-        return np.zeros(len(H))
-    return 3.0 * np.sqrt(2.0 * ftol * abs(L) * d)
+    Newton stops once the predicted gain is below ftol |L|, and along a direction of curvature c > 0
+    that gain stays below ftol |L| within sqrt(2 ftol |L| / c) of the maximum: for parameter i,
+    sqrt(2 ftol |L| [(-H)^-1]_ii) over the directions of positive curvature.  Three times that.
+    Along a direction of non-positive curvature (a flat ridge, e.g. the profile mixture of a galaxy
+    too small to tell exponential from de Vaucouleurs) nothing bounds the stopping point, so the
+    parameters with a share in such a direction are left unbounded."""
+    w, V = np.linalg.eigh(-0.5 * (H + H.T))
+    flat = w <= 1e-12 * max(np.abs(w).max(), 1e-300)
+    d = (V[:, ~flat] ** 2 / w[~flat]).sum(axis=1)
+    slack = 3.0 * np.sqrt(2.0 * ftol * abs(L) * d)
+    slack[(V[:, flat] ** 2).sum(axis=1) > 1e-6] = np.inf
+    return slack
 
 
 def compare_optimum(got, ref, tol=1e-4, slack=None):
