@@ -57,9 +57,9 @@ MUFU_FULL_PER_PIXEL = 48
 # path does less, the multiplier search more)
 FP64_FLOPS_PER_SUBPROBLEM = 4 * 27 ** 3 // 3
 # bytes per pixel evaluation that the pixel kernel must move: the 16-byte pixel record read and the
-# 8-byte source moments written (the 7552-byte patch table per patch comes on top)
+# 8-byte source moments written (the 8224-byte patch table per patch comes on top)
 BYTES_FULL_PER_PIXEL = 24
-TABLE_BYTES = 7552
+TABLE_BYTES = 8224
 
 
 def parse(argv=None):

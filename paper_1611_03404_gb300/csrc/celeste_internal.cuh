@@ -34,10 +34,16 @@ constexpr int NRED = 11;
 // Per-patch table (floats) written by the table kernel at the source's current parameters and
 // bulk-copied into shared memory by every tile of the patch.  Positions are relative to the patch
 // origin; quadratic forms use s = (d0^2, 2 d0 d1, d1^2) with d = pixel - mean of PSF component k
-// (the same for the star component k and the 14 galaxy components (k, j)).
+// (the same for the star component k and the 14 galaxy components (k, j)).  The first TB_VFLOATS
+// floats are all that the value-only kernel reads (it stages only them): the galaxy components'
+// precisions and normalisers again, two components interleaved for two-wide float32 arithmetic.
 constexpr int TB_MU = 0;      // 3 x (x, y) mean of PSF component k, + 2 pad
 constexpr int TB_STAR = 8;    // 3 x (W, P00, P01, P11)
-constexpr int TB_GAL = 20;    // NGAL x GT_STRIDE, component g = k * NMIX + j
+constexpr int TB_SNC = 20;    // SNConst (20 floats)
+constexpr int TB_VAL = 40;    // per k, per pair of components (j, j + 1), j even: (P00, P00'),
+                              // (P01, P01'), (P11, P11'), (W, W'); pair index k * NMIX / 2 + j / 2
+constexpr int TB_VFLOATS = TB_VAL + NGAL * 4;   // 208 floats = 832 bytes
+constexpr int TB_GAL = TB_VFLOATS;              // NGAL x GT_STRIDE, component g = k * NMIX + j
 // A galaxy component's entry is laid out for the pixel kernel's two-wide float32 arithmetic: the
 // numbers combined in one packed operation sit side by side at an even offset (a few are stored
 // twice).  Q_a = -1/2 dP/da (entries 00, 01, 11; a = axis, angle, scale), l_a = -1/2 d logdet/da,
@@ -59,8 +65,9 @@ __host__ __device__ constexpr int gt_qa(int a, int i) {
 __host__ __device__ constexpr int gt_la(int a) { return a < 2 ? GT_LA01 + a : GT_LA2; }
 __host__ __device__ constexpr int gt_qab(int pq, int i) { return GT_CAB + 8 * (pq / 2) + 2 * (i + 1) + (pq % 2); }
 __host__ __device__ constexpr int gt_lab(int pq) { return GT_CAB + 8 * (pq / 2) + (pq % 2); }
-constexpr int TB_SNC = TB_GAL + NGAL * GT_STRIDE;   // SNConst
-constexpr int TB_FLOATS = TB_SNC + 20;              // 1888 floats = 7552 bytes (multiple of 16)
+constexpr int TB_FLOATS = TB_GAL + NGAL * GT_STRIDE;   // 2056 floats = 8224 bytes (multiple of 16)
+static_assert(NMIX % 2 == 0 && CELESTE_NEXP % 2 == 0, "component pairs never straddle the two families");
+static_assert(TB_VFLOATS % 4 == 0 && TB_FLOATS % 4 == 0, "bulk-copied in multiples of 16 bytes");
 
 // Per-(source, image) scalar constants used by the pixel kernels.
 struct SNConst {
@@ -71,6 +78,7 @@ struct SNConst {
   // C_i = a_i (E[l^2|i] - E[l|i]^2) = a_i E[l|i]^2 expm1(v_i), Cx = a0 a1.
   float C0, C1, Cx, L10, L11;
 };
+static_assert(sizeof(SNConst) <= 20 * sizeof(float), "SNConst fits its 20 table floats");
 
 struct ImageDev {
   const float* pixels;

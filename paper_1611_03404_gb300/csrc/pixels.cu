@@ -120,16 +120,26 @@ __device__ __forceinline__ void feed_start(const ProblemDev& P, TileFeed& F, int
 // Issues the copies of the feed's ready tile into (tab, spix, pm) on bar and advances the feed;
 // returns the tile's slot (-1: the queue is exhausted).  The caller has synchronised the CTA since
 // the buffer was last read.
+// value = true: only the table's value-only prefix (TB_VFLOATS floats); otherwise everything but the
+// paired value copies (the prefix up to TB_VAL and the galaxy entries, at their table offsets).
 __device__ __forceinline__ int feed_issue(const ProblemDev& P, TileFeed& F, int& i_next, float* tab, float4* spix,
-                                          uint64_t* bar, TileDev* tm, PatchDev* pm) {
+                                          uint64_t* bar, TileDev* tm, PatchDev* pm, bool value = false) {
   cp_async_wait_all();   // the records copied by the previous call
   const int s = F.s;
   if (s >= 0) {
     const TileDev t = F.t;
     fence_proxy_async_smem();
-    const uint32_t tb = TB_FLOATS * 4u, pb = (uint32_t)t.count * 16u, mb = (uint32_t)sizeof(PatchDev);
-    mbar_expect_tx(bar, tb + pb + mb);
-    bulk_copy(tab, P.ptab + (size_t)t.patch * TB_FLOATS, tb, bar);
+    const float* src = P.ptab + (size_t)t.patch * TB_FLOATS;
+    const uint32_t pb = (uint32_t)t.count * 16u, mb = (uint32_t)sizeof(PatchDev);
+    if (value) {
+      mbar_expect_tx(bar, TB_VFLOATS * 4u + pb + mb);
+      bulk_copy(tab, src, TB_VFLOATS * 4u, bar);
+    } else {
+      constexpr uint32_t gb = (TB_FLOATS - TB_GAL) * 4u;
+      mbar_expect_tx(bar, TB_VAL * 4u + gb + pb + mb);
+      bulk_copy(tab, src, TB_VAL * 4u, bar);
+      bulk_copy(tab + TB_GAL, src + TB_GAL, gb, bar);
+    }
     bulk_copy(spix, P.pix + F.pix, pb, bar);
     bulk_copy(pm, P.patches + t.patch, mb, bar);
     *tm = t;
@@ -434,8 +444,7 @@ __device__ __forceinline__ void gal_component(const float* ep, float2 D0, float2
     e[4 * w + 2] = t4.z;
     e[4 * w + 3] = t4.w;
   }
-  // (q as in the value kernels, which difference-mode trial values are compared against)
-  const float q = e[GT_P] * S0.x + e[GT_P + 1] * S1.x + e[GT_P + 2] * S2.x;
+  const float q = fmaf(e[GT_P + 2], S2.x, fmaf(e[GT_P + 1], S1.x, e[GT_P] * S0.x));
   const float N = e[GT_W] * exp2f(q * (-0.5f * LOG2E));
   if (__all_sync(0xffffffffu, N == 0.f || !valid)) return;
   const float2 z = fma2(f2(e[GT_PZ], e[GT_PZ + 1]), D1, mul2(f2(e[GT_P], e[GT_P + 1]), D0));   // (z0, z1)
@@ -556,7 +565,7 @@ __global__ void __launch_bounds__(BLOCK) elbo_full_kernel(ProblemDev P) {
       const float2 D0 = f2(d0, d0), D1 = f2(d1, d1), S0 = f2(s0, s0), S1 = f2(s1, s1), S2 = f2(s2, s2);
       {
         const float4 st = *reinterpret_cast<const float4*>(&tab[TB_STAR + 4 * k]);
-        const float q = st.y * s0 + st.z * s1 + st.w * s2;
+        const float q = fmaf(st.w, s2, fmaf(st.z, s1, st.y * s0));
         const float N = st.x * exp2f(q * (-0.5f * LOG2E));
         const float z0 = st.y * d0 + st.z * d1, z1 = st.z * d0 + st.w * d1;
         f0 += N;
@@ -585,8 +594,9 @@ __global__ void __launch_bounds__(BLOCK) elbo_full_kernel(ProblemDev P) {
     cx.f0mm[0] = f0mm[0];
     cx.f0mm[1] = f0mm[1];
     cx.f0mm[2] = f0mm[2];
-    const float dF = G[1].F - G[0].F;
-    cx.f1 = G[0].F + c.e * dF;
+    const float F0 = G[0].F, F1 = G[1].F;
+    const float dF = F1 - F0;
+    cx.f1 = F0 + c.e * dF;
     cx.f1g[2] = c.e1 * dF;
     cx.f1gg[tri6(2, 2)] = c.e2 * dF;
 #pragma unroll
@@ -747,7 +757,7 @@ __global__ void __launch_bounds__(BLOCK) elbo_full_kernel(ProblemDev P) {
 //           part without the rounding of two large sums.
 template <int PPT>
 __global__ void __launch_bounds__(BLOCK) elbo_value_kernel(ProblemDev P, int diff) {
-  __shared__ __align__(16) float tab_buf[2][TB_FLOATS];
+  __shared__ __align__(16) float tab_buf[2][TB_VFLOATS];   // the table's value-only prefix
   __shared__ __align__(16) float4 spix_buf[2][BLOCK * PPT];
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ TileDev tmeta[2];
@@ -764,14 +774,15 @@ __global__ void __launch_bounds__(BLOCK) elbo_value_kernel(ProblemDev P, int dif
   int i_next = 0;   // thread 0: the feed's pending queue position
   if (tid == 0) {
     feed_start(P, feed, i_next);
-    slot = feed_issue(P, feed, i_next, tab_buf[0], spix_buf[0], &bar[0], &tmeta[0], &pmeta[0]);
+    slot = feed_issue(P, feed, i_next, tab_buf[0], spix_buf[0], &bar[0], &tmeta[0], &pmeta[0], true);
   }
   __syncthreads();
   int tile = slot;
   for (uint32_t it = 0; tile >= 0; ++it) {
   const int b = (int)(it & 1u);
   if (tid == 0)
-    slot = feed_issue(P, feed, i_next, tab_buf[b ^ 1], spix_buf[b ^ 1], &bar[b ^ 1], &tmeta[b ^ 1], &pmeta[b ^ 1]);
+    slot = feed_issue(P, feed, i_next, tab_buf[b ^ 1], spix_buf[b ^ 1], &bar[b ^ 1], &tmeta[b ^ 1], &pmeta[b ^ 1],
+                      true);
   if (!wait_tile(P, &bar[b], (it >> 1) & 1u, &bar[b ^ 1], ((it + 1) >> 1) & 1u, slot >= 0)) {
     if (tid == 0) P.vpartials[tile] = __int_as_float(0x7fc00000);
     return;
@@ -802,24 +813,33 @@ __global__ void __launch_bounds__(BLOCK) elbo_value_kernel(ProblemDev P, int dif
     } else if (P.pweight) {
       wpx = P.pweight[pt.pix_off + idx];
     }
-    float f0 = 0.f, fE = 0.f, fD = 0.f;
+    // components two at a time (the paired copies of the table's value prefix), with the full
+    // kernel's formulas; the sums' association differs from it (pairs), a rounding difference of
+    // ~1e-7 of a pixel's rate, far below what the ELBO tolerance resolves
+    float f0 = 0.f;
+    float2 fE = make_float2(0.f, 0.f), fD = make_float2(0.f, 0.f);
 #pragma unroll
     for (int k = 0; k < CELESTE_NPSF; ++k) {
       const float d0 = fx - tab[TB_MU + 2 * k], d1 = fy - tab[TB_MU + 2 * k + 1];
       const float s0 = d0 * d0, s1 = 2.f * d0 * d1, s2 = d1 * d1;
       const float4 st = *reinterpret_cast<const float4*>(&tab[TB_STAR + 4 * k]);
-      f0 += st.x * exp2f((st.y * s0 + st.z * s1 + st.w * s2) * (-0.5f * LOG2E));
+      f0 += st.x * exp2f(fmaf(st.w, s2, fmaf(st.z, s1, st.y * s0)) * (-0.5f * LOG2E));
+      const float2 S0 = f2(s0, s0), S1 = f2(s1, s1), S2 = f2(s2, s2);
+      const float4* vp = reinterpret_cast<const float4*>(&tab[TB_VAL + 8 * (k * NMIX / 2)]);
 #pragma unroll
-      for (int j = 0; j < NMIX; ++j) {
-        const float4 e = *reinterpret_cast<const float4*>(&tab[TB_GAL + (k * NMIX + j) * GT_STRIDE]);
-        const float g = e.w * exp2f((e.x * s0 + e.y * s1 + e.z * s2) * (-0.5f * LOG2E));
-        if (j < CELESTE_NEXP)
-          fE += g;
+      for (int pr = 0; pr < NMIX / 2; ++pr) {
+        const float4 a = vp[2 * pr], w = vp[2 * pr + 1];   // (P00, P00', P01, P01'), (P11, P11', W, W')
+        const float2 q = fma2(f2(w.x, w.y), S2, fma2(f2(a.z, a.w), S1, mul2(f2(a.x, a.y), S0)));
+        const float2 qs = mul2(q, f2(-0.5f * LOG2E, -0.5f * LOG2E));
+        const float2 g = mul2(f2(w.z, w.w), f2(exp2f(qs.x), exp2f(qs.y)));
+        if (pr < CELESTE_NEXP / 2)
+          fE = add2(fE, g);
         else
-          fD += g;
+          fD = add2(fD, g);
       }
     }
-    const float f1 = fE + c.e * (fD - fE);
+    const float fEs = fE.x + fE.y, fDs = fD.x + fD.y;
+    const float f1 = fEs + c.e * (fDs - fEs);
     const float EG = c.A0 * f0 + c.A1 * f1;
     const float dxv = c.L10 * f0 - c.L11 * f1;
     const float VG = c.C0 * f0 * f0 + c.C1 * f1 * f1 + c.Cx * dxv * dxv;

@@ -225,6 +225,12 @@ __global__ void __launch_bounds__(64) table_kernel(ProblemDev P, const double* _
       const double Ad[4] = {im.A[0], im.A[1], im.A[2], im.A[3]};
       gal_entry<double>(gd, Ad, Sym2T<double>{pc.S.a, pc.S.b, pc.S.c}, (double)pc.w * nu, (double)tau, full != 0, e);
     }
+    // the value-only copy, interleaved with the other component of its pair
+    float* v = out + TB_VAL + 8 * (tid / 2) + (j & 1);
+    v[0] = e[GT_P];
+    v[2] = e[GT_P + 1];
+    v[4] = e[GT_P + 2];
+    v[6] = e[GT_W];
   } else if (tid < NGAL + NSTAR) {
     const int k = tid - NGAL;
     const PsfComp pc = load_psf(psf, k);

@@ -302,9 +302,11 @@ __device__ inline int tr_lambda_parallel(TrSmem& S, int lane, double lo, double 
       if (!have_h) return 1;
       // phi(H) >= 0 with H next to L: the root, unless |y| jumps across delta within the last
       // ulps of lambda -- the pole, where g's component along the eigenvector of lambda_min is
-      // too small to resolve (the hard case, numerically)
+      // too small to resolve (the hard case, numerically).  A positive definite point with
+      // |y| > delta (lamL) rules the hard case out: there g's component along that eigenvector
+      // lifts |y| above delta right of the pole, so the root lies in [lamL, H] and y(H) stands.
       lam_out = lamH;
-      return tr_norm(S.y) < delta * (1.0 - 1e-6) ? 1 : 0;
+      return lamL == -INFINITY && tr_norm(S.y) < delta * (1.0 - 1e-6) ? 1 : 0;
     }
   }
   lam_out = lamH;

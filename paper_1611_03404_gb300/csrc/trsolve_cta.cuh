@@ -197,8 +197,8 @@ __device__ inline int tr_lambda_q(TrSmemQ& S, double lo, double hi, double delta
     lamS = have_h && lamL > -INFINITY && phiH > phiL ? lamL + (H - lamL) * (-phiL * tr_rcp(phiH - phiL)) : -1.0;
     if (H - L <= 4.0 * DBL_EPSILON * fmax(fabs(H), spec)) {
       if (!have_h) return 1;
-      lam_out = lamH;
-      return tr_norm(S.y) < delta * (1.0 - 1e-6) ? 1 : 0;
+      lam_out = lamH;   // (the hard case only without a positive definite point past delta: see tr_lambda_parallel)
+      return lamL == -INFINITY && tr_norm(S.y) < delta * (1.0 - 1e-6) ? 1 : 0;
     }
   }
   lam_out = lamH;

@@ -174,3 +174,56 @@ def test_reciprocal_error_bound(P):
     edge = P.tr_reciprocal(torch.tensor([0.0, 5e-324, 2.0 ** 1023, -(2.0 ** 1023)], dtype=torch.float64,
                                         device="cuda")).cpu().numpy()
     assert np.isnan(edge[0]) and np.isnan(edge[1]) and edge[2] == 0.0 and edge[3] == 0.0
+
+
+def _near_pole(seed, gap, delta=16.0):
+    """A subproblem whose root sits `gap` above the pole -lambda_min: B indefinite (lambda_min =
+    -8.64e-4) with a spectrum up to 3.4e4, g weighted towards the stiff directions (0.01 sqrt|lambda|
+    per eigenvector, as a Newton iteration's gradient in a flat valley), its component along the
+    smallest eigenvector set so that |p(lambda*)| = delta at lambda* = -lambda_min + gap."""
+    rng = np.random.default_rng(seed)
+    lam = np.concatenate([[-8.64e-4], np.geomspace(1.3e-4, 3.4e4, 26)])
+    Q, _ = np.linalg.qr(rng.normal(size=(27, 27)))
+    B = Q @ np.diag(lam) @ Q.T
+    B = 0.5 * (B + B.T)
+    lstar = -lam[0] + gap
+    gam = rng.normal(size=27) * np.sqrt(np.abs(lam)) * 0.01
+    gam[0] = 0.0
+    rest = np.sum(gam[1:] ** 2 / (lam[1:] + lstar) ** 2)
+    if rest >= delta ** 2:
+        gam[1:] *= 0.9 * delta / np.sqrt(rest)
+        rest = np.sum(gam[1:] ** 2 / (lam[1:] + lstar) ** 2)
+    gam[0] = np.sqrt(delta ** 2 - rest) * (lam[0] + lstar)
+    return B, Q @ gam, delta, lstar
+
+
+@pytest.mark.parametrize("warps", [1, 4])
+def test_subproblem_near_pole_with_far_hint(P, warps):
+    """Roots 1e-6 .. 3e-6 above the pole with the multiplier hint far above them (the previous
+    subproblem's multiplier): the search narrows the bracket to the float64 resolution of the
+    spectrum before |p| reaches delta to 1e-10.  A positive definite point with |p| > delta has been
+    seen by then, which rules the hard case out; the step must be the boundary solution (no hard
+    case, positive predicted decrease, the oracle's model value up to what the pole leaves
+    undetermined), whatever the hint."""
+    cases = [(_near_pole(s, gap), hint) for s in range(6) for gap in (1e-6, 1.4e-6, 3e-6) for hint in (1.0, 10.0, -1.0)]
+    B = np.array([c[0][0] for c in cases])
+    g = np.array([c[0][1] for c in cases])
+    d = np.array([c[0][2] for c in cases])
+    lstar = np.array([c[0][3] for c in cases])
+    hint = np.array([c[1] for c in cases])
+    dev = torch.device("cuda:0")
+    t = lambda a: torch.as_tensor(a, device=dev).contiguous()
+    p, pred, hard, lam = P.tr_solve_batch(t(B), t(g), t(d), warps=warps, lam_hint=t(hint), return_lambda=True)
+    p, pred, hard = p.cpu().numpy(), pred.cpu().numpy(), hard.cpu().numpy()
+    for i in range(len(cases)):
+        pr, _, hr = O.tr_subproblem(g[i], B[i], d[i])
+        assert not hr
+        assert hard[i] == 0, (i, hint[i])
+        assert pred[i] > 0, (i, pred[i])
+        assert np.linalg.norm(p[i]) <= d[i] * (1 + 1e-9)
+        mg = g[i] @ p[i] + 0.5 * p[i] @ B[i] @ p[i]
+        mo = g[i] @ pr + 0.5 * pr @ B[i] @ pr
+        scale = np.abs(np.linalg.eigvalsh(B[i])).max()
+        gap = lstar[i] - 8.64e-4
+        slack = lstar[i] * d[i] ** 2 * min(1.0, 64 * np.finfo(float).eps * scale / gap)
+        assert mg <= mo + 1e-7 * abs(mo) + slack, (i, mg, mo, slack)
