@@ -382,9 +382,9 @@ int celeste_measure_peak(int kind, double* ops_per_s, double* seconds, celeste_s
  * The paper has no counterpart; it is a deployment variant of the evaluation above.
  *   p must be bound and have its background rendered; theta, elbo, grad, hess as in
  *   celeste_elbo_batch (all four required).
- *   Limit: 432 * n_tiles, 4 * n_sources, 6880 * n_patches, 8 * n_pixels,
+ *   Limit: 432 * n_tiles, 4 * n_sources, 8224 * n_patches, 8 * n_pixels,
  *   4 * (n_tiles + n_patches + n_sources) and 340 * n_sources bytes, each rounded up to 256, plus
- *   256 must fit in 8 MiB (e.g. ~1000 patches of 17 x 17 pixels); larger problems get
+ *   256 must fit in 8 MiB (e.g. ~700 patches of 17 x 17 pixels); larger problems get
  *   CELESTE_ERR_INVALID_ARG before any launch.
  *   The error words and the profiling counters stay in the bound workspace: the call clears the
  *   timeout word first, a timed-out bulk-copy wait sets it there (celeste_problem_check reports

@@ -88,7 +88,7 @@ def test_noalloc_rejects_problems_beyond_the_fixed_array(pkg):
     sc = synth.tiny(seed=2, n_sources=200, n_images=1, H=400, W=400, radius=(64, 64), noise=False)
     hp = P.HostProblem(sc, tile_pixels=128)
     c = hp.counts()
-    need = (c["tiles"] * 436 + c["patches"] * 6884 + c["pixels"] * 8 + c["sources"] * 348)
+    need = (c["tiles"] * 436 + c["patches"] * 8228 + c["pixels"] * 8 + c["sources"] * 348)
     assert need > (8 << 20)
     z = ctypes.c_void_p(8)
     rc = P.lib().celeste_elbo_batch_noalloc(hp.handle, z, z, z, z, None)
