@@ -758,11 +758,12 @@ def joint_report(P, prob, theta0):
 
 
 def _build_hash():
+    """The pixel kernels' source: the kernel file and the header with the table layout."""
     import hashlib
     h = hashlib.sha256()
-    src = os.path.join(ROOT, "paper_1611_03404_gb300", "csrc", "pixels.cu")
-    with open(src, "rb") as f:
-        h.update(f.read())
+    for name in ("pixels.cu", "celeste_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_1611_03404_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
     return h.hexdigest()[:16]
 
 
