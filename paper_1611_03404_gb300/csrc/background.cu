@@ -16,7 +16,8 @@ namespace celeste {
 constexpr int NB_CHUNK = 8;   // neighbours staged per pass
 
 struct NbrStage {
-  float4 gal[NGAL];            // (P00, P01, P11) * (-1/2 log2 e), weighted normaliser
+  float4 gal[NGAL];            // per pair of components (the table's value prefix): (P00, P00', P01,
+                               // P01') * (-1/2 log2 e), then (P11, P11') * (-1/2 log2 e), (W, W')
   float4 star[NSTAR];
   float mu[2 * CELESTE_NPSF];  // component means relative to the target patch's origin
   float c[8];                  // A0 A1 C0 C1 Cx L10 L11 e
@@ -50,8 +51,9 @@ __global__ void __launch_bounds__(BLOCK) background_kernel(ProblemDev P, int cli
       const float* tb = P.ptab + (size_t)np * TB_FLOATS;
       NbrStage& S = nbs[q];
       if (e < NGAL) {
-        const float4 g = *reinterpret_cast<const float4*>(tb + TB_GAL + e * GT_STRIDE);
-        S.gal[e] = make_float4(g.x * NL2, g.y * NL2, g.z * NL2, g.w);
+        const float4 g = *reinterpret_cast<const float4*>(tb + TB_VAL + 4 * e);
+        S.gal[e] = (e & 1) ? make_float4(g.x * NL2, g.y * NL2, g.z, g.w)
+                           : make_float4(g.x * NL2, g.y * NL2, g.z * NL2, g.w * NL2);
       } else if (e < NGAL + NSTAR) {
         const float4 g = *reinterpret_cast<const float4*>(tb + TB_STAR + 4 * (e - NGAL));
         S.star[e - NGAL] = make_float4(g.x, g.y * NL2, g.z * NL2, g.w * NL2);
@@ -90,24 +92,30 @@ __global__ void __launch_bounds__(BLOCK) background_kernel(ProblemDev P, int cli
         const NbrStage& S = nbs[q];
         if (clip && (col < S.win[0] || col >= S.win[2] || row < S.win[1] || row >= S.win[3])) continue;
         cover[r] += 1;
-        float f0 = 0.f, fE = 0.f, fD = 0.f;
+        // galaxy components two at a time, on packed two-wide float32 arithmetic
+        float f0 = 0.f;
+        float2 fE = make_float2(0.f, 0.f), fD = make_float2(0.f, 0.f);
 #pragma unroll
         for (int k = 0; k < CELESTE_NPSF; ++k) {
           const float d0 = fx - S.mu[2 * k], d1 = fy - S.mu[2 * k + 1];
           const float s0 = d0 * d0, s1 = 2.f * d0 * d1, s2 = d1 * d1;
           const float4 st = S.star[k];
           f0 += st.x * exp2f(st.y * s0 + st.z * s1 + st.w * s2);
+          const float2 S0 = make_float2(s0, s0), S1 = make_float2(s1, s1), S2 = make_float2(s2, s2);
 #pragma unroll
-          for (int j = 0; j < NMIX; ++j) {
-            const float4 g = S.gal[k * NMIX + j];
-            const float v = g.w * exp2f(g.x * s0 + g.y * s1 + g.z * s2);
-            if (j < CELESTE_NEXP)
-              fE += v;
+          for (int pr = 0; pr < NMIX / 2; ++pr) {
+            const float4 a = S.gal[2 * (k * NMIX / 2 + pr)], b = S.gal[2 * (k * NMIX / 2 + pr) + 1];
+            const float2 q = __ffma2_rn(make_float2(b.x, b.y), S2,
+                                        __ffma2_rn(make_float2(a.z, a.w), S1, __fmul2_rn(make_float2(a.x, a.y), S0)));
+            const float2 v = __fmul2_rn(make_float2(b.z, b.w), make_float2(exp2f(q.x), exp2f(q.y)));
+            if (pr < CELESTE_NEXP / 2)
+              fE = __fadd2_rn(fE, v);
             else
-              fD += v;
+              fD = __fadd2_rn(fD, v);
           }
         }
-        const float f1 = fE + S.c[7] * (fD - fE);
+        const float fEs = fE.x + fE.y, fDs = fD.x + fD.y;
+        const float f1 = fEs + S.c[7] * (fDs - fEs);
         bE[r] += S.c[0] * f0 + S.c[1] * f1;
         const float dx = S.c[5] * f0 - S.c[6] * f1;
         bV[r] += S.c[2] * f0 * f0 + S.c[3] * f1 * f1 + S.c[4] * dx * dx;
