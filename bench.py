@@ -332,10 +332,11 @@ def run_reference(args, rank, world):
 # ----------------------------------------------------------------------------- GPU arm
 def measure_peaks(P):
     out = {}
-    for kind in ("fp32", "ex2", "fp64"):
+    for kind in ("fp32", "ex2", "fp64", "fp32x2"):
         rate, _ = P.measure_peak(kind)
         out[kind] = rate
     return {"fp32_fma_tflops": out["fp32"] / 1e12, "ex2_tops": out["ex2"] / 1e12, "fp64_fma_tflops": out["fp64"] / 1e12,
+            "fp32x2_fma_tflops": out["fp32x2"] / 1e12,
             "how": "celeste_measure_peak: independent FMA / ex2.approx chains on every SM, best of 3 launches of "
                    "~25 ms each, CUDA events, before the timed steps"}
 

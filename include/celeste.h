@@ -367,7 +367,9 @@ int celeste_profile_stop(celeste_problem* p, celeste_profile_stats* out);
  * rooflines (not part of the method):
  *   kind 0: FP32 fused multiply-add, in flop/s (2 per FMA) - the pixel kernels' bound;
  *   kind 1: the special-function unit's base-2 exponential (ex2.approx), in operations/s;
- *   kind 2: FP64 fused multiply-add, in flop/s - the trust-region step's pipe.
+ *   kind 2: FP64 fused multiply-add, in flop/s - the trust-region step's pipe;
+ *   kind 3: FP32 fused multiply-add issued two lanes wide (packed FP32), in flop/s - the form the
+ *           pixel kernels' galaxy components use.
  * Runs independent FMA (or ex2) chains on every SM, grown until a launch lasts ~25 ms, and reports
  * the best of three launches timed by CUDA events on `stream`; *seconds (may be NULL) gets that
  * launch's duration.  Synchronous; allocates and frees a few MB of device memory. */

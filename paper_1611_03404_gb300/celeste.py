@@ -369,8 +369,9 @@ def tr_reciprocal(x, stream=None):
 
 def measure_peak(kind, stream=None):
     """Measured rate of one pipe of the current device: kind "fp32" (FMA flop/s), "ex2" (special-function
-    exponentials/s) or "fp64" (FMA flop/s).  Returns (rate, seconds of the timed launch)."""
-    k = {"fp32": 0, "ex2": 1, "fp64": 2}[kind]
+    exponentials/s), "fp64" (FMA flop/s) or "fp32x2" (packed two-wide FP32 FMA flop/s).  Returns (rate,
+    seconds of the timed launch)."""
+    k = {"fp32": 0, "ex2": 1, "fp64": 2, "fp32x2": 3}[kind]
     rate, sec = ctypes.c_double(0.0), ctypes.c_double(0.0)
     _check(lib().celeste_measure_peak(ctypes.c_int(k), ctypes.byref(rate), ctypes.byref(sec), _stream(stream)))
     return rate.value, sec.value

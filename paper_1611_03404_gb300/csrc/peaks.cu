@@ -34,6 +34,25 @@ __global__ void __launch_bounds__(PK_THREADS) peak_ffma_kernel(float* out, int i
   out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
+// The same chains two lanes wide (Blackwell's packed FP32 multiply-add): PK_CHAINS / 2 packed
+// chains do PK_CHAINS multiply-adds per step, the count the FP32 kernel above does.
+__global__ void __launch_bounds__(PK_THREADS) peak_ffma2_kernel(float* out, int iters, float a, float b) {
+  float2 x[PK_CHAINS / 2];
+#pragma unroll
+  for (int c = 0; c < PK_CHAINS / 2; ++c) x[c] = make_float2(1e-3f * (threadIdx.x + 2 * c), 1e-3f * (threadIdx.x + 2 * c + 1));
+  const float2 a2 = make_float2(a, a), b2 = make_float2(b, b);
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int u = 0; u < 16; ++u)
+#pragma unroll
+      for (int c = 0; c < PK_CHAINS / 2; ++c) x[c] = __ffma2_rn(x[c], a2, b2);
+  }
+  float s = 0.f;
+#pragma unroll
+  for (int c = 0; c < PK_CHAINS / 2; ++c) s += x[c].x + x[c].y;
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
 __device__ __forceinline__ float ex2_approx(float x) {
   float y;
   asm volatile("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -77,7 +96,7 @@ __global__ void __launch_bounds__(PK_THREADS) peak_dfma_kernel(double* out, int 
 using namespace celeste;
 
 extern "C" int celeste_measure_peak(int kind, double* ops_per_s, double* seconds, celeste_stream_t stream) {
-  if (!ops_per_s || kind < 0 || kind > 2) return fail(CELESTE_ERR_INVALID_ARG, "kind must be 0, 1 or 2");
+  if (!ops_per_s || kind < 0 || kind > 3) return fail(CELESTE_ERR_INVALID_ARG, "kind must be 0, 1, 2 or 3");
   cudaStream_t st = (cudaStream_t)stream;
   int dev = 0, n_sm = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -103,6 +122,8 @@ extern "C" int celeste_measure_peak(int kind, double* ops_per_s, double* seconds
         peak_ffma_kernel<<<grid, PK_THREADS, 0, st>>>(static_cast<float*>(buf), it, 0.9999f, 1e-4f);
       else if (kind == 1)
         peak_ex2_kernel<<<grid, PK_THREADS, 0, st>>>(static_cast<float*>(buf), it);
+      else if (kind == 3)
+        peak_ffma2_kernel<<<grid, PK_THREADS, 0, st>>>(static_cast<float*>(buf), it, 0.9999f, 1e-4f);
       else
         peak_dfma_kernel<<<grid, PK_THREADS, 0, st>>>(static_cast<double*>(buf), it, 0.9999, 1e-4);
     };
